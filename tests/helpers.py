@@ -1,0 +1,65 @@
+"""Small hand-built scenes and cameras for the pins and parity tests."""
+import numpy as np
+
+from paper_2501_00342_b300 import inputs as I
+
+
+def make_scene(means, scales, quats, opacity, sh, sg_amp=None, sg_axis=None, sg_sharp=None,
+               axis_mode=I.AXIS_FREE):
+    """means [n,3], scales [n,3], quats [n,4] (w,x,y,z), opacity [n], sh [n,(L+1)^2,3],
+    sg_amp [n,K,3], sg_axis [n,K,3], sg_sharp [n,K]."""
+    means = np.asarray(means, np.float64).reshape(-1, 3)
+    n = means.shape[0]
+    s = I.padded_stride(n)
+    sh = np.asarray(sh, np.float64).reshape(n, -1, 3)
+    nsh = sh.shape[1]
+    L = int(round(np.sqrt(nsh))) - 1
+    K = 0 if sg_amp is None else np.asarray(sg_amp).reshape(n, -1, 3).shape[1]
+
+    def plane(shape):
+        return np.zeros(shape + (s,), np.float32)
+
+    mean = plane((3,)); mean[:, :n] = means.T
+    scale = plane((3,)); scale[:, :n] = np.asarray(scales, np.float64).reshape(n, 3).T
+    rot = plane((4,)); rot[:, :n] = np.asarray(quats, np.float64).reshape(n, 4).T
+    opa = plane(()); opa[:n] = np.asarray(opacity, np.float64).reshape(n)
+    shp = plane((nsh, 3)); shp[:, :, :n] = np.transpose(sh, (1, 2, 0))
+    amp = plane((K, 3)); sharp = plane((K,)); axis = None
+    if K:
+        amp[:, :, :n] = np.transpose(np.asarray(sg_amp, np.float64).reshape(n, K, 3), (1, 2, 0))
+        sharp[:, :n] = np.asarray(sg_sharp, np.float64).reshape(n, K).T
+        if axis_mode == I.AXIS_FREE:
+            axis = plane((K, 3))
+            axis[:, :, :n] = np.transpose(np.asarray(sg_axis, np.float64).reshape(n, K, 3), (1, 2, 0))
+    return I.Scene(n, s, L, K, axis_mode, mean, scale, rot, opa, shp, amp, axis, sharp)
+
+
+def axis_camera(width=128, height=128, fov=60.0, dist=4.0, cx=None, cy=None):
+    """Camera on +z at ``dist`` looking at the origin; optional principal point."""
+    cam = I.look_at((0.0, 0.0, dist), (0.0, 0.0, 0.0), width, height, fov)
+    if cx is not None:
+        cam.cx = cx
+    if cy is not None:
+        cam.cy = cy
+    return cam
+
+
+def random_small_scene(n, seed, sh_degree=1, K=2, axis_mode=I.AXIS_FREE, log_scale=(-1.6, 0.3),
+                       extent=0.8):
+    """Bigger Gaussians than the workloads, so that each covers many pixels of a small
+    image (useful for finite differences)."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-extent, extent, (n, 3))
+    scales = np.exp(rng.normal(log_scale[0], log_scale[1], (n, 3)))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q *= rng.uniform(0.5, 2.0, (n, 1))  # unnormalised on purpose
+    opacity = 1.0 / (1.0 + np.exp(-rng.normal(0.0, 1.5, n)))
+    nsh = (sh_degree + 1) ** 2
+    sh = rng.normal(0.0, 0.3, (n, nsh, 3))
+    sh[:, 0, :] = rng.normal(0.5, 0.3, (n, 3))
+    amp = rng.normal(0.0, 0.3, (n, K, 3))
+    axis = rng.normal(size=(n, K, 3)) * rng.uniform(0.5, 2.0, (n, K, 1))
+    sharp = np.exp(rng.uniform(0.0, np.log(20.0), (n, K)))
+    return make_scene(means, scales, q, opacity, sh, amp if K else None,
+                      axis if K else None, sharp if K else None, axis_mode)
