@@ -1,0 +1,221 @@
+/*
+ * sgs.h -- C ABI of the SG-Splatting tile rasterizer for NVIDIA B300 (sm_103a).
+ *
+ * The method (arXiv 2501.00342, SG-Splatting) renders a set of 3D Gaussians
+ * {X, Sigma(q, s), opacity, colour parameters} seen from a pinhole camera into an image
+ * (Sec. "Overview" and "Preliminaries": Eq. 2-3, the EWA projection the paper cites, and
+ * alpha blending).  Colour is a low-degree SH term plus K spherical-Gaussian lobes
+ * (Eq. 4-9).  The hot path has five stages, each a hand-written CUDA kernel:
+ *   (a) per-Gaussian preprocess: EWA projection to a 2D conic, 3-sigma radius, tile
+ *       rectangle, SH+SG colour                                       -> sgs_preprocess
+ *   (b) tile|depth key duplication, (c) LSD radix sort of the 64-bit keys,
+ *   (d) per-tile range identification                                 -> sgs_bin_sort
+ *   (e) front-to-back alpha blending per pixel                        -> sgs_render
+ * and a hand-written backward pass                                    -> sgs_render_backward
+ *
+ * Conventions shared by every entry point:
+ *  - Memory: the caller owns all device memory and streams.  No entry point allocates
+ *    device or host memory.  The caller sizes the workspace with sgs_workspace_size()
+ *    and keeps the filled sgs_plan (plain host struct) for the later calls.
+ *  - Streams: every call enqueues work on the given stream and returns without
+ *    synchronising, except sgs_bin_sort() with a non-NULL count pointer and
+ *    sgs_read_device_status(), which synchronise that stream.
+ *  - Errors: argument errors are returned at once (SGS_ERR_INVALID).  Errors found on
+ *    the device (instance overflow, a bounded wait that ran out) are OR-ed into a
+ *    status word in the workspace; read it with sgs_read_device_status().  CUDA launch
+ *    errors return SGS_ERR_CUDA.  Nothing traps on the device.
+ *  - Numerics: FP32 throughout.  The stages that decide integers (cull, depth bits,
+ *    radius, tile rectangle, support membership) use correctly rounded FP32
+ *    operations in a fixed order, so keys, sort order and ranges are reproducible
+ *    bit for bit.
+ *  - Views: B cameras of any resolutions are processed together ("batched"); B = 1 is
+ *    the plain single-view path.  Images are planar RGB [3][H_v][W_v] per view, the
+ *    views packed one after the other (view v starts at 3 * pixel_offset(v) floats).
+ */
+#ifndef SGS_H
+#define SGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGS_MAX_VIEWS 64
+#define SGS_MAX_SH_DEGREE 3
+#define SGS_MAX_LOBES 4
+
+typedef enum {
+    SGS_OK = 0,
+    SGS_ERR_INVALID = 1,  /* bad argument, size, alignment or layout */
+    SGS_ERR_CAPACITY = 2, /* more (record, tile) instances than the workspace holds */
+    SGS_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out (the result is invalid) */
+    SGS_ERR_CUDA = 8      /* a CUDA runtime call or launch failed */
+} sgs_status;
+
+typedef enum {
+    SGS_AXIS_FREE = 0,       /* each lobe has its own axis mu_k, normalised in the kernel */
+    SGS_AXIS_ORTHO_FIXED = 1 /* lobes k = 0,1,2 use the world axes (Eq. 7-8 and
+                                Sec. "Implementation"); no axis is stored, K <= 3 */
+} sgs_axis_mode;
+
+/* Pinhole camera, OpenCV axes (+x right, +y down, +z forward).
+ * viewmat: world->camera [R | t], 3x4 row-major.  campos: camera centre in world space
+ * (the view direction of Eq. 5 is d = (X - campos)/|X - campos|).  Pixel (x, y) has its
+ * centre at (x + 0.5, y + 0.5).  88 bytes. */
+typedef struct {
+    float viewmat[12];
+    float campos[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_plane; /* Gaussians with view depth <= near_plane are culled */
+} sgs_camera;
+
+/* Gaussian parameters, structure of arrays, device pointers.  Each plane has n valid
+ * entries and a row stride of `stride` floats (stride >= n, a multiple of 4, every
+ * pointer 16-byte aligned).  Parameters are already activated: scale > 0,
+ * opacity in (0, 1), sharpness lambda as given.
+ *   mean     [3][stride]              X (Eq. 2)
+ *   scale    [3][stride]              s (Eq. 3)
+ *   rot      [4][stride]              q = (w, x, y, z), any non-zero norm (Eq. 3)
+ *   opacity  [stride]
+ *   sh       [(L+1)^2][3][stride]     SH coefficients c_lm per RGB channel (Eq. 4),
+ *                                     basis index l*l + l + m, Condon-Shortley phase
+ *   sg_amp   [K][3][stride]           lobe amplitudes alpha_k per channel (Eq. 5, 7)
+ *   sg_axis  [K][3][stride]           lobe axes mu_k (free-axis mode; NULL otherwise)
+ *   sg_sharp [K][stride]              lobe sharpness lambda_k
+ * colour = max(0, sum_lm c_lm Y_lm(d) + 0.5 + sum_k alpha_k exp(lambda_k (mu_k.d - 1))). */
+typedef struct {
+    int64_t n, stride;
+    int32_t sh_degree; /* L in 0..3 */
+    int32_t num_lobes; /* K in 0..4 (0..3 in SGS_AXIS_ORTHO_FIXED) */
+    int32_t axis_mode; /* sgs_axis_mode */
+    const float *mean, *scale, *rot, *opacity, *sh, *sg_amp, *sg_axis, *sg_sharp;
+} sgs_gaussians;
+
+/* Parameter gradients, same layouts as sgs_gaussians (device pointers, overwritten). */
+typedef struct {
+    float *mean, *scale, *rot, *opacity, *sh, *sg_amp, *sg_axis, *sg_sharp;
+} sgs_grads;
+
+typedef struct {
+    int32_t tile_w, tile_h; /* screen tile, pixels; tile_w * tile_h in {64,128,256,512} */
+    int32_t batch_depth;    /* Gaussians staged in shared memory per blend batch: 32..1024 */
+    int32_t digit_bits;     /* radix-sort digit width, 4..8 */
+    int32_t memory_mode;    /* 0: backward recomputes per tile from the sorted list
+                               (no per-pixel contributor lists are ever stored) */
+    float bg[3];            /* background colour added as T_final * bg */
+} sgs_settings;
+
+/* Host-side plan: sizes and workspace offsets.  Filled by sgs_workspace_size(); the
+ * caller owns it (stack or heap) and passes it to the stage calls.  Opaque fields. */
+typedef struct {
+    int64_t n, stride;
+    int32_t sh_degree, num_lobes, axis_mode, B;
+    sgs_settings settings;
+    sgs_camera cams[SGS_MAX_VIEWS];
+    int32_t tiles_x[SGS_MAX_VIEWS], tiles_y[SGS_MAX_VIEWS];
+    int64_t tile_base[SGS_MAX_VIEWS + 1];  /* first global tile id of each view */
+    int64_t pixel_base[SGS_MAX_VIEWS + 1]; /* first pixel of each view */
+    int64_t num_records;                   /* B * n */
+    int64_t num_tiles, num_pixels;
+    int64_t instance_capacity;
+    int32_t key_bits, sort_passes;
+    int32_t stage; /* last stage run on the bound workspace: 1 preprocess, 2 bin/sort,
+                      3 render; a stage call before its predecessor returns SGS_ERR_INVALID */
+    size_t offsets[32]; /* byte offsets of the workspace regions */
+    size_t workspace_bytes;
+    void* workspace; /* bound by sgs_preprocess() */
+} sgs_plan;
+
+/* Fills *plan and *bytes (device workspace size, 256-byte aligned) for n Gaussians seen
+ * by B <= SGS_MAX_VIEWS cameras (host array), at most instance_capacity (record, tile)
+ * instances (< 2^32).  Pure host computation.  Returns SGS_ERR_INVALID for bad sizes or
+ * settings. */
+sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, int32_t B,
+                              const sgs_settings* settings, int64_t instance_capacity,
+                              sgs_plan* plan, size_t* bytes);
+
+/* Stage (a): per (view, Gaussian) record -- cull, depth, screen mean, conic, radius,
+ * tile rectangle, colour -- for all B views in one launch (parameters are read once).
+ * Binds `workspace` (device, >= plan->workspace_bytes, 256-byte aligned) to the plan
+ * and clears the device status word.  g must match the sizes the plan was made for. */
+sgs_status sgs_preprocess(sgs_plan* plan, const sgs_gaussians* g, void* workspace,
+                          size_t ws_bytes, cudaStream_t stream);
+
+/* Stages (b)-(d): exclusive scan of tiles touched, duplication of
+ * (global tile id << 32 | float bits of view depth, record id) pairs, stable LSD radix
+ * sort on the low plan->key_bits bits, per-tile [start, end) ranges.  With
+ * num_instances != NULL the call synchronises `stream`, stores the instance count M
+ * and returns SGS_ERR_CAPACITY if M > capacity (then nothing past the scan ran
+ * correctly).  With NULL it does not synchronise (graph capture); overflow is then
+ * reported through the status word and the stages write nothing out of bounds. */
+sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t stream);
+
+/* Stage (e): front-to-back blending of every pixel of every view.  out_rgb: device
+ * float[3 * num_pixels] (planar per view); out_T: device float[num_pixels] final
+ * transmittance, or NULL.  The per-pixel state the backward pass needs stays in the
+ * workspace. */
+sgs_status sgs_render(sgs_plan* plan, float* out_rgb, float* out_T, cudaStream_t stream);
+
+/* Backward of (a)-(e): given dL/d(out_rgb) (device, same layout as out_rgb), writes the
+ * gradient of every parameter plane of g into `out` (overwritten; sg_axis ignored in
+ * ORTHO_FIXED mode).  Requires sgs_render() on the same plan and workspace before. */
+sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const float* dL_drgb,
+                               sgs_grads* out, cudaStream_t stream);
+
+/* Synchronises `stream` and reads the device status word (an OR of sgs_status bits). */
+sgs_status sgs_read_device_status(const sgs_plan* plan, int32_t* status, cudaStream_t stream);
+
+/* Device byte offset of workspace region `which` (sgs_region) and its size; lets tests
+ * and tools read intermediate results (records, keys, ranges). */
+typedef enum {
+    SGS_REGION_STATUS = 0,  /* int32 status, uint32 M (clamped), uint64 M (exact) ... */
+    SGS_REGION_REC0 = 1,    /* float4[R]: px, py, -A/2, -B           (R = B * n) */
+    SGS_REGION_REC1 = 2,    /* float4[R]: -C/2, opacity, view depth, radius */
+    SGS_REGION_REC2 = 3,    /* float4[R]: r, g, b, clamp mask bits */
+    SGS_REGION_RECT = 4,    /* uint2[R]:  x0 | y0 << 16, x1 | y1 << 16 (0,0 if culled) */
+    SGS_REGION_TILES = 5,   /* uint32[R]: tiles touched (0 if culled) */
+    SGS_REGION_OFFSETS = 6, /* uint32[R]: exclusive scan of TILES */
+    SGS_REGION_KEYS = 7,    /* uint64[capacity]: sorted keys after sgs_bin_sort */
+    SGS_REGION_VALS = 8,    /* uint32[capacity]: sorted record ids */
+    SGS_REGION_KEYS_IN = 9, /* uint64[capacity]: keys before the sort (clobbered by it
+                               when the pass count is even) */
+    SGS_REGION_VALS_IN = 10,
+    SGS_REGION_RANGES = 11, /* uint2[num_tiles]: [start, end) per global tile */
+    SGS_REGION_PIX_T = 12,  /* float[num_pixels]: final transmittance */
+    SGS_REGION_PIX_LAST = 13, /* uint32[num_pixels]: 1 + position of the last contributor
+                                 in the tile's list (0: none) */
+    SGS_REGION_GRAD2D = 14, /* float4[3][R]: dL/d(px, py, A, B), (C, opacity, r, g), (b) */
+    SGS_REGION_COUNT = 15
+} sgs_region;
+sgs_status sgs_region_info(const sgs_plan* plan, int32_t which, size_t* offset, size_t* bytes);
+
+/* Stable LSD radix sort of m (uint64 key, uint32 value) pairs in place on their low
+ * key_bits bits (1..64), the same onesweep kernels sgs_bin_sort uses.  `temp` is device
+ * scratch of at least sgs_sort_temp_bytes(m, key_bits, digit_bits) bytes.  Exposed for
+ * tests of the sort alone. */
+sgs_status sgs_sort_temp_bytes(int64_t m, int32_t key_bits, int32_t digit_bits, size_t* bytes);
+sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key_bits,
+                          int32_t digit_bits, void* temp, size_t temp_bytes,
+                          cudaStream_t stream);
+
+/* Mean absolute error loss of a rendered image against a target, and its gradient:
+ * loss[0] = sum |img - target| / count (device float, written), dL_dimg = sign(img -
+ * target) / count (sign(0) = 0).  Used for the differentiable training step. */
+sgs_status sgs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
+                       float* dL_dimg, cudaStream_t stream);
+
+const char* sgs_status_string(sgs_status s);
+
+/* sizeof(sgs_plan), sizeof(sgs_camera), sizeof(sgs_gaussians), sizeof(sgs_settings) in
+ * that order into sizes[4]: lets a foreign-language binding check its struct layouts. */
+void sgs_abi_sizes(size_t* sizes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGS_H */

@@ -1,0 +1,312 @@
+// Stage (e): front-to-back alpha blending per pixel, and its reverse-mode pass.
+//
+// One CTA per (view, tile), one pixel per thread.  The tile's depth-sorted instance list
+// [start, end) is staged batch_depth Gaussians at a time in shared memory (three float4
+// records per Gaussian, gathered through the sorted record ids).  Per pixel centre p:
+//   power = -1/2 (A dx^2 + C dy^2) - B dx dy;  skip if power < -4.5 (outside 3 sigma)
+//   alpha = min(0.99, opacity exp(power));      skip if alpha < 1/255
+//   T' = T (1 - alpha);                          stop before this Gaussian if T' < 1e-4
+//   C += rgb alpha T;  T = T'
+// and the pixel is C + T bg.  A thread whose pixel is finished leaves the inner loop (its
+// warp leaves when all 32 lanes have), and the CTA stops fetching batches once
+// __syncthreads_count reports every pixel finished.
+//
+// The backward pass walks each tile's list from the last contributor to the front,
+// rebuilding T_k = T_{k+1} / (1 - alpha_k) from the stored final transmittance and
+// carrying the normalised colour behind (acc = acc (1 - alpha) + rgb alpha, starting at
+// bg).  It recomputes power and alpha with the same operations as the forward pass, so
+// every skip decision is identical; per Gaussian the warp's 9 gradient terms are summed
+// with shuffles and added with one vector atomic per float4.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgs {
+namespace {
+
+struct TileCoord {
+    int v, tx, ty;
+};
+
+__device__ __forceinline__ TileCoord tile_of(const ViewTable& vt, uint32_t g) {
+    int v = 0;
+    while (v + 1 < vt.B && vt.v[v + 1].tile_base <= g) ++v;
+    const uint32_t local = g - vt.v[v].tile_base;
+    TileCoord c;
+    c.v = v;
+    c.tx = (int)(local % (uint32_t)vt.v[v].tiles_x);
+    c.ty = (int)(local / (uint32_t)vt.v[v].tiles_x);
+    return c;
+}
+
+// Tile range clipped to the instances actually written (all of them unless overflowed).
+__device__ __forceinline__ uint2 clamp_range(uint2 r, uint32_t m) {
+    r.y = min(r.y, m);
+    r.x = min(r.x, r.y);
+    return r;
+}
+
+__global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const uint2* __restrict__ ranges,
+                                                     const uint32_t* __restrict__ vals, uint32_t R,
+                                                     const float4* __restrict__ rec0,
+                                                     const float4* __restrict__ rec1,
+                                                     const float4* __restrict__ rec2, int batch,
+                                                     float bg0, float bg1, float bg2,
+                                                     float* __restrict__ out_rgb,
+                                                     float* __restrict__ out_T,
+                                                     float* __restrict__ pix_T,
+                                                     uint32_t* __restrict__ pix_last,
+                                                     const DeviceStatus* __restrict__ st) {
+    extern __shared__ float4 sbuf[];
+    float4* s0 = sbuf;
+    float4* s1 = sbuf + batch;
+    float4* s2 = sbuf + 2 * batch;
+    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const View& cam = vt.v[tc.v];
+    const int lx = threadIdx.x % vt.tile_w, ly = threadIdx.x / vt.tile_w;
+    const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly;
+    const bool inside = x < cam.W && y < cam.H;
+    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    const int n = (int)(range.y - range.x);
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (int base = 0; base < n; base += batch) {
+        if (__syncthreads_count(!done) == 0) break;
+        const int cnt = min(batch, n - base);
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const uint32_t id = min(vals[range.x + base + j], R - 1);  // ids are < R by construction
+            s0[j] = rec0[id];
+            s1[j] = rec1[id];
+            s2[j] = rec2[id];
+        }
+        __syncthreads();
+        for (int k = 0; !done && k < cnt; ++k) {
+            const float4 a = s0[k];
+            const float4 b = s1[k];
+            const float power = support_power(a.z, a.w, b.x, a.x - pxc, a.y - pyc);
+            if (!(power >= kSupportPower)) continue;  // also skips a NaN exponent
+            const float alpha = fminf(kAlphaMax, b.y * __expf(power));
+            if (alpha < kAlphaMin) continue;
+            const float Tn = T * (1.0f - alpha);
+            if (Tn < kTransmittanceMin) {
+                done = true;
+                break;
+            }
+            const float4 c = s2[k];
+            const float w = alpha * T;
+            C0 += c.x * w;
+            C1 += c.y * w;
+            C2 += c.z * w;
+            T = Tn;
+            last = (uint32_t)(base + k + 1);
+        }
+    }
+    if (inside) {
+        const int64_t hw = (int64_t)cam.W * cam.H;
+        const int64_t p = (int64_t)y * cam.W + x;
+        float* img = out_rgb + 3 * cam.pixel_base;
+        img[p] = C0 + T * bg0;
+        img[hw + p] = C1 + T * bg1;
+        img[2 * hw + p] = C2 + T * bg2;
+        if (out_T) out_T[cam.pixel_base + p] = T;
+        pix_T[cam.pixel_base + p] = T;
+        pix_last[cam.pixel_base + p] = last;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(512) blend_backward_kernel(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, uint32_t R32,
+    const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
+    int batch, float bg0, float bg1, float bg2, const float* __restrict__ pix_T,
+    const uint32_t* __restrict__ pix_last, const float* __restrict__ dL_drgb,
+    float4* __restrict__ grad2d, int64_t R, const DeviceStatus* __restrict__ st) {
+    extern __shared__ float4 sbuf[];
+    float4* s0 = sbuf;
+    float4* s1 = sbuf + batch;
+    float4* s2 = sbuf + 2 * batch;
+    uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
+    __shared__ uint32_t s_max_last;
+    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const View& cam = vt.v[tc.v];
+    const int lx = threadIdx.x % vt.tile_w, ly = threadIdx.x / vt.tile_w;
+    const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly;
+    const bool inside = x < cam.W && y < cam.H;
+    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    uint32_t last = 0;
+    if (threadIdx.x == 0) s_max_last = 0;
+    __syncthreads();
+    if (inside) {
+        const int64_t hw = (int64_t)cam.W * cam.H;
+        const int64_t p = (int64_t)y * cam.W + x;
+        const float* gi = dL_drgb + 3 * cam.pixel_base;
+        g0 = gi[p];
+        g1 = gi[hw + p];
+        g2 = gi[2 * hw + p];
+        T = pix_T[cam.pixel_base + p];
+        last = min(pix_last[cam.pixel_base + p], range.y - range.x);
+    }
+    const uint32_t wmax = __reduce_max_sync(kFullMask, last);
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_max_last, wmax);
+    __syncthreads();
+    const int top = (int)s_max_last;
+    float acc0 = bg0, acc1 = bg1, acc2 = bg2;
+    const int lane = threadIdx.x & 31;
+    for (int hi = top; hi > 0; hi -= batch) {
+        const int lo = max(0, hi - batch);
+        __syncthreads();
+        for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) {
+            const uint32_t id = min(vals[range.x + lo + j], R32 - 1);  // ids are < R by construction
+            sid[j] = id;
+            s0[j] = rec0[id];
+            s1[j] = rec1[id];
+            s2[j] = rec2[id];
+        }
+        __syncthreads();
+        for (int k = hi - 1; k >= lo; --k) {
+            const float4 a = s0[k - lo];
+            const float4 b = s1[k - lo];
+            float d[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) d[q] = 0.0f;
+            bool contrib = (uint32_t)k < last;
+            if (contrib) {
+                const float dx = a.x - pxc, dy = a.y - pyc;
+                const float power = support_power(a.z, a.w, b.x, dx, dy);
+                const float G = __expf(power);
+                const float oG = b.y * G;
+                const float alpha = fminf(kAlphaMax, oG);
+                contrib = power >= kSupportPower && alpha >= kAlphaMin;
+                if (contrib) {
+                    const float4 c = s2[k - lo];
+                    T = T / (1.0f - alpha);
+                    const float w = alpha * T;
+                    d[6] = g0 * w;
+                    d[7] = g1 * w;
+                    d[8] = g2 * w;
+                    const float dalpha = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
+                    acc0 = acc0 * (1.0f - alpha) + c.x * alpha;
+                    acc1 = acc1 * (1.0f - alpha) + c.y * alpha;
+                    acc2 = acc2 * (1.0f - alpha) + c.z * alpha;
+                    if (oG <= kAlphaMax) {
+                        const float gpow = dalpha * b.y * G;
+                        // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2)
+                        d[0] = gpow * (2.0f * a.z * dx + a.w * dy);
+                        d[1] = gpow * (a.w * dx + 2.0f * b.x * dy);
+                        d[2] = gpow * (-0.5f * dx * dx);
+                        d[3] = gpow * (-dx * dy);
+                        d[4] = gpow * (-0.5f * dy * dy);
+                        d[5] = dalpha * G;
+                    }
+                }
+            }
+            if (__any_sync(kFullMask, contrib)) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) d[q] = warp_sum(d[q]);
+                if (lane == 0) {
+                    const uint32_t id = sid[k - lo];
+                    atomicAdd(grad2d + id, make_float4(d[0], d[1], d[2], d[3]));
+                    atomicAdd(grad2d + R + id, make_float4(d[4], d[5], d[6], d[7]));
+                    atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), d[8]);
+                }
+            }
+        }
+    }
+}
+
+__global__ void zero_grad2d_kernel(float4* __restrict__ g, const uint32_t* __restrict__ tiles, int64_t R) {
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (tiles[r] == 0u) continue;
+        g[r] = z;
+        g[R + r] = z;
+        g[2 * R + r] = z;
+    }
+}
+
+__global__ void l1_zero_kernel(float* loss) { *loss = 0.0f; }
+
+__global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, const float* __restrict__ tgt,
+                                                  int64_t count, float* loss, float* __restrict__ grad) {
+    const float inv = 1.0f / (float)count;
+    float acc = 0.0f;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const float e = img[j] - tgt[j];
+        acc += fabsf(e);
+        grad[j] = e > 0.0f ? inv : (e < 0.0f ? -inv : 0.0f);
+    }
+    acc = warp_sum(acc);
+    __shared__ float s[8];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+        atomicAdd(loss, t * inv);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
+                         int64_t R, const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
+                         float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
+                         const DeviceStatus* st, cudaStream_t s) {
+    if (vt.num_tiles == 0) return cudaSuccess;
+    const int threads = vt.tile_w * vt.tile_h;
+    const size_t smem = (size_t)batch * 3 * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(blend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // with no records every range is empty and no id is read; the kernel still writes bg
+    blend_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch,
+                                                              bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
+                                  const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
+                                  const float* pix_T, const uint32_t* pix_last,
+                                  const float* dL_drgb, float4* grad2d, int64_t R,
+                                  const DeviceStatus* st, cudaStream_t s) {
+    if (vt.num_tiles == 0 || R == 0) return cudaSuccess;
+    const int threads = vt.tile_w * vt.tile_h;
+    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t));
+    cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    blend_backward_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(
+        vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb,
+        grad2d, R, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    const int64_t want = (R + 255) / 256;
+    zero_grad2d_kernel<<<(int)(want < 148 * 16 ? want : 148 * 16), 256, 0, s>>>(grad2d, tiles, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float* loss,
+                           float* dL_dimg, cudaStream_t s) {
+    l1_zero_kernel<<<1, 1, 0, s>>>(loss);
+    if (count > 0) {
+        const int64_t want = (count + 255) / 256;
+        l1_kernel<<<(int)(want < 148 * 8 ? want : 148 * 8), 256, 0, s>>>(img, target, count, loss, dL_dimg);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sgs

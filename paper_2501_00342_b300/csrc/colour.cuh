@@ -1,0 +1,232 @@
+// SH + SG view-dependent colour (Eq. 4-9) on the device, forward and gradient.
+//
+// Real SH basis Y_lm, index l*l + l + m, Condon-Shortley phase, written as polynomials of
+// the unit direction d = (x, y, z).  The constants are the normalisations
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0) multiplied into the
+// Legendre-derivative factors:
+//   l=0: 1/(2 sqrt(pi))
+//   l=1: sqrt(3/(4 pi)) {-y, z, -x}
+//   l=2: 1/2 sqrt(15/pi) {xy, -yz, -xz}, 1/4 sqrt(5/pi) (3z^2-1), 1/4 sqrt(15/pi) (x^2-y^2)
+//   l=3: -1/4 sqrt(35/(2pi)) {y(3x^2-y^2), x(x^2-3y^2)}, 1/2 sqrt(105/pi) xyz,
+//        -1/4 sqrt(21/(2pi)) {y, x}(5z^2-1), 1/4 sqrt(7/pi) z(5z^2-3),
+//        1/4 sqrt(105/pi) z(x^2-y^2)
+// SG lobe (Eq. 5): a_k exp(lambda_k (mu_k . d - 1)), mu_k normalised (free axes) or the
+// world axis e_k (Eq. 7-8 with the axes of Sec. "Implementation").
+// colour = max(0, SH(d) + 0.5 + sum_k SG_k(d)) per channel (Eq. 9 with the diffuse term
+// being the l = 0 SH band).
+#pragma once
+#include "sgs.h"
+
+namespace sgs {
+
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.4886025119029199f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.5462742152960396f;
+constexpr float kY3a = -0.5900435899266435f;
+constexpr float kY3b = 2.890611442640554f;
+constexpr float kY3c = -0.4570457994644658f;
+constexpr float kY3d = 0.3731763325901154f;
+constexpr float kY3e = 1.445305721320277f;
+
+template <int L>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = kY0;
+    if (L >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+    }
+    if (L >= 2) {
+        const float z2 = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = -kY2a * y * z;
+        Y[6] = kY2b * (3.0f * z2 - 1.0f);
+        Y[7] = -kY2a * x * z;
+        Y[8] = kY2c * (x * x - y * y);
+    }
+    if (L >= 3) {
+        const float x2 = x * x, y2 = y * y, z2 = z * z;
+        Y[9] = kY3a * y * (3.0f * x2 - y2);
+        Y[10] = kY3b * x * y * z;
+        Y[11] = kY3c * y * (5.0f * z2 - 1.0f);
+        Y[12] = kY3d * z * (5.0f * z2 - 3.0f);
+        Y[13] = kY3c * x * (5.0f * z2 - 1.0f);
+        Y[14] = kY3e * z * (x2 - y2);
+        Y[15] = kY3a * x * (x2 - 3.0f * y2);
+    }
+}
+
+// Accumulates g_k * grad(Y_k) (ambient gradient of the polynomial forms above).
+template <int L>
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float* g, float& gx,
+                                             float& gy, float& gz) {
+    if (L >= 1) {
+        gx += -kY1 * g[3];
+        gy += -kY1 * g[1];
+        gz += kY1 * g[2];
+    }
+    if (L >= 2) {
+        gx += kY2a * y * g[4] - kY2a * z * g[7] + 2.0f * kY2c * x * g[8];
+        gy += kY2a * x * g[4] - kY2a * z * g[5] - 2.0f * kY2c * y * g[8];
+        gz += -kY2a * y * g[5] + 6.0f * kY2b * z * g[6] - kY2a * x * g[7];
+    }
+    if (L >= 3) {
+        const float x2 = x * x, y2 = y * y, z2 = z * z;
+        gx += 6.0f * kY3a * x * y * g[9] + kY3b * y * z * g[10] + kY3c * (5.0f * z2 - 1.0f) * g[13] +
+              2.0f * kY3e * x * z * g[14] + kY3a * (3.0f * x2 - 3.0f * y2) * g[15];
+        gy += kY3a * (3.0f * x2 - 3.0f * y2) * g[9] + kY3b * x * z * g[10] +
+              kY3c * (5.0f * z2 - 1.0f) * g[11] - 2.0f * kY3e * y * z * g[14] - 6.0f * kY3a * x * y * g[15];
+        gz += kY3b * x * y * g[10] + 10.0f * kY3c * y * z * g[11] + kY3d * (15.0f * z2 - 3.0f) * g[12] +
+              10.0f * kY3c * x * z * g[13] + kY3e * (x2 - y2) * g[14];
+    }
+}
+
+// Colour parameters of one Gaussian held in registers.
+template <int L, int K, bool FIXED>
+struct ColourParams {
+    static constexpr int NSH = (L + 1) * (L + 1);
+    float sh[NSH][3];
+    float amp[K > 0 ? K : 1][3];
+    float axis[(K > 0 && !FIXED) ? K : 1][3];  // normalised in load()
+    float axis_norm[(K > 0 && !FIXED) ? K : 1];
+    float sharp[K > 0 ? K : 1];
+
+    __device__ __forceinline__ void load(const sgs_gaussians& g, int64_t i) {
+        const int64_t S = g.stride;
+#pragma unroll
+        for (int k = 0; k < NSH; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[k][c] = __ldg(g.sh + (k * 3 + c) * S + i);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) amp[k][c] = __ldg(g.sg_amp + (k * 3 + c) * S + i);
+            sharp[k] = __ldg(g.sg_sharp + k * S + i);
+            if (!FIXED) {
+                float m[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
+                const float n = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                axis_norm[k] = n;
+                const float inv = 1.0f / n;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) axis[k][c] = m[c] * inv;
+            }
+        }
+    }
+
+    __device__ __forceinline__ float lobe_cos(int k, const float* d) const {
+        if (FIXED) return d[k];
+        return axis[k][0] * d[0] + axis[k][1] * d[1] + axis[k][2] * d[2];
+    }
+
+    // pre-clamp colour at unit direction d
+    __device__ __forceinline__ void eval(const float* d, float* pre) const {
+        float Y[NSH];
+        sh_basis<L>(d[0], d[1], d[2], Y);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pre[c] = 0.5f;
+#pragma unroll
+        for (int k = 0; k < NSH; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pre[c] = fmaf(sh[k][c], Y[k], pre[c]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float e = expf(sharp[k] * (lobe_cos(k, d) - 1.0f));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pre[c] = fmaf(amp[k][c], e, pre[c]);
+        }
+    }
+};
+
+// Gradient accumulators of the colour parameters (summed over views).
+template <int L, int K, bool FIXED>
+struct ColourGrads {
+    static constexpr int NSH = (L + 1) * (L + 1);
+    float sh[NSH][3];
+    float amp[K > 0 ? K : 1][3];
+    float axis[(K > 0 && !FIXED) ? K : 1][3];  // w.r.t. the normalised axis
+    float sharp[K > 0 ? K : 1];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < NSH; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[k][c] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                amp[k][c] = 0.0f;
+                if (!FIXED) axis[k][c] = 0.0f;
+            }
+            sharp[k] = 0.0f;
+        }
+    }
+
+    // g_pre: dL/d(pre-clamp colour) at direction d; accumulates into this and returns
+    // dL/dd (ambient) in gd.
+    __device__ __forceinline__ void accumulate(const ColourParams<L, K, FIXED>& p, const float* d,
+                                               const float* g_pre, float* gd) {
+        float Y[NSH];
+        sh_basis<L>(d[0], d[1], d[2], Y);
+        float gY[NSH];
+#pragma unroll
+        for (int k = 0; k < NSH; ++k) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[k][c] = fmaf(g_pre[c], Y[k], sh[k][c]);
+            gY[k] = g_pre[0] * p.sh[k][0] + g_pre[1] * p.sh[k][1] + g_pre[2] * p.sh[k][2];
+        }
+        gd[0] = gd[1] = gd[2] = 0.0f;
+        sh_basis_vjp<L>(d[0], d[1], d[2], gY, gd[0], gd[1], gd[2]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float cs = p.lobe_cos(k, d);
+            const float e = expf(p.sharp[k] * (cs - 1.0f));
+            float s = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                amp[k][c] = fmaf(g_pre[c], e, amp[k][c]);
+                s = fmaf(g_pre[c] * p.amp[k][c], e, s);
+            }
+            sharp[k] = fmaf(s, cs - 1.0f, sharp[k]);
+            const float gcos = s * p.sharp[k];
+            if (FIXED) {
+                gd[k] += gcos;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    gd[c] = fmaf(gcos, p.axis[k][c], gd[c]);
+                    axis[k][c] = fmaf(gcos, d[c], axis[k][c]);
+                }
+            }
+        }
+    }
+
+    __device__ __forceinline__ void store(const ColourParams<L, K, FIXED>& p, const sgs_grads& out,
+                                          int64_t S, int64_t i) const {
+#pragma unroll
+        for (int k = 0; k < NSH; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out.sh[(k * 3 + c) * S + i] = sh[k][c];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out.sg_amp[(k * 3 + c) * S + i] = amp[k][c];
+            out.sg_sharp[k * S + i] = sharp[k];
+            if (!FIXED) {
+                // mu = m/|m|:  dL/dm = (g - mu (mu . g)) / |m|
+                const float dot = axis[k][0] * p.axis[k][0] + axis[k][1] * p.axis[k][1] +
+                                  axis[k][2] * p.axis[k][2];
+                const float inv = 1.0f / p.axis_norm[k];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.axis[k][c] * dot) * inv;
+            }
+        }
+    }
+};
+
+}  // namespace sgs

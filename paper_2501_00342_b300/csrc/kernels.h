@@ -1,0 +1,71 @@
+// Host-side launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sgs {
+
+struct RecordPtrs {
+    float4* rec0;  // px, py, -A/2, -B
+    float4* rec1;  // -C/2, opacity, depth, radius
+    float4* rec2;  // r, g, b, clamp mask
+    uint2* rect;
+    uint32_t* tiles;
+};
+
+// (a) preprocess and its backward
+cudaError_t launch_preprocess(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                              cudaStream_t s);
+cudaError_t launch_preprocess_backward(const sgs_gaussians& g, const ViewTable& vt,
+                                       const RecordPtrs& p, const float4* grad2d, int64_t R,
+                                       const sgs_grads& out, cudaStream_t s);
+
+// (b), (d): scan + duplicate, ranges
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStream_t s);
+cudaError_t launch_scan(const uint32_t* tiles, uint32_t* offsets, int64_t R,
+                        unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
+                        cudaStream_t s);
+cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* offsets,
+                             int64_t n, int64_t R, DeviceStatus* st, int64_t capacity,
+                             unsigned long long* keys, uint32_t* vals, cudaStream_t s);
+cudaError_t launch_ranges(const unsigned long long* keys, const DeviceStatus* st, int64_t capacity,
+                          int64_t num_tiles, uint2* ranges, cudaStream_t s);
+
+// (c) onesweep radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 15;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxSortPasses = 16;
+size_t sort_lookback_entries(int64_t capacity, int digit_bits);
+// Sorts m = *m_ptr pairs (m <= capacity) on bits [0, key_bits); result in (k0,v0) if the
+// pass count is even, else in (k1,v1).  hist/goff: kMaxSortPasses*256 u32 each;
+// counters: kMaxSortPasses u32 (zeroed here); lookback: sort_lookback_entries u64.
+cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
+                        const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
+                        uint32_t* hist, uint32_t* goff, uint32_t* counters,
+                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s);
+int sort_passes(int key_bits, int digit_bits);
+
+// (e) blend and its backward
+cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
+                         int64_t R, const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
+                         float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
+                         const DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
+                                  const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
+                                  const float* pix_T, const uint32_t* pix_last,
+                                  const float* dL_drgb, float4* grad2d, int64_t R,
+                                  const DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s);
+
+cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float* loss,
+                           float* dL_dimg, cudaStream_t s);
+cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
+                              uint32_t* vd, int64_t m, cudaStream_t s);
+cudaError_t launch_sort_init(DeviceStatus* st, uint32_t m, cudaStream_t s);
+
+}  // namespace sgs

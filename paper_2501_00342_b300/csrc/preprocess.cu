@@ -1,0 +1,434 @@
+// Stage (a) of the rasterizer and its backward: per (view, Gaussian) projection and colour.
+//
+// Forward, per Gaussian i (one thread), parameters read once, then for every view v:
+//   t = W X + t_v; cull if t.z <= near
+//   Sigma = R S S^T R^T from q/|q| and s (Eq. 3)
+//   Sigma2D = J W Sigma W^T J^T + 0.3 I, J the EWA Jacobian at t with x/z, y/z clamped
+//             to 1.3x the half field of view (the projection of Sec. "Preliminaries")
+//   conic = Sigma2D^-1, radius = ceil(3 sqrt(lambda_max)), screen mean, tile rectangle
+//   colour = max(0, SH(d) + 0.5 + sum_k SG_k(d)), d = (X - campos)/|X - campos| (Eq. 4-9)
+// Everything up to the tile rectangle and the conic uses correctly rounded operations in
+// one fixed order (mul_rn/add_rn/...), so the cull, depth bits, radius and rectangle are
+// a function of the inputs alone and identical on every run and launch shape.
+#include <cuda_runtime.h>
+
+#include "colour.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgs {
+namespace {
+
+struct Geometry {
+    float Sig[3][3];  // 3D covariance (exactly rounded, fixed order)
+    float R[3][3];
+    float q[4];       // normalised quaternion
+    float qnorm;
+    float s[3];
+};
+
+__device__ __forceinline__ void geometry_exact(const sgs_gaussians& g, int64_t i, Geometry& G) {
+    const int64_t S = g.stride;
+    const float qw0 = __ldg(g.rot + i), qx0 = __ldg(g.rot + S + i), qy0 = __ldg(g.rot + 2 * S + i),
+                qz0 = __ldg(g.rot + 3 * S + i);
+    float nq = mul_rn(qw0, qw0);
+    nq = add_rn(nq, mul_rn(qx0, qx0));
+    nq = add_rn(nq, mul_rn(qy0, qy0));
+    nq = add_rn(nq, mul_rn(qz0, qz0));
+    const float sq = sqrt_rn(nq);
+    const float rq = div_rn(1.0f, sq);
+    const float w = mul_rn(qw0, rq), x = mul_rn(qx0, rq), y = mul_rn(qy0, rq), z = mul_rn(qz0, rq);
+    G.q[0] = w; G.q[1] = x; G.q[2] = y; G.q[3] = z;
+    G.qnorm = sq;
+    const float xx = mul_rn(x, x), yy = mul_rn(y, y), zz = mul_rn(z, z);
+    const float xy = mul_rn(x, y), xz = mul_rn(x, z), yz = mul_rn(y, z);
+    const float wx = mul_rn(w, x), wy = mul_rn(w, y), wz = mul_rn(w, z);
+    G.R[0][0] = sub_rn(1.0f, mul_rn(2.0f, add_rn(yy, zz)));
+    G.R[0][1] = mul_rn(2.0f, sub_rn(xy, wz));
+    G.R[0][2] = mul_rn(2.0f, add_rn(xz, wy));
+    G.R[1][0] = mul_rn(2.0f, add_rn(xy, wz));
+    G.R[1][1] = sub_rn(1.0f, mul_rn(2.0f, add_rn(xx, zz)));
+    G.R[1][2] = mul_rn(2.0f, sub_rn(yz, wx));
+    G.R[2][0] = mul_rn(2.0f, sub_rn(xz, wy));
+    G.R[2][1] = mul_rn(2.0f, add_rn(yz, wx));
+    G.R[2][2] = sub_rn(1.0f, mul_rn(2.0f, add_rn(xx, yy)));
+    G.s[0] = __ldg(g.scale + i);
+    G.s[1] = __ldg(g.scale + S + i);
+    G.s[2] = __ldg(g.scale + 2 * S + i);
+    float M[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[r][c] = mul_rn(G.R[r][c], G.s[c]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            float acc = mul_rn(M[r][0], M[c][0]);
+            acc = add_rn(acc, mul_rn(M[r][1], M[c][1]));
+            acc = add_rn(acc, mul_rn(M[r][2], M[c][2]));
+            G.Sig[r][c] = acc;
+            G.Sig[c][r] = acc;
+        }
+}
+
+struct Projected {
+    bool visible;
+    float t[3];
+    float px, py;
+    float A, B, C;
+    float radius;
+    int x0, y0, x1, y1;
+    // EWA intermediates for the backward pass
+    float u, v;  // clamped x/z, y/z
+    bool clampx, clampy;
+    float J00, J02, J11, J12;
+    float T[2][3];
+    float a, b, c;
+};
+
+// Exact-order projection of one Gaussian into one view.
+__device__ __forceinline__ void project_exact(const View& cam, const float X[3], const Geometry& G,
+                                              int tile_w, int tile_h, Projected& P) {
+    P.visible = false;
+    const float* V = cam.V;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float acc = mul_rn(V[4 * r + 0], X[0]);
+        acc = add_rn(acc, mul_rn(V[4 * r + 1], X[1]));
+        acc = add_rn(acc, mul_rn(V[4 * r + 2], X[2]));
+        P.t[r] = add_rn(acc, V[4 * r + 3]);
+    }
+    const float tz = P.t[2];
+    if (!(tz > cam.near_plane)) return;
+    const float limx = mul_rn(1.3f, div_rn(mul_rn(0.5f, (float)cam.W), cam.fx));
+    const float limy = mul_rn(1.3f, div_rn(mul_rn(0.5f, (float)cam.H), cam.fy));
+    const float u0 = div_rn(P.t[0], tz), v0 = div_rn(P.t[1], tz);
+    P.u = fminf(limx, fmaxf(-limx, u0));
+    P.v = fminf(limy, fmaxf(-limy, v0));
+    P.clampx = P.u != u0;
+    P.clampy = P.v != v0;
+    const float tx = mul_rn(P.u, tz), ty = mul_rn(P.v, tz);
+    const float z2 = mul_rn(tz, tz);
+    P.J00 = div_rn(cam.fx, tz);
+    P.J02 = -div_rn(mul_rn(cam.fx, tx), z2);
+    P.J11 = div_rn(cam.fy, tz);
+    P.J12 = -div_rn(mul_rn(cam.fy, ty), z2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        P.T[0][c] = add_rn(mul_rn(P.J00, V[c]), mul_rn(P.J02, V[8 + c]));
+        P.T[1][c] = add_rn(mul_rn(P.J11, V[4 + c]), mul_rn(P.J12, V[8 + c]));
+    }
+    float U[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float acc = mul_rn(P.T[r][0], G.Sig[0][c]);
+            acc = add_rn(acc, mul_rn(P.T[r][1], G.Sig[1][c]));
+            acc = add_rn(acc, mul_rn(P.T[r][2], G.Sig[2][c]));
+            U[r][c] = acc;
+        }
+    float s00 = mul_rn(U[0][0], P.T[0][0]);
+    s00 = add_rn(s00, mul_rn(U[0][1], P.T[0][1]));
+    s00 = add_rn(s00, mul_rn(U[0][2], P.T[0][2]));
+    float s01 = mul_rn(U[0][0], P.T[1][0]);
+    s01 = add_rn(s01, mul_rn(U[0][1], P.T[1][1]));
+    s01 = add_rn(s01, mul_rn(U[0][2], P.T[1][2]));
+    float s11 = mul_rn(U[1][0], P.T[1][0]);
+    s11 = add_rn(s11, mul_rn(U[1][1], P.T[1][1]));
+    s11 = add_rn(s11, mul_rn(U[1][2], P.T[1][2]));
+    P.a = add_rn(s00, 0.3f);
+    P.b = s01;
+    P.c = add_rn(s11, 0.3f);
+    const float det = sub_rn(mul_rn(P.a, P.c), mul_rn(P.b, P.b));
+    if (!(det > 0.0f)) return;
+    P.A = div_rn(P.c, det);
+    P.B = -div_rn(P.b, det);
+    P.C = div_rn(P.a, det);
+    const float mid = mul_rn(0.5f, add_rn(P.a, P.c));
+    const float disc = sub_rn(mul_rn(mid, mid), det);
+    const float l1 = add_rn(mid, sqrt_rn(fmaxf(0.1f, disc)));
+    const float rad = ceilf(mul_rn(3.0f, sqrt_rn(l1)));
+    const float px = add_rn(mul_rn(cam.fx, div_rn(P.t[0], tz)), cam.cx);
+    const float py = add_rn(mul_rn(cam.fy, div_rn(P.t[1], tz)), cam.cy);
+    if (rad != rad || px != px || py != py) return;
+    const float fx0 = floorf(div_rn(sub_rn(px, rad), (float)tile_w));
+    const float fx1 = floorf(div_rn(add_rn(px, rad), (float)tile_w));
+    const float fy0 = floorf(div_rn(sub_rn(py, rad), (float)tile_h));
+    const float fy1 = floorf(div_rn(add_rn(py, rad), (float)tile_h));
+    const float x0 = fmaxf(fx0, 0.0f), x1 = fminf(fx1, (float)(cam.tiles_x - 1));
+    const float y0 = fmaxf(fy0, 0.0f), y1 = fminf(fy1, (float)(cam.tiles_y - 1));
+    P.px = px;
+    P.py = py;
+    P.radius = rad;
+    if (!(x0 <= x1 && y0 <= y1)) return;
+    P.x0 = (int)x0;
+    P.x1 = (int)x1;
+    P.y0 = (int)y0;
+    P.y1 = (int)y1;
+    P.visible = true;
+}
+
+__device__ __forceinline__ void view_direction(const View& cam, const float X[3], float d[3],
+                                               float& len) {
+    const float dx = X[0] - cam.campos[0], dy = X[1] - cam.campos[1], dz = X[2] - cam.campos[2];
+    len = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float inv = 1.0f / len;
+    d[0] = dx * inv;
+    d[1] = dy * inv;
+    d[2] = dz * inv;
+}
+
+template <int L, int K, bool FIXED>
+__global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, const ViewTable vt,
+                                                         float4* __restrict__ rec0,
+                                                         float4* __restrict__ rec1,
+                                                         float4* __restrict__ rec2,
+                                                         uint2* __restrict__ rect,
+                                                         uint32_t* __restrict__ tiles) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int64_t S = g.stride;
+    const float X[3] = {__ldg(g.mean + i), __ldg(g.mean + S + i), __ldg(g.mean + 2 * S + i)};
+    const float opacity = __ldg(g.opacity + i);
+    Geometry G;
+    geometry_exact(g, i, G);
+    ColourParams<L, K, FIXED> cp;
+    cp.load(g, i);
+    for (int v = 0; v < vt.B; ++v) {
+        const View& cam = vt.v[v];
+        const int64_t r = (int64_t)v * g.n + i;
+        Projected P;
+        project_exact(cam, X, G, vt.tile_w, vt.tile_h, P);
+        if (!P.visible) {
+            rect[r] = make_uint2(0u, 0u);
+            tiles[r] = 0u;
+            continue;
+        }
+        float d[3], len;
+        view_direction(cam, X, d, len);
+        float pre[3];
+        cp.eval(d, pre);
+        uint32_t mask = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (pre[c] < 0.0f) {
+                pre[c] = 0.0f;
+                mask |= 1u << c;
+            }
+        rec0[r] = make_float4(P.px, P.py, -0.5f * P.A, -P.B);
+        rec1[r] = make_float4(-0.5f * P.C, opacity, P.t[2], P.radius);
+        rec2[r] = make_float4(pre[0], pre[1], pre[2], __uint_as_float(mask));
+        rect[r] = make_uint2((uint32_t)P.x0 | ((uint32_t)P.y0 << 16),
+                             (uint32_t)P.x1 | ((uint32_t)P.y1 << 16));
+        tiles[r] = (uint32_t)((P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1));
+    }
+}
+
+// ------------------------------------------------------------------------------ backward
+template <int L, int K, bool FIXED>
+__global__ void __launch_bounds__(128) preprocess_backward_kernel(
+    const sgs_gaussians g, const ViewTable vt, const float4* __restrict__ rec0,
+    const float4* __restrict__ rec1, const uint32_t* __restrict__ tiles,
+    const float4* __restrict__ grad2d, int64_t R, sgs_grads out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int64_t S = g.stride;
+    const float X[3] = {__ldg(g.mean + i), __ldg(g.mean + S + i), __ldg(g.mean + 2 * S + i)};
+    Geometry G;
+    geometry_exact(g, i, G);
+    ColourParams<L, K, FIXED> cp;
+    cp.load(g, i);
+    ColourGrads<L, K, FIXED> cg;
+    cg.zero();
+    float gX[3] = {0.0f, 0.0f, 0.0f};
+    float gSig[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gSig[r][c] = 0.0f;
+    float gop = 0.0f;
+    for (int v = 0; v < vt.B; ++v) {
+        const int64_t r = (int64_t)v * g.n + i;
+        if (tiles[r] == 0u) continue;
+        const float4 g0 = grad2d[r], g1 = grad2d[R + r], g2 = grad2d[2 * R + r];
+        const View& cam = vt.v[v];
+        Projected P;
+        project_exact(cam, X, G, vt.tile_w, vt.tile_h, P);
+        gop += g1.y;
+        // colour
+        {
+            float d[3], len;
+            view_direction(cam, X, d, len);
+            float pre[3];
+            cp.eval(d, pre);
+            const float grgb[3] = {g1.z, g1.w, g2.x};
+            float gpre[3], gd[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gpre[c] = pre[c] < 0.0f ? 0.0f : grgb[c];
+            cg.accumulate(cp, d, gpre, gd);
+            const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+            const float inv = 1.0f / len;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gX[c] += (gd[c] - d[c] * dot) * inv;
+        }
+        // conic -> Sigma2D:  dS = -Con G Con,  G = [[gA, gB/2], [gB/2, gC]]
+        const float A = P.A, B = P.B, C = P.C;
+        const float gA = g0.z, gB = g0.w, gC = g1.x;
+        const float P00 = A * gA + 0.5f * B * gB, P01 = 0.5f * A * gB + B * gC;
+        const float P10 = B * gA + 0.5f * C * gB, P11 = 0.5f * B * gB + C * gC;
+        const float G2[2][2] = {{-(P00 * A + P01 * B), -(P00 * B + P01 * C)},
+                                {-(P00 * B + P01 * C), -(P10 * B + P11 * C)}};
+        // Sigma2D = T Sigma T^T:  dSigma += T^T G2 T,  dT = 2 G2 T Sigma
+        float TS[2][3];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                TS[rr][c] = P.T[rr][0] * G.Sig[0][c] + P.T[rr][1] * G.Sig[1][c] + P.T[rr][2] * G.Sig[2][c];
+        float gT[2][3];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gT[rr][c] = 2.0f * (G2[rr][0] * TS[0][c] + G2[rr][1] * TS[1][c]);
+        float GT[2][3];  // G2 T
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) GT[rr][c] = G2[rr][0] * P.T[0][c] + G2[rr][1] * P.T[1][c];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gSig[j][k] += P.T[0][j] * GT[0][k] + P.T[1][j] * GT[1][k];
+        // T = J W
+        const float* V = cam.V;
+        const float gJ00 = gT[0][0] * V[0] + gT[0][1] * V[1] + gT[0][2] * V[2];
+        const float gJ02 = gT[0][0] * V[8] + gT[0][1] * V[9] + gT[0][2] * V[10];
+        const float gJ11 = gT[1][0] * V[4] + gT[1][1] * V[5] + gT[1][2] * V[6];
+        const float gJ12 = gT[1][0] * V[8] + gT[1][1] * V[9] + gT[1][2] * V[10];
+        const float tz = P.t[2], iz = 1.0f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        const float tx = P.u * tz, ty = P.v * tz;
+        float gt[3] = {0.0f, 0.0f, 0.0f};
+        gt[2] += -cam.fx * iz2 * gJ00 - cam.fy * iz2 * gJ11 + 2.0f * cam.fx * tx * iz3 * gJ02 +
+                 2.0f * cam.fy * ty * iz3 * gJ12;
+        const float gtx = -cam.fx * iz2 * gJ02, gty = -cam.fy * iz2 * gJ12;
+        if (P.clampx) gt[2] += gtx * P.u; else gt[0] += gtx;
+        if (P.clampy) gt[2] += gty * P.v; else gt[1] += gty;
+        // screen mean
+        gt[0] += cam.fx * iz * g0.x;
+        gt[2] += -cam.fx * P.t[0] * iz2 * g0.x;
+        gt[1] += cam.fy * iz * g0.y;
+        gt[2] += -cam.fy * P.t[1] * iz2 * g0.y;
+        // t = W X + t_v
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gX[c] += V[c] * gt[0] + V[4 + c] * gt[1] + V[8 + c] * gt[2];
+    }
+    // Sigma = M M^T, M = R diag(s):  dM = 2 dSigma_sym M
+    float gR[3][3], gs[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) acc += (gSig[r][l] + gSig[l][r]) * (G.R[l][c] * G.s[c]);
+            gR[r][c] = acc * G.s[c];
+            gs[c] += acc * G.R[r][c];
+        }
+    const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
+    float gq[4];
+    gq[0] = 2.0f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+    gq[1] = 2.0f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.0f * x * gR[1][1] - w * gR[1][2] +
+                    z * gR[2][0] + w * gR[2][1] - 2.0f * x * gR[2][2]);
+    gq[2] = 2.0f * (-2.0f * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] -
+                    w * gR[2][0] + z * gR[2][1] - 2.0f * y * gR[2][2]);
+    gq[3] = 2.0f * (-2.0f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2.0f * z * gR[1][1] +
+                    y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+    const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    const float iq = 1.0f / G.qnorm;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out.rot[c * S + i] = (gq[c] - G.q[c] * dot) * iq;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        out.mean[c * S + i] = gX[c];
+        out.scale[c * S + i] = gs[c];
+    }
+    out.opacity[i] = gop;
+    cg.store(cp, out, S, i);
+}
+
+template <int L, int K, bool FIXED>
+cudaError_t launch_pre(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                       cudaStream_t s) {
+    const int threads = 128;
+    const int blocks = (int)((g.n + threads - 1) / threads);
+    if (blocks > 0)
+        preprocess_kernel<L, K, FIXED><<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.rec2, p.rect,
+                                                                 p.tiles);
+    return cudaGetLastError();
+}
+
+template <int L, int K, bool FIXED>
+cudaError_t launch_pre_bwd(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                           const float4* grad2d, int64_t R, const sgs_grads& out, cudaStream_t s) {
+    const int threads = 128;
+    const int blocks = (int)((g.n + threads - 1) / threads);
+    if (blocks > 0)
+        preprocess_backward_kernel<L, K, FIXED>
+            <<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.tiles, grad2d, R, out);
+    return cudaGetLastError();
+}
+
+template <int L, int K>
+cudaError_t dispatch_axis(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                          const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
+    if (g.axis_mode == SGS_AXIS_ORTHO_FIXED) {
+        if constexpr (K <= 3) {
+            return fwd ? launch_pre<L, K, true>(g, vt, p, s)
+                       : launch_pre_bwd<L, K, true>(g, vt, p, grad2d, R, *out, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    return fwd ? launch_pre<L, K, false>(g, vt, p, s)
+               : launch_pre_bwd<L, K, false>(g, vt, p, grad2d, R, *out, s);
+}
+
+template <int L>
+cudaError_t dispatch_k(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                       const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
+    switch (g.num_lobes) {
+        case 0: return dispatch_axis<L, 0>(fwd, g, vt, p, grad2d, R, out, s);
+        case 1: return dispatch_axis<L, 1>(fwd, g, vt, p, grad2d, R, out, s);
+        case 2: return dispatch_axis<L, 2>(fwd, g, vt, p, grad2d, R, out, s);
+        case 3: return dispatch_axis<L, 3>(fwd, g, vt, p, grad2d, R, out, s);
+        case 4: return dispatch_axis<L, 4>(fwd, g, vt, p, grad2d, R, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dispatch(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                     const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
+    switch (g.sh_degree) {
+        case 0: return dispatch_k<0>(fwd, g, vt, p, grad2d, R, out, s);
+        case 1: return dispatch_k<1>(fwd, g, vt, p, grad2d, R, out, s);
+        case 2: return dispatch_k<2>(fwd, g, vt, p, grad2d, R, out, s);
+        case 3: return dispatch_k<3>(fwd, g, vt, p, grad2d, R, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                              cudaStream_t s) {
+    return dispatch(true, g, vt, p, nullptr, 0, nullptr, s);
+}
+
+cudaError_t launch_preprocess_backward(const sgs_gaussians& g, const ViewTable& vt,
+                                       const RecordPtrs& p, const float4* grad2d, int64_t R,
+                                       const sgs_grads& out, cudaStream_t s) {
+    return dispatch(false, g, vt, p, grad2d, R, &out, s);
+}
+
+}  // namespace sgs

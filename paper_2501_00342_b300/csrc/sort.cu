@@ -1,0 +1,330 @@
+// Stage (c): stable LSD radix sort of (uint64 key, uint32 value) pairs, onesweep style.
+//
+//   1. one read of all keys builds the digit histograms of every pass at once;
+//   2. an exclusive scan per pass turns them into global bucket offsets;
+//   3. per pass, one kernel: each CTA takes the next tile of kSortTile keys (dynamic tile
+//      id), ranks its keys by digit with warp match-any (stable: input order within
+//      the tile), publishes its per-digit counts and resolves its global per-digit
+//      offsets by decoupled look-back over the preceding tiles, then scatters through
+//      shared memory so that each digit's run leaves the CTA as contiguous stores.
+// Look-back words are 64 bits: an 8-bit tag (2p+1 aggregate, 2p+2 inclusive for pass p)
+// and a 56-bit count, so one table serves all passes of a sort after a single clear.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgs {
+namespace {
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+constexpr unsigned long long kCountMask = (1ull << 56) - 1;
+
+template <int RB>
+__global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long* __restrict__ keys,
+                                                        const uint32_t* m_ptr, int passes,
+                                                        uint32_t* __restrict__ hist) {
+    constexpr int RADIX = 1 << RB;
+    __shared__ uint32_t h[kMaxSortPasses * RADIX];
+    for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) h[j] = 0;
+    __syncthreads();
+    const uint32_t m = *m_ptr;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < m; base += stride) {
+        const uint32_t idx = base + threadIdx.x;
+        const bool valid = idx < m;
+        const unsigned long long k = valid ? keys[idx] : 0ull;
+        const uint32_t active = __ballot_sync(kFullMask, valid);
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> (p * RB)) & (RADIX - 1) : RADIX;
+            const uint32_t peers = __match_any_sync(kFullMask, d) & active;
+            if (valid && (threadIdx.x & 31) == 31 - __clz(peers))
+                atomicAdd(&h[p * RADIX + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x)
+        if (h[j]) atomicAdd(&hist[j], h[j]);
+}
+
+// One CTA per pass: exclusive scan over the RADIX buckets.
+template <int RB>
+__global__ void histogram_scan_kernel(const uint32_t* __restrict__ hist, uint32_t* __restrict__ goff) {
+    constexpr int RADIX = 1 << RB;
+    __shared__ uint32_t s[RADIX];
+    const int p = blockIdx.x;
+    const int d = threadIdx.x;
+    if (d < RADIX) s[d] = hist[p * RADIX + d];
+    __syncthreads();
+    if (d == 0) {
+        uint32_t acc = 0;
+        for (int j = 0; j < RADIX; ++j) {
+            const uint32_t c = s[j];
+            s[j] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    if (d < RADIX) goff[p * RADIX + d] = s[d];
+}
+
+template <int RB>
+struct OnesweepSmem {
+    static constexpr int RADIX = 1 << RB;
+    static constexpr int WARPS = kSortThreads / 32;
+    unsigned long long keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t warp_hist[WARPS][RADIX + 1];  // +1: sentinel bucket of the ragged tail
+    uint32_t digit_start[RADIX];
+    uint32_t gbase[RADIX];
+    uint32_t wsum[WARPS];
+    uint32_t tile;
+};
+
+template <int RB>
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
+    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
+    unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* m_ptr,
+    const uint32_t* __restrict__ goff, unsigned long long* lookback, uint32_t* counter, int shift,
+    int pass, DeviceStatus* st) {
+    constexpr int RADIX = 1 << RB;
+    constexpr int WARPS = kSortThreads / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem<RB>& sm = *reinterpret_cast<OnesweepSmem<RB>*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sm.tile = atomicAdd(counter, 1u);
+    for (int j = threadIdx.x; j < WARPS * (RADIX + 1); j += kSortThreads)
+        (&sm.warp_hist[0][0])[j] = 0;
+    __syncthreads();
+    const uint32_t m = *m_ptr;
+    const uint32_t tile = sm.tile;
+    const uint64_t tile_start = (uint64_t)tile * kSortTile;
+    if (tile_start >= m) return;  // whole CTA: nothing in this tile
+    const uint32_t count = (uint32_t)(m - tile_start < (uint64_t)kSortTile ? m - tile_start : kSortTile);
+
+    // load warp-striped: item k of lane l of warp w is element w*32*ITEMS + k*32 + l
+    unsigned long long key[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t rank[kSortItems];
+    uint32_t dig[kSortItems];
+    const uint32_t wbase = warp * 32 * kSortItems;
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const uint32_t e = wbase + k * 32 + lane;
+        if (e < count) {
+            key[k] = kin[tile_start + e];
+            val[k] = vin[tile_start + e];
+            dig[k] = (uint32_t)(key[k] >> shift) & (RADIX - 1);
+        } else {
+            key[k] = 0;
+            val[k] = 0;
+            dig[k] = RADIX;
+        }
+    }
+    // stable warp-level ranking
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const uint32_t peers = __match_any_sync(kFullMask, dig[k]);
+        const int leader = 31 - __clz(peers);
+        uint32_t prior = 0;
+        if (lane == leader) {
+            prior = sm.warp_hist[warp][dig[k]];
+            sm.warp_hist[warp][dig[k]] = prior + __popc(peers);
+        }
+        prior = __shfl_sync(kFullMask, prior, leader);
+        rank[k] = prior + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps and the tile total
+    uint32_t total = 0;
+    if (threadIdx.x < RADIX) {
+        const int d = threadIdx.x;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = sm.warp_hist[w][d];
+            sm.warp_hist[w][d] = acc;
+            acc += c;
+        }
+        total = acc;
+    }
+    // exclusive scan of the digit totals over the CTA -> CTA-local digit start
+    {
+        uint32_t x = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm.wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < WARPS ? sm.wsum[lane] : 0u;
+            uint32_t inc = w;
+#pragma unroll
+            for (int o = 1; o < WARPS; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFullMask, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane < WARPS) sm.wsum[lane] = inc - w;
+        }
+        __syncthreads();
+        if (threadIdx.x < RADIX) sm.digit_start[threadIdx.x] = x - total + sm.wsum[warp];
+    }
+    // publish this tile's per-digit counts, then look back for the global prefix
+    if (threadIdx.x < RADIX) {
+        const int d = threadIdx.x;
+        unsigned long long* row = lookback + (size_t)tile * RADIX;
+        const unsigned long long tag_agg = (unsigned long long)(2 * pass + 1) << 56;
+        const unsigned long long tag_inc = (unsigned long long)(2 * pass + 2) << 56;
+        unsigned long long prefix = goff[d];
+        if (tile == 0) {
+            st_relaxed(row + d, tag_inc | (prefix + total));
+        } else {
+            st_relaxed(row + d, tag_agg | total);
+            int64_t j = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            unsigned long long acc = 0;
+            while (j >= 0) {
+                const unsigned long long e = ld_relaxed(lookback + (size_t)j * RADIX + d);
+                const unsigned long long tag = e & ~kCountMask;
+                if (tag == tag_inc) {
+                    acc += e & kCountMask;
+                    break;
+                } else if (tag == tag_agg) {
+                    acc += e & kCountMask;
+                    --j;
+                } else if (++spins > kSpinLimit) {
+                    set_status(st, SGS_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            prefix = acc;  // the inclusive prefix of a tile includes goff[d]
+            st_relaxed(row + d, tag_inc | (prefix + total));
+        }
+        sm.gbase[d] = (uint32_t)prefix;
+    }
+    __syncthreads();
+    // place keys in CTA-local sorted order
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        if (dig[k] < RADIX) {
+            const uint32_t pos = sm.digit_start[dig[k]] + sm.warp_hist[warp][dig[k]] + rank[k];
+            sm.keys[pos] = key[k];
+            sm.vals[pos] = val[k];
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
+        const unsigned long long kk = sm.keys[j];
+        const uint32_t d = (uint32_t)(kk >> shift) & (RADIX - 1);
+        const uint32_t dest = sm.gbase[d] + (j - sm.digit_start[d]);
+        if (dest < m) {
+            kout[dest] = kk;
+            vout[dest] = sm.vals[j];
+        }
+    }
+}
+
+__global__ void copy_pairs_kernel(const unsigned long long* __restrict__ ks, const uint32_t* __restrict__ vs,
+                                  unsigned long long* __restrict__ kd, uint32_t* __restrict__ vd, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        kd[j] = ks[j];
+        vd[j] = vs[j];
+    }
+}
+
+__global__ void sort_init_kernel(DeviceStatus* st, uint32_t m) {
+    st->status = 0;
+    st->m_clamped = m;
+    st->m = m;
+    for (int j = 0; j < 16; ++j) st->tile_counter[j] = 0;
+}
+
+template <int RB>
+cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
+                      const uint32_t* m_ptr, int64_t capacity, int key_bits, uint32_t* hist,
+                      uint32_t* goff, uint32_t* counters, unsigned long long* lookback,
+                      DeviceStatus* st, cudaStream_t s) {
+    constexpr int RADIX = 1 << RB;
+    const int passes = (key_bits + RB - 1) / RB;
+    cudaError_t e;
+    if ((e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s)) != cudaSuccess) return e;
+    if ((e = launch_fill_u32(counters, 0u, kMaxSortPasses, s)) != cudaSuccess) return e;
+    const size_t tiles = (size_t)((capacity + kSortTile - 1) / kSortTile);
+    if ((e = launch_fill_u32(reinterpret_cast<uint32_t*>(lookback), 0u, tiles * RADIX * 2, s)) != cudaSuccess)
+        return e;
+    if (capacity == 0 || tiles == 0) return cudaSuccess;
+    {
+        const int64_t want = (capacity + 255) / 256;
+        const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
+        histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, hist);
+        histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : RADIX, 0, s>>>(hist, goff);
+    }
+    const size_t smem = sizeof(OnesweepSmem<RB>);
+    if ((e = cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    for (int p = 0; p < passes; ++p) {
+        const unsigned long long* kin = (p & 1) ? k1 : k0;
+        const uint32_t* vin = (p & 1) ? v1 : v0;
+        unsigned long long* kout = (p & 1) ? k0 : k1;
+        uint32_t* vout = (p & 1) ? v0 : v1;
+        onesweep_kernel<RB><<<(unsigned)tiles, kSortThreads, smem, s>>>(
+            kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, p * RB, p, st);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int sort_passes(int key_bits, int digit_bits) { return (key_bits + digit_bits - 1) / digit_bits; }
+
+size_t sort_lookback_entries(int64_t capacity, int digit_bits) {
+    return (size_t)((capacity + kSortTile - 1) / kSortTile) * ((size_t)1 << digit_bits);
+}
+
+cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
+                        const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
+                        uint32_t* hist, uint32_t* goff, uint32_t* counters,
+                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s) {
+    switch (digit_bits) {
+        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
+        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
+        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
+        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
+        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
+                              uint32_t* vd, int64_t m, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    const int64_t want = (m + 255) / 256;
+    copy_pairs_kernel<<<(int)(want < 148 * 16 ? want : 148 * 16), 256, 0, s>>>(ks, vs, kd, vd, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_init(DeviceStatus* st, uint32_t m, cudaStream_t s) {
+    sort_init_kernel<<<1, 1, 0, s>>>(st, m);
+    return cudaGetLastError();
+}
+
+}  // namespace sgs

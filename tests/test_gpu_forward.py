@@ -1,0 +1,222 @@
+"""GPU parity of the forward path against the oracle: bit-exact records, keys, sort order
+and tile ranges against the FP32 mirror; images within 1e-4 of the FP64 brute force;
+invariances (tile size, batching, permutation) and edge cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2501_00342_b300 import inputs as I
+from paper_2501_00342_b300.render import GaussianModel, Rasterizer, RenderSettings
+from tests.helpers import axis_camera, make_scene
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4      # max abs per RGB channel
+AMBIGUOUS = 1e-5    # relative margin of an FP64 decision below which a pixel is excluded
+
+
+def _run(scene, cams, settings=RenderSettings(), capacity=None):
+    model = GaussianModel.from_scene(scene)
+    rast = Rasterizer(model, cams, settings, capacity)
+    out_T = torch.empty(rast.num_pixels, device="cuda")
+    img = rast.forward(model, out_T=out_T)
+    torch.cuda.synchronize()
+    assert rast.device_status() == 0
+    return rast, model, img, out_T
+
+
+def _records(rast, R):
+    rec0 = rast.region("REC0", torch.float32)[:4 * R].view(R, 4).cpu().numpy()
+    rec1 = rast.region("REC1", torch.float32)[:4 * R].view(R, 4).cpu().numpy()
+    rec2 = rast.region("REC2", torch.float32)[:4 * R].view(R, 4).cpu().numpy()
+    rect = rast.region("RECT", torch.int32)[:2 * R].view(R, 2).cpu().numpy().view(np.uint32)
+    tiles = rast.region("TILES", torch.int32)[:R].cpu().numpy().view(np.uint32)
+    return rec0, rec1, rec2, rect, tiles
+
+
+def _check_records(scene, cams, rast, tile_w=16, tile_h=16):
+    R = scene.n * len(cams)
+    rec0, rec1, rec2, rect, tiles = _records(rast, R)
+    m = O.mirror_preprocess(scene, cams, tile_w, tile_h)
+    vis = m["visible"]
+    assert ((tiles > 0) == vis).all()
+    assert (tiles[vis] == m["tiles_touched"][vis]).all()
+    assert (rec1[vis, 2].view(np.uint32) == m["depth_bits"][vis]).all()
+    assert (rec0[vis, 0] == m["mean2d"][vis, 0]).all() and (rec0[vis, 1] == m["mean2d"][vis, 1]).all()
+    assert (-2.0 * rec0[vis, 2] == m["conic"][vis, 0]).all()
+    assert (-rec0[vis, 3] == m["conic"][vis, 1]).all()
+    assert (-2.0 * rec1[vis, 0] == m["conic"][vis, 2]).all()
+    assert (rec1[vis, 3] == m["radius"][vis]).all()
+    r = m["rect"][vis].astype(np.uint32)
+    assert (rect[vis, 0] == (r[:, 0] | (r[:, 1] << 16))).all()
+    assert (rect[vis, 1] == (r[:, 2] | (r[:, 3] << 16))).all()
+    # colour against the FP64 oracle
+    p64 = O.preprocess64(scene, cams)
+    assert np.abs(rec2[vis, :3] - p64["rgb"][vis]).max() < 2e-5
+    assert (rec1[vis, 1] == np.asarray(scene.opacity[:scene.n], np.float32)[np.nonzero(vis)[0] % scene.n]).all()
+    return vis.sum()
+
+
+def _check_bins(scene, cams, rast, tile_w=16, tile_h=16):
+    b = O.mirror_bin(scene, cams, tile_w, tile_h)
+    M = len(b["keys"])
+    assert rast.num_instances == M
+    keys = rast.region("KEYS", torch.int64)[:M].cpu().numpy().view(np.uint64)
+    vals = rast.region("VALS", torch.int32)[:M].cpu().numpy().view(np.uint32)
+    nt = O.num_tiles(cams, tile_w, tile_h)
+    ranges = rast.region("RANGES", torch.int32)[:2 * nt].view(nt, 2).cpu().numpy().view(np.uint32)
+    assert (keys == b["keys"]).all()
+    assert (vals == b["vals"]).all()
+    assert (ranges == b["ranges"]).all()
+    return M
+
+
+def _check_image(scene, cams, img, view=0, bg=(0.0, 0.0, 0.0), rast=None, out_T=None):
+    ref = O.render_image(scene, cams, view=view, bg=bg)
+    c = cams[view]
+    if rast is not None:
+        got = rast.images(img)[view].cpu().numpy()
+    else:
+        got = img.cpu().numpy().reshape(3, c.height, c.width)
+    amb = ref["margin"][..., 0] < AMBIGUOUS
+    err = np.abs(got - ref["rgb"]).max(0)
+    assert err[~amb].max() <= IMG_TOL, (err[~amb].max(), np.unravel_index(np.argmax(np.where(amb, 0, err)), err.shape))
+    assert amb.mean() < 2e-3
+    if out_T is not None and rast is not None:
+        b = rast.pixel_base[view]
+        T = out_T[b:b + c.height * c.width].view(c.height, c.width).cpu().numpy()
+        assert np.abs(T - ref["T"])[~amb].max() <= IMG_TOL
+    return err[~amb].max(), int(amb.sum())
+
+
+def test_config0_records_bins_and_image():
+    sc, cams = I.workload(0)
+    rast, model, img, out_T = _run(sc, cams)
+    assert _check_records(sc, cams, rast) == sc.n
+    _check_bins(sc, cams, rast)
+    _check_image(sc, cams, img, rast=rast, out_T=out_T)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 8), (8, 16), (32, 16), (16, 32)])
+def test_tile_size_bins_exact_and_image_unchanged(tile):
+    sc, cams = I.workload(0)
+    st = RenderSettings(tile_w=tile[0], tile_h=tile[1])
+    rast, model, img, _ = _run(sc, cams, st)
+    _check_records(sc, cams, rast, *tile)
+    _check_bins(sc, cams, rast, *tile)
+    _, _, ref_img, _ = _run(sc, cams)
+    assert torch.equal(img, ref_img)  # same contributors in the same order: bit-identical
+
+
+@pytest.mark.parametrize("batch", [32, 64, 128, 512, 1024])
+def test_batch_depth_does_not_change_image(batch):
+    sc, cams = I.workload(0)
+    _, _, img, _ = _run(sc, cams, RenderSettings(batch_depth=batch))
+    _, _, ref_img, _ = _run(sc, cams)
+    assert torch.equal(img, ref_img)
+
+
+@pytest.mark.parametrize("digit", [4, 5, 6, 7])
+def test_digit_width_gives_identical_sort(digit):
+    sc, cams = I.workload(0)
+    rast, _, img, _ = _run(sc, cams, RenderSettings(digit_bits=digit))
+    _check_bins(sc, cams, rast)
+
+
+def test_batched_views_equal_single_views():
+    sc = I.cluster_scene(20000, 1, 3, config=1)
+    cams = I.orbit_cameras(4, [320, 200, 256, 160], [180, 120, 256, 96], 50.0)
+    rast, _, img, _ = _run(sc, cams)
+    _check_records(sc, cams, rast)
+    _check_bins(sc, cams, rast)
+    views = rast.images(img)
+    for v, c in enumerate(cams):
+        _, _, one, _ = _run(sc, [c])
+        assert torch.equal(views[v].reshape(-1), one), v
+
+
+def test_multi_view_images_against_oracle():
+    sc = I.cluster_scene(6000, 1, 3, config=1)
+    cams = I.orbit_cameras(3, [96, 64, 80], [64, 80, 48], 50.0)
+    rast, _, img, out_T = _run(sc, cams)
+    for v in range(3):
+        _check_image(sc, cams, img, view=v, rast=rast, out_T=out_T)
+
+
+def test_background_and_world_axes_and_sh3():
+    for L, K, mode in [(3, 0, I.AXIS_FREE), (0, 3, I.AXIS_ORTHO_FIXED), (2, 4, I.AXIS_FREE), (1, 1, I.AXIS_ORTHO_FIXED)]:
+        sc = I.uniform_cube_scene(1500, L, K, mode, config=0, stream=L * 10 + K)
+        cams = [I.look_at((0.3, 0.5, 3.8), (0, 0, 0), 72, 56, 60.0)]
+        bg = (0.2, 0.5, 0.9)
+        rast, _, img, out_T = _run(sc, cams, RenderSettings(bg=bg))
+        _check_records(sc, cams, rast)
+        _check_image(sc, cams, img, bg=bg, rast=rast, out_T=out_T)
+
+
+def test_permutation_invariance():
+    sc, cams = I.workload(0)
+    perm = np.random.default_rng(5).permutation(sc.n)
+    _, _, a, _ = _run(sc, cams)
+    _, _, b, _ = _run(sc.subset(perm), cams)
+    assert (a - b).abs().max().item() < 1e-6
+
+
+def test_ragged_image_sizes():
+    sc = I.uniform_cube_scene(3000, 1, 2, config=0, stream=3)
+    for w, h in [(1, 1), (17, 5), (33, 47), (129, 65)]:
+        cams = [I.look_at((0.0, 0.2, 3.5), (0, 0, 0), w, h, 60.0)]
+        rast, _, img, out_T = _run(sc, cams)
+        _check_bins(sc, cams, rast)
+        _check_image(sc, cams, img, rast=rast, out_T=out_T)
+
+
+def test_empty_and_all_culled():
+    cams = [axis_camera(40, 24)]
+    # every Gaussian behind the camera
+    sc = make_scene([[0, 0, 5.0], [0.1, 0, 6.0]], [[0.1] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.5, 0.5],
+                    [[[1, 1, 1]], [[1, 1, 1]]])
+    bg = (0.1, 0.2, 0.3)
+    rast, _, img, out_T = _run(sc, cams, RenderSettings(bg=bg))
+    assert rast.num_instances == 0
+    exp = torch.tensor(bg, device="cuda").repeat_interleave(40 * 24)
+    assert torch.equal(img, exp) and torch.equal(out_T, torch.ones_like(out_T))
+    # no Gaussians at all
+    sc0 = I.uniform_cube_scene(0, 0, 0, config=0)
+    rast, _, img, _ = _run(sc0, cams, RenderSettings(bg=bg))
+    assert torch.equal(img, exp)
+
+
+def test_capacity_overflow_is_reported_not_written():
+    sc, cams = I.workload(0)
+    model = GaussianModel.from_scene(sc)
+    rast = Rasterizer(model, cams, RenderSettings(), capacity=1000)
+    guard = rast.region("KEYS_IN", torch.int64)
+    out = torch.empty(3 * rast.num_pixels, device="cuda")
+    rast.forward(model, out_rgb=out, sync=False)
+    torch.cuda.synchronize()
+    assert rast.device_status() & 2  # SGS_ERR_CAPACITY
+    # the synchronising path grows the workspace and succeeds
+    rast.forward(model, out_rgb=out, sync=True)
+    assert rast.num_instances == len(O.mirror_bin(sc, cams)["keys"]) and rast.capacity >= rast.num_instances
+    _check_image(sc, cams, out, rast=rast)
+
+
+def test_graph_capture_replay_matches_eager():
+    sc, cams = I.workload(0)
+    model = GaussianModel.from_scene(sc)
+    rast = Rasterizer(model, cams, RenderSettings())
+    eager = rast.forward(model).clone()
+    out = torch.empty_like(eager)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rast.forward(model, out_rgb=out, sync=False)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rast.forward(model, out_rgb=out, sync=False)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
