@@ -1,0 +1,469 @@
+"""Benchmark of the SG-Splatting rasterizer on one node.
+
+Headline (printed as ONE JSON line by rank 0): forward+backward views/s of the batched
+path -- 3 M clustered Gaussians (SH degree 1 + 4 SG lobes), 16 cameras of mixed
+resolution {640x360, 1280x720, 1600x900, 1920x1080} rendered, L1-compared with seeded
+U(0,1) targets and differentiated in one batched pass per step.  Beside it: the same
+views as 16 sequential plain (one view per launch) passes, render FPS of the 1 M-Gaussian
+1280x720 scene with SH-1 + 3 SG lobes and with SH degree 3 (48 coefficients), per-kernel
+times from CUDA events inside the timed region, the roofline of the dominant kernel, an
+end-to-end number through host buffers, and the CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank renders its own batch (weak scaling, no collective on the data
+path); times are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_00342_b300 import inputs as I  # noqa: E402
+
+METRIC = "fwd+bwd views/sec (batched launch, 16 mixed-resolution views)"
+UNIT = "views/s"
+WORKLOAD = ("3M clustered Gaussians, SH-1 + 4 SG lobes (free axes), 16 orbit views at mixed "
+            "{640x360,1280x720,1600x900,1920x1080}, L1 vs U(0,1) targets, forward + backward")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2032.0)), "measured"
+    except Exception:
+        return 6400.0, 2032.0, "fallback"
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 3 + k and r[3 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_00342_b300 import binding as B
+    from paper_2501_00342_b300.render import GaussianModel, Rasterizer, RenderSettings, l1_loss
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    settings = RenderSettings(tile_w=args.tile[0], tile_h=args.tile[1], batch_depth=args.batch_depth,
+                              digit_bits=args.digit_bits)
+    if args.workload == "single":  # small profiling case: 1 M Gaussians, one 1280x720 view
+        scene, cams = I.workload(1, sh_degree=1, num_lobes=4)
+        cams = cams[:1]
+    else:
+        scene, cams = I.workload(3)
+    n, nv = scene.n, len(cams)
+    model = GaussianModel.from_scene(scene)
+    targets = I.target_images(cams, config=3)
+    target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets])).cuda()
+    rast = Rasterizer(model, cams, settings)
+    img = torch.empty(3 * rast.num_pixels, device="cuda")
+    rast.forward(model, out_rgb=img, sync=True)  # sizes the instance capacity
+    M = rast.num_instances
+    rast = Rasterizer(model, cams, settings, capacity=int(M * 1.02) + 4096)
+    grads = model.empty_grads()
+
+    def step(sync=False):
+        rast.forward(model, out_rgb=img, sync=sync)
+        loss, dimg = l1_loss(img, target)
+        rast.backward(model, dimg, grads=grads)
+        return loss
+
+    step(sync=True)
+    assert rast.num_instances == M and rast.device_status() == 0
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # per-kernel probe events, one set per timed step
+    names = B.EVENTS
+    ev_sets, handle_sets = [], []
+    for _ in range(args.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in names]
+        for e in evs:
+            e.record(stream)
+        torch.cuda.synchronize()
+        ev_sets.append(evs)
+        handle_sets.append((C_void_p_array(len(names)))(*[e.cuda_event for e in evs]))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            B.set_events(rast.plan, handle_sets[k])
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    B.set_events(rast.plan, None)
+    barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps)
+    value = world * nv / (ms / 1e3)
+
+    def span(a, b):
+        ia, ib = names.index(a), names.index(b)
+        return float(np.mean([ev[ia].elapsed_time(ev[ib]) for ev in ev_sets]))
+
+    P = rast.plan.sort_passes
+    stages = {
+        "preprocess": span("PRE_BEGIN", "PRE_END"),
+        "scan": span("BIN_BEGIN", "SCAN_END"),
+        "duplicate": span("SCAN_END", "DUP_END"),
+        "sort_histogram": span("DUP_END", "HIST_END"),
+        "sort_onesweep_all_passes": span("HIST_END", "SORT_END"),
+        "ranges": span("SORT_END", "RANGES_END"),
+        "blend": span("BLEND_BEGIN", "BLEND_END"),
+        "loss": span("BLEND_END", "BWD_BEGIN"),
+        "backward_zero": span("BWD_BEGIN", "BWD_ZERO_END"),
+        "backward_blend": span("BWD_ZERO_END", "BWD_BLEND_END"),
+        "backward_preprocess": span("BWD_BLEND_END", "BWD_PRE_END"),
+    }
+
+    # algorithmic work of each kernel
+    tiles = rast.region("TILES", torch.int32)[:n * nv]
+    visible = int((tiles != 0).sum().item())
+    counts = rast.region("PIX_COUNT", torch.int32)[:2 * rast.num_pixels].view(-1, 2).to(torch.int64)
+    e_eval, e_contrib = int(counts[:, 0].sum().item()), int(counts[:, 1].sum().item())
+    p_bytes = 4 * scene.floats_per_gaussian()
+    hbm, sm_max, peak_kind = _peaks()
+    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12  # Tops/s: one FP32 op per lane per clock
+    kernels = {
+        "preprocess_kernel": dict(ms=stages["preprocess"], launches=1, bound="hbm",
+                                  work=n * p_bytes + visible * 48 + n * nv * 12),
+        "onesweep_kernel": dict(ms=stages["sort_onesweep_all_passes"] / P, launches=P, bound="hbm",
+                                work=24 * M),
+        "blend_kernel": dict(ms=stages["blend"], launches=1, bound="alu",
+                             work=8 * e_eval + 11 * e_contrib),
+        "blend_backward_kernel": dict(ms=stages["backward_blend"], launches=1, bound="alu",
+                                      work=None),
+        "preprocess_backward_kernel": dict(ms=stages["backward_preprocess"], launches=1, bound="hbm",
+                                           work=2 * n * p_bytes + visible * 48),
+    }
+    dom_name = max(kernels, key=lambda k: kernels[k]["ms"] * kernels[k]["launches"])
+    roofs = {}
+    for name, k in kernels.items():
+        if k["work"] is None:
+            continue
+        if k["bound"] == "hbm":
+            achieved = k["work"] / (k["ms"] / 1e3) / 1e9
+            roofs[name] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                           "frac": round(achieved / hbm, 4), "traffic": None,
+                           "algorithmic_bytes_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
+        else:
+            achieved = k["work"] / (k["ms"] / 1e3) / 1e12
+            roofs[name] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
+                           "unit": "Tops/s (FP32 ops)", "frac": round(achieved / alu_peak, 4), "traffic": None,
+                           "algorithmic_ops_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
+    dominant = dict(roofs.get(dom_name, {}))
+    dominant["kernel"] = dom_name
+    dominant["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs; alu = 148 SMs x 128 lanes x sm_max_mhz)"
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; stands in for Mip-NeRF360/T&T/DB)",
+        "config": {"workload": WORKLOAD if args.workload == "batched" else
+                   "profiling case: 1M clustered Gaussians, SH-1 + 4 SG, one 1280x720 view, fwd+bwd",
+                   "gaussians": n, "views": nv,
+                   "resolutions": [[c.width, c.height] for c in cams], "pixels": int(rast.num_pixels),
+                   "instances": M, "sort_passes": P, "key_bits": int(rast.plan.key_bits),
+                   "tile": list(args.tile), "batch_depth": args.batch_depth, "digit_bits": args.digit_bits,
+                   "l2": f"inputs larger than L2: {n * p_bytes / 1e6:.0f} MB parameters, "
+                         f"{rast.nbytes / 1e9:.2f} GB workspace",
+                   "parallelism": f"view batches per rank x{world}"},
+        "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "blend_evaluations": e_eval, "blend_contributions": e_contrib, "visible_records": visible,
+        "roofline": dominant, "roofline_all": roofs,
+        "gpu_launches": (19 + P) * args.steps,
+        "clocks": clk.summary(),
+    }
+
+    # ---- the same views as 16 plain launches (one view each)
+    if args.extras:
+        plain = []
+        for c in cams:
+            r1 = Rasterizer(model, [c], settings)
+            r1.forward(model, sync=True)
+            r1 = Rasterizer(model, [c], settings, capacity=int(r1.num_instances * 1.02) + 4096)
+            i1 = torch.empty(3 * r1.num_pixels, device="cuda")
+            plain.append([r1, i1, None, model.empty_grads()])
+        offs = rast.pixel_base
+        for v, pl in enumerate(plain):  # view v's slice of the packed targets
+            pl[2] = target[3 * offs[v]:3 * offs[v + 1]]
+
+        def plain_step():
+            for r1, i1, tv, g1 in plain:
+                r1.forward(model, out_rgb=i1, sync=False)
+                _, d1 = l1_loss(i1, tv)
+                r1.backward(model, d1, grads=g1)
+
+        for _ in range(max(1, args.warmup)):
+            plain_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            plain_step()
+        b2.record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(a.elapsed_time(b2) / args.steps)
+        out["plain"] = {"ms_per_16_views": round(pms, 4), "views_per_s": round(world * nv / (pms / 1e3), 3),
+                        "batched_over_plain": round(pms / ms, 4)}
+        del plain
+
+        # ---- render FPS, 1 M Gaussians at 1280x720: SG colour vs SH degree 3
+        fps = {}
+        for label, L, K in (("sh1_sg3", 1, 3), ("sh3", 3, 0)):
+            sc1, cams1 = I.workload(1, sh_degree=L, num_lobes=K)
+            m1 = GaussianModel.from_scene(sc1)
+            cams1 = cams1[:8]
+            rs = []
+            for c in cams1:
+                r1 = Rasterizer(m1, [c], settings)
+                r1.forward(m1, sync=True)
+                r1 = Rasterizer(m1, [c], settings, capacity=int(r1.num_instances * 1.02) + 4096)
+                rs.append((r1, torch.empty(3 * r1.num_pixels, device="cuda")))
+            for r1, o1 in rs:
+                r1.forward(m1, out_rgb=o1, sync=False)
+            torch.cuda.synchronize()
+            a.record(stream)
+            reps = max(2, args.steps)
+            for _ in range(reps):
+                for r1, o1 in rs:
+                    r1.forward(m1, out_rgb=o1, sync=False)
+            b2.record(stream)
+            torch.cuda.synchronize()
+            fms = max_over_ranks(a.elapsed_time(b2) / (reps * len(rs)))
+            fps[label] = {"ms_per_frame": round(fms, 4), "fps": round(1e3 / fms, 1),
+                          "floats_per_gaussian": sc1.floats_per_gaussian()}
+            del rs, m1
+        fps["sg_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["sh1_sg3"]["ms_per_frame"], 4)
+        fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
+        out["render_fps"] = fps
+
+    # ---- end to end through the public API: host (pinned) parameters and targets in,
+    # loss out, every step
+    host_planes = {p: (None if t is None else t.cpu().pin_memory()) for p, t in model.planes.items()}
+    host_target = target.cpu().pin_memory()
+    h2d = sum(t.numel() * 4 for t in host_planes.values() if t is not None) + host_target.numel() * 4
+    loss_host = torch.empty(1).pin_memory()
+
+    def e2e_step():
+        for p, t in host_planes.items():
+            if t is not None:
+                model.planes[p].copy_(t, non_blocking=True)
+        target.copy_(host_target, non_blocking=True)
+        loss = step()
+        loss_host.copy_(loss, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b2.record(stream)
+    torch.cuda.synchronize()
+    ems = max_over_ranks(a.elapsed_time(b2) / args.steps)
+    out["e2e"] = {"value": round(world * nv / (ems / 1e3), 3), "unit": UNIT, "ms_per_step": round(ems, 4),
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only); same sample checks parity
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        out["cpu_baseline"], out["oracle_parity"] = cpu_baseline(scene, cams, img, rast, args)
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def C_void_p_array(k):
+    import ctypes
+    return ctypes.c_void_p * k
+
+
+def _oracle_sample(scene, cams, patches=1, views=(0, 1)):
+    rows = []
+    for v in views:
+        p = I.sample_pixels([cams[v]], patches_per_view=patches, patch=16, stream=v)
+        p[:, 0] = v
+        rows.append(p)
+    return np.concatenate(rows)
+
+
+def cpu_baseline(scene, cams, img, rast, args):
+    """The oracle as it stands, timed on this host's cores on a bounded sample of the
+    workload (forward + adjoint of sampled pixels, brute force over all Gaussians)."""
+    import oracle as O
+    threads = O.default_threads()
+    pix = _oracle_sample(scene, cams)
+    t = time.time()
+    ref = O.render_pixels(scene, cams, pix, threads=threads)
+    w = np.random.default_rng(0).normal(size=(len(pix), 3))
+    O.adjoint_pixels(scene, cams, pix, w, threads=threads)
+    secs = time.time() - t
+    avg_pix = sum(c.width * c.height for c in cams) / len(cams)
+    views_per_s = len(pix) / secs / avg_pix
+    base = {"value": views_per_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(pix)} pixels (one 16x16 patch in each of views 0 and 1), FP64 forward + "
+                      f"adjoint, brute force over all {scene.n} Gaussians; {secs:.1f} s; views/s "
+                      f"extrapolated by the mean pixels per view ({avg_pix:.0f})"}
+    # parity of the timed GPU image on the same pixels
+    got = np.empty((len(pix), 3))
+    flat = img.cpu().numpy()
+    for j, (v, x, y) in enumerate(pix):
+        c = cams[v]
+        b = rast.plan.pixel_base[v]
+        hw = c.width * c.height
+        for ch in range(3):
+            got[j, ch] = flat[3 * b + ch * hw + y * c.width + x]
+    ok = ref["margin"][:, 0] >= 1e-5
+    err = float(np.abs(got - ref["rgb"]).max(1)[ok].max()) if ok.any() else None
+    parity = {"pixels": int(len(pix)), "ambiguous": int((~ok).sum()), "max_abs_err": err, "tolerance": 1e-4,
+              "pass": bool(err is not None and err <= 1e-4)}
+    return base, parity
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The oracle as the reference implementation, on the host cores: each step is a
+    bounded sample of the same workload (one 16x16 patch, forward + adjoint)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import oracle as O
+    threads = O.default_threads()
+    scene, cams = I.workload(3)
+    avg_pix = sum(c.width * c.height for c in cams) / len(cams)
+
+    def one(k):
+        pix = I.sample_pixels([cams[k % len(cams)]], patches_per_view=1, patch=16, stream=100 + k)
+        pix[:, 0] = k % len(cams)
+        t = time.time()
+        O.render_pixels(scene, cams, pix, threads=threads)
+        O.adjoint_pixels(scene, cams, pix, np.ones((len(pix), 3)), threads=threads)
+        return len(pix), time.time() - t
+
+    for k in range(args.warmup):
+        one(k)
+    tot_pix = tot_s = 0.0
+    for k in range(args.steps):
+        p, s = one(args.warmup + k)
+        tot_pix += p
+        tot_s += s
+    v = tot_pix / tot_s / avg_pix
+    sample = (f"per step one 16x16 patch of one view, FP64 forward + adjoint, brute force over all "
+              f"{scene.n} Gaussians; views/s extrapolated by mean pixels per view ({avg_pix:.0f})")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--tile", type=int, nargs=2, default=(16, 16))
+    ap.add_argument("--batch-depth", type=int, default=256)
+    ap.add_argument("--digit-bits", type=int, default=8)
+    ap.add_argument("--workload", default="batched", choices=("batched", "single"),
+                    help="single: 1M Gaussians, one 1280x720 view (a small case for profilers)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

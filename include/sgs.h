@@ -126,10 +126,32 @@ typedef struct {
     int32_t key_bits, sort_passes;
     int32_t stage; /* last stage run on the bound workspace: 1 preprocess, 2 bin/sort,
                       3 render; a stage call before its predecessor returns SGS_ERR_INVALID */
+    cudaEvent_t* events; /* optional caller-owned array[SGS_EV_COUNT] (see sgs_set_events) */
     size_t offsets[32]; /* byte offsets of the workspace regions */
     size_t workspace_bytes;
     void* workspace; /* bound by sgs_preprocess() */
 } sgs_plan;
+
+/* Probe points between the kernels of the stage calls.  When a plan carries an event
+ * array, each stage call records events[k] (if non-NULL) on its stream at point k. */
+typedef enum {
+    SGS_EV_PRE_BEGIN = 0, SGS_EV_PRE_END = 1,          /* preprocess kernel */
+    SGS_EV_BIN_BEGIN = 2, SGS_EV_SCAN_END = 3,         /* scan of tiles touched */
+    SGS_EV_DUP_END = 4,                                /* key duplication */
+    SGS_EV_HIST_END = 5,                               /* sort: clears + digit histograms */
+    SGS_EV_SORT_END = 6,                               /* sort: all onesweep passes */
+    SGS_EV_RANGES_END = 7,                             /* clears + tile ranges */
+    SGS_EV_BLEND_BEGIN = 8, SGS_EV_BLEND_END = 9,      /* blend kernel */
+    SGS_EV_BWD_BEGIN = 10, SGS_EV_BWD_ZERO_END = 11,   /* clear of the 2D gradients */
+    SGS_EV_BWD_BLEND_END = 12,                         /* reverse blend */
+    SGS_EV_BWD_PRE_END = 13,                           /* preprocess backward */
+    SGS_EV_COUNT = 14
+} sgs_event_point;
+
+/* Attaches (events != NULL) or detaches (NULL) a caller-owned array of SGS_EV_COUNT
+ * CUDA events (created by the caller, any entry may be NULL) to the plan.  Used to time
+ * single kernels inside a running pipeline; the array must outlive its use. */
+sgs_status sgs_set_events(sgs_plan* plan, cudaEvent_t* events);
 
 /* Fills *plan and *bytes (device workspace size, 256-byte aligned) for n Gaussians seen
  * by B <= SGS_MAX_VIEWS cameras (host array), at most instance_capacity (record, tile)
@@ -190,7 +212,9 @@ typedef enum {
     SGS_REGION_PIX_LAST = 13, /* uint32[num_pixels]: 1 + position of the last contributor
                                  in the tile's list (0: none) */
     SGS_REGION_GRAD2D = 14, /* float4[3][R]: dL/d(px, py, A, B), (C, opacity, r, g), (b) */
-    SGS_REGION_COUNT = 15
+    SGS_REGION_PIX_COUNT = 15, /* uint2[num_pixels]: list entries the pixel evaluated, and
+                                  how many of them it blended */
+    SGS_REGION_COUNT = 16
 } sgs_region;
 sgs_status sgs_region_info(const sgs_plan* plan, int32_t which, size_t* offset, size_t* bytes);
 

@@ -20,13 +20,19 @@ SGS_ERR_TIMEOUT = 4
 SGS_ERR_CUDA = 8
 
 REGION = dict(STATUS=0, REC0=1, REC1=2, REC2=3, RECT=4, TILES=5, OFFSETS=6, KEYS=7, VALS=8,
-              KEYS_IN=9, VALS_IN=10, RANGES=11, PIX_T=12, PIX_LAST=13, GRAD2D=14)
+              KEYS_IN=9, VALS_IN=10, RANGES=11, PIX_T=12, PIX_LAST=13, GRAD2D=14,
+              PIX_COUNT=15)
 
 # every symbol include/sgs.h declares
 EXPORTS = ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
            "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
            "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss", "sgs_status_string",
-           "sgs_abi_sizes")
+           "sgs_abi_sizes", "sgs_set_events")
+
+# probe points of sgs_set_events (sgs_event_point)
+EVENTS = ("PRE_BEGIN", "PRE_END", "BIN_BEGIN", "SCAN_END", "DUP_END", "HIST_END", "SORT_END",
+          "RANGES_END", "BLEND_BEGIN", "BLEND_END", "BWD_BEGIN", "BWD_ZERO_END", "BWD_BLEND_END",
+          "BWD_PRE_END")
 
 
 class Camera(C.Structure):
@@ -60,8 +66,8 @@ class Plan(C.Structure):
                 ("tile_base", C.c_int64 * (MAX_VIEWS + 1)), ("pixel_base", C.c_int64 * (MAX_VIEWS + 1)),
                 ("num_records", C.c_int64), ("num_tiles", C.c_int64), ("num_pixels", C.c_int64),
                 ("instance_capacity", C.c_int64), ("key_bits", C.c_int32), ("sort_passes", C.c_int32),
-                ("stage", C.c_int32), ("offsets", C.c_size_t * 32), ("workspace_bytes", C.c_size_t),
-                ("workspace", C.c_void_p)]
+                ("stage", C.c_int32), ("events", C.c_void_p), ("offsets", C.c_size_t * 32),
+                ("workspace_bytes", C.c_size_t), ("workspace", C.c_void_p)]
 
 
 class SgsError(RuntimeError):
@@ -95,6 +101,8 @@ def lib():
         L.sgs_status_string.argtypes = [C.c_int]
         L.sgs_status_string.restype = C.c_char_p
         L.sgs_abi_sizes.argtypes = [P(C.c_size_t)]
+        L.sgs_set_events.argtypes = [P(Plan), vp]
+        L.sgs_set_events.restype = st
         for f in ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
                   "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
                   "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss"):
@@ -106,6 +114,12 @@ def lib():
             raise RuntimeError(f"sgs ABI mismatch: library {tuple(sizes)} vs binding {want}")
         _lib = L
     return _lib
+
+
+def set_events(plan, handles):
+    """Attaches a ctypes array of cudaEvent_t handles (len(EVENTS), 0 = unused) to the plan,
+    or detaches with None.  The caller keeps the array alive."""
+    check("sgs_set_events", lib().sgs_set_events(C.byref(plan), None if handles is None else C.cast(handles, C.c_void_p)))
 
 
 def status_string(code: int) -> str:

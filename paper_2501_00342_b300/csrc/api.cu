@@ -15,8 +15,8 @@ namespace {
 
 enum Region {
     O_STATUS, O_REC0, O_REC1, O_REC2, O_RECT, O_TILES, O_OFFS, O_K0, O_V0, O_K1, O_V1,
-    O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_SCANLB, O_HIST, O_GOFF, O_SORTLB, O_COUNTERS,
-    O_END
+    O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
+    O_COUNTERS, O_END
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -106,6 +106,11 @@ RecordPtrs records(const sgs_plan* p) {
 
 sgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SGS_OK : SGS_ERR_CUDA; }
 
+cudaError_t probe(const sgs_plan* p, int k, cudaStream_t s) {
+    if (!p->events || !p->events[k]) return cudaSuccess;
+    return cudaEventRecord(p->events[k], s);
+}
+
 #define SGS_TRY(expr)                                  \
     do {                                               \
         cudaError_t _e = (expr);                       \
@@ -192,6 +197,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_RANGES] = 8 * (size_t)tiles;
     sz[O_PIXT] = sz[O_PIXLAST] = 4 * (size_t)pixels;
     sz[O_GRAD2D] = 48 * (size_t)R;
+    sz[O_PIXCOUNT] = 8 * (size_t)pixels;
     sz[O_SCANLB] = 8 * (size_t)((R + kScanTile - 1) / kScanTile + 1);
     sz[O_HIST] = sz[O_GOFF] = 4 * (size_t)kMaxSortPasses * 256;
     sz[O_SORTLB] = 8 * sort_lookback_entries(instance_capacity, settings->digit_bits);
@@ -216,7 +222,9 @@ sgs_status sgs_preprocess(sgs_plan* plan, const sgs_gaussians* g, void* workspac
     DeviceStatus* st = region<DeviceStatus>(plan, O_STATUS);
     SGS_TRY(launch_sort_init(st, 0u, stream));
     const ViewTable vt = view_table(plan);
+    SGS_TRY(probe(plan, SGS_EV_PRE_BEGIN, stream));
     if (plan->n > 0) SGS_TRY(launch_preprocess(*g, vt, records(plan), stream));
+    SGS_TRY(probe(plan, SGS_EV_PRE_END, stream));
     plan->stage = 1;
     return SGS_OK;
 }
@@ -229,22 +237,28 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     const int64_t R = plan->num_records;
     const int64_t cap = plan->instance_capacity;
     unsigned long long* scan_lb = region<unsigned long long>(plan, O_SCANLB);
+    SGS_TRY(probe(plan, SGS_EV_BIN_BEGIN, stream));
     SGS_TRY(launch_fill_u32(st->tile_counter, 0u, 16, stream));
     SGS_TRY(launch_fill_u32(reinterpret_cast<uint32_t*>(scan_lb), 0u,
                             2 * (size_t)((R + kScanTile - 1) / kScanTile + 1), stream));
-    SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));
     SGS_TRY(launch_scan(rp.tiles, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));
+    SGS_TRY(probe(plan, SGS_EV_SCAN_END, stream));
     SGS_TRY(launch_duplicate(vt, rp, region<uint32_t>(plan, O_OFFS), plan->n, R, st, cap,
                              region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0), stream));
+    SGS_TRY(probe(plan, SGS_EV_DUP_END, stream));
+    cudaEvent_t hist_end = plan->events ? plan->events[SGS_EV_HIST_END] : nullptr;
     SGS_TRY(launch_sort(region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
                         region<unsigned long long>(plan, O_K1), region<uint32_t>(plan, O_V1),
                         &st->m_clamped, cap, plan->key_bits, plan->settings.digit_bits,
                         region<uint32_t>(plan, O_HIST), region<uint32_t>(plan, O_GOFF),
                         region<uint32_t>(plan, O_COUNTERS), region<unsigned long long>(plan, O_SORTLB),
-                        st, stream));
+                        st, stream, hist_end));
+    SGS_TRY(probe(plan, SGS_EV_SORT_END, stream));
     const int kreg = (plan->sort_passes & 1) ? O_K1 : O_K0;
+    SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));
     SGS_TRY(launch_ranges(region<unsigned long long>(plan, kreg), st, cap, plan->num_tiles,
                           region<uint2>(plan, O_RANGES), stream));
+    SGS_TRY(probe(plan, SGS_EV_RANGES_END, stream));
     plan->stage = 2;
     if (num_instances) {
         unsigned long long m = 0;
@@ -261,11 +275,13 @@ sgs_status sgs_render(sgs_plan* plan, float* out_rgb, float* out_T, cudaStream_t
     const ViewTable vt = view_table(plan);
     const int vreg = (plan->sort_passes & 1) ? O_V1 : O_V0;
     const sgs_settings& s = plan->settings;
+    SGS_TRY(probe(plan, SGS_EV_BLEND_BEGIN, stream));
     SGS_TRY(launch_blend(vt, region<uint2>(plan, O_RANGES), region<uint32_t>(plan, vreg),
                          plan->num_records, records(plan),
                          s.batch_depth, s.bg[0], s.bg[1], s.bg[2], out_rgb, out_T,
                          region<float>(plan, O_PIXT), region<uint32_t>(plan, O_PIXLAST),
-                         region<DeviceStatus>(plan, O_STATUS), stream));
+                         region<uint2>(plan, O_PIXCOUNT), region<DeviceStatus>(plan, O_STATUS), stream));
+    SGS_TRY(probe(plan, SGS_EV_BLEND_END, stream));
     plan->stage = 3;
     return SGS_OK;
 }
@@ -286,12 +302,22 @@ sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const flo
     float4* grad2d = region<float4>(plan, O_GRAD2D);
     const int vreg = (plan->sort_passes & 1) ? O_V1 : O_V0;
     const sgs_settings& s = plan->settings;
+    SGS_TRY(probe(plan, SGS_EV_BWD_BEGIN, stream));
     SGS_TRY(launch_zero_grad2d(grad2d, rp.tiles, R, stream));
+    SGS_TRY(probe(plan, SGS_EV_BWD_ZERO_END, stream));
     SGS_TRY(launch_blend_backward(vt, region<uint2>(plan, O_RANGES), region<uint32_t>(plan, vreg), rp,
                                   s.batch_depth, s.bg[0], s.bg[1], s.bg[2], region<float>(plan, O_PIXT),
                                   region<uint32_t>(plan, O_PIXLAST), dL_drgb, grad2d, R,
                                   region<DeviceStatus>(plan, O_STATUS), stream));
+    SGS_TRY(probe(plan, SGS_EV_BWD_BLEND_END, stream));
     if (plan->n > 0) SGS_TRY(launch_preprocess_backward(*g, vt, rp, grad2d, R, *out, stream));
+    SGS_TRY(probe(plan, SGS_EV_BWD_PRE_END, stream));
+    return SGS_OK;
+}
+
+sgs_status sgs_set_events(sgs_plan* plan, cudaEvent_t* events) {
+    if (!plan) return SGS_ERR_INVALID;
+    plan->events = events;
     return SGS_OK;
 }
 
@@ -324,6 +350,7 @@ sgs_status sgs_region_info(const sgs_plan* plan, int32_t which, size_t* offset, 
         case SGS_REGION_PIX_T: r = O_PIXT; break;
         case SGS_REGION_PIX_LAST: r = O_PIXLAST; break;
         case SGS_REGION_GRAD2D: r = O_GRAD2D; break;
+        case SGS_REGION_PIX_COUNT: r = O_PIXCOUNT; break;
         default: return SGS_ERR_INVALID;
     }
     *offset = plan->offsets[r];
@@ -363,7 +390,7 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
     unsigned long long* k0 = reinterpret_cast<unsigned long long*>(keys);
     SGS_TRY(launch_sort_init(st, (uint32_t)m, stream));
     SGS_TRY(launch_sort(k0, vals, k1, v1, &st->m_clamped, m, key_bits, digit_bits, hist, goff, counters, lb,
-                        st, stream));
+                        st, stream, nullptr));
     if (sort_passes(key_bits, digit_bits) & 1) SGS_TRY(launch_copy_pairs(k1, v1, k0, vals, m, stream));
     return SGS_OK;
 }

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
                                                      float* __restrict__ out_T,
                                                      float* __restrict__ pix_T,
                                                      uint32_t* __restrict__ pix_last,
+                                                     uint2* __restrict__ pix_count,
                                                      const DeviceStatus* __restrict__ st) {
     extern __shared__ float4 sbuf[];
     float4* s0 = sbuf;
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
     const int n = (int)(range.y - range.x);
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0;
+    uint32_t last = 0, evaluated = 0, contributed = 0;
     bool done = !inside;
     for (int base = 0; base < n; base += batch) {
         if (__syncthreads_count(!done) == 0) break;
@@ -83,7 +84,9 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
             s2[j] = rec2[id];
         }
         __syncthreads();
-        for (int k = 0; !done && k < cnt; ++k) {
+        const bool was_done = done;
+        int k = 0;
+        for (; !done && k < cnt; ++k) {
             const float4 a = s0[k];
             const float4 b = s1[k];
             const float power = support_power(a.z, a.w, b.x, a.x - pxc, a.y - pyc);
@@ -102,7 +105,9 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
             C2 += c.z * w;
             T = Tn;
             last = (uint32_t)(base + k + 1);
+            ++contributed;
         }
+        if (!was_done) evaluated += (uint32_t)k + (done ? 1u : 0u);  // the stopping one counts
     }
     if (inside) {
         const int64_t hw = (int64_t)cam.W * cam.H;
@@ -114,6 +119,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         if (out_T) out_T[cam.pixel_base + p] = T;
         pix_T[cam.pixel_base + p] = T;
         pix_last[cam.pixel_base + p] = last;
+        pix_count[cam.pixel_base + p] = make_uint2(evaluated, contributed);
     }
 }
 
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
                          int64_t R, const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
                          float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
-                         const DeviceStatus* st, cudaStream_t s) {
+                         uint2* pix_count, const DeviceStatus* st, cudaStream_t s) {
     if (vt.num_tiles == 0) return cudaSuccess;
     const int threads = vt.tile_w * vt.tile_h;
     const size_t smem = (size_t)batch * 3 * sizeof(float4);
@@ -271,7 +277,7 @@ cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_
     if (e != cudaSuccess) return e;
     // with no records every range is empty and no id is read; the kernel still writes bg
     blend_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch,
-                                                              bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, st);
+                                                              bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, pix_count, st);
     return cudaGetLastError();
 }
 

@@ -47,14 +47,15 @@ size_t sort_lookback_entries(int64_t capacity, int digit_bits);
 cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
                         const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
-                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s);
+                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
+                        cudaEvent_t hist_end);
 int sort_passes(int key_bits, int digit_bits);
 
 // (e) blend and its backward
 cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
                          int64_t R, const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
                          float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
-                         const DeviceStatus* st, cudaStream_t s);
+                         uint2* pix_count, const DeviceStatus* st, cudaStream_t s);
 cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
                                   const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
                                   const float* pix_T, const uint32_t* pix_last,

@@ -261,7 +261,7 @@ template <int RB>
 cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
                       const uint32_t* m_ptr, int64_t capacity, int key_bits, uint32_t* hist,
                       uint32_t* goff, uint32_t* counters, unsigned long long* lookback,
-                      DeviceStatus* st, cudaStream_t s) {
+                      DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end) {
     constexpr int RADIX = 1 << RB;
     const int passes = (key_bits + RB - 1) / RB;
     cudaError_t e;
@@ -277,6 +277,7 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
         histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, hist);
         histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : RADIX, 0, s>>>(hist, goff);
     }
+    if (hist_end && (e = cudaEventRecord(hist_end, s)) != cudaSuccess) return e;
     const size_t smem = sizeof(OnesweepSmem<RB>);
     if ((e = cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
@@ -303,13 +304,14 @@ size_t sort_lookback_entries(int64_t capacity, int digit_bits) {
 cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
                         const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
-                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s) {
+                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
+                        cudaEvent_t hist_end) {
     switch (digit_bits) {
-        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
-        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
-        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
-        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
-        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s);
+        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
+        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
+        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
+        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
+        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
         default: return cudaErrorInvalidValue;
     }
 }
