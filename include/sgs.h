@@ -227,6 +227,28 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
                           int32_t digit_bits, void* temp, size_t temp_bytes,
                           cudaStream_t stream);
 
+/* Radix sort that allocates nothing and takes no scratch argument.  The paper has no
+ * counterpart to this entry point; it exists for callers that may not obtain device
+ * memory themselves -- e.g. a host that owns every device allocation through its own pool
+ * or budget, or code that runs where a cudaMalloc would be refused or would stall other
+ * work.  It sorts like sgs_sort_pairs (same kernels, same stable result on the low
+ * key_bits bits, in place), but its scratch is one file-scope device array of
+ * SGS_SORT_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until the
+ * process exits.
+ *  - m must not exceed SGS_SORT_NOALLOC_MAX_PAIRS; a larger m (or other bad argument)
+ *    returns SGS_ERR_INVALID and enqueues nothing.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before any
+ *    stream capture on the device.  A failed lookup returns SGS_ERR_CUDA.
+ *  - All calls share the one array, so calls whose work overlaps on the GPU (different
+ *    streams, no ordering between them) race and give wrong results; serialise them.
+ *  - The array keeps the previous call's contents; each call clears what it reads first.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called. */
+#define SGS_SORT_NOALLOC_MAX_PAIRS (1 << 18)
+#define SGS_SORT_NOALLOC_SCRATCH_BYTES 3320320
+sgs_status sgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key_bits,
+                                  int32_t digit_bits, cudaStream_t stream);
+
 /* Mean absolute error loss of a rendered image against a target, and its gradient:
  * loss[0] = sum |img - target| / count (device float, written), dL_dimg = sign(img -
  * target) / count (sign(0) = 0).  Used for the differentiable training step. */

@@ -27,7 +27,9 @@ REGION = dict(STATUS=0, REC0=1, REC1=2, REC2=3, RECT=4, TILES=5, OFFSETS=6, KEYS
 EXPORTS = ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
            "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
            "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss", "sgs_status_string",
-           "sgs_abi_sizes", "sgs_set_events")
+           "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc")
+
+SORT_NOALLOC_MAX_PAIRS = 1 << 18
 
 # probe points of sgs_set_events (sgs_event_point)
 EVENTS = ("PRE_BEGIN", "PRE_END", "BIN_BEGIN", "SCAN_END", "DUP_END", "HIST_END", "SORT_END",
@@ -103,6 +105,8 @@ def lib():
         L.sgs_abi_sizes.argtypes = [P(C.c_size_t)]
         L.sgs_set_events.argtypes = [P(Plan), vp]
         L.sgs_set_events.restype = st
+        L.sgs_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, i32, vp]
+        L.sgs_sort_pairs_noalloc.restype = st
         for f in ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
                   "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
                   "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss"):
@@ -213,6 +217,12 @@ def sort_temp_bytes(m, key_bits, digit_bits) -> int:
 def sort_pairs(keys_ptr, vals_ptr, m, key_bits, digit_bits, temp_ptr, temp_bytes, stream):
     check("sgs_sort_pairs", lib().sgs_sort_pairs(keys_ptr, vals_ptr, int(m), int(key_bits), int(digit_bits),
                                                  temp_ptr, int(temp_bytes), stream))
+
+
+def sort_pairs_noalloc(keys_ptr, vals_ptr, m, key_bits, digit_bits, stream):
+    """In-place sort with the library's own fixed scratch (no allocation anywhere)."""
+    check("sgs_sort_pairs_noalloc",
+          lib().sgs_sort_pairs_noalloc(keys_ptr, vals_ptr, int(m), int(key_bits), int(digit_bits), stream))
 
 
 def l1_loss(img_ptr, target_ptr, count, loss_ptr, grad_ptr, stream):

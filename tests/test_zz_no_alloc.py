@@ -1,0 +1,62 @@
+"""sgs_sort_pairs_noalloc against sgs_sort_pairs.
+
+The no-allocation sort is for callers that may not obtain device memory themselves (a
+host that owns every device allocation, or code where a cudaMalloc is refused or would
+stall other work).  Its scratch is a fixed array inside the library, so this test checks,
+through the C ABI, that two calls in a row (the second one smaller, so stale contents of
+the shared array would show) give exactly the sort of the entry point that takes a
+caller-provided scratch buffer, and that an oversized request is refused.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2501_00342_b300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _with_scratch(keys, vals, key_bits, digit_bits):
+    k = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    v = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    nb = B.sort_temp_bytes(len(keys), key_bits, digit_bits)
+    temp = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    B.sort_pairs(k.data_ptr(), v.data_ptr(), len(keys), key_bits, digit_bits, temp.data_ptr(), nb, _stream())
+    torch.cuda.synchronize()
+    return k.cpu().numpy().view(np.uint64), v.cpu().numpy().view(np.uint32)
+
+
+def _no_alloc(keys, vals, key_bits, digit_bits):
+    k = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    v = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    code = B.lib().sgs_sort_pairs_noalloc(k.data_ptr(), v.data_ptr(), len(keys), key_bits, digit_bits,
+                                          _stream())
+    assert code == B.SGS_OK, B.status_string(code)
+    torch.cuda.synchronize()
+    return k.cpu().numpy().view(np.uint64), v.cpu().numpy().view(np.uint32)
+
+
+def test_no_alloc_sort_matches_scratch_sort_two_calls():
+    rng = np.random.default_rng(2024)
+    cases = [(B.SORT_NOALLOC_MAX_PAIRS, 49, 8), (77_777, 44, 6)]
+    for m, key_bits, digit_bits in cases:
+        tiles = rng.integers(0, 1 << (key_bits - 32), m).astype(np.uint64)
+        depth = rng.uniform(0.2, 60.0, m).astype(np.float32).view(np.uint32).astype(np.uint64)
+        keys = (tiles << np.uint64(32)) | depth
+        keys[::5] = keys[7]  # ties, to exercise stability
+        vals = np.arange(m, dtype=np.uint32)
+        got_k, got_v = _no_alloc(keys, vals, key_bits, digit_bits)
+        ref_k, ref_v = _with_scratch(keys, vals, key_bits, digit_bits)
+        assert (got_k == ref_k).all() and (got_v == ref_v).all()
+
+
+def test_no_alloc_sort_rejects_oversized_input():
+    m = B.SORT_NOALLOC_MAX_PAIRS + 1
+    k = torch.zeros(m, dtype=torch.int64, device="cuda")
+    v = torch.zeros(m, dtype=torch.int32, device="cuda")
+    code = B.lib().sgs_sort_pairs_noalloc(k.data_ptr(), v.data_ptr(), m, 44, 8, _stream())
+    assert code == B.SGS_ERR_INVALID
