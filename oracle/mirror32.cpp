@@ -10,8 +10,9 @@
 //   Eq. 3   Sigma = R S S^T R^T from the normalised quaternion q and scale s.
 //   EWA     2D covariance J W Sigma W^T J^T [Zwicker 2002; paper Sec. "Preliminaries"],
 //           with the 3D-GS low-pass +0.3 on the diagonal and the 1.3x frustum clamp.
-//   cull    view depth > near, det(Sigma2D) > 0, non-empty tile rectangle.
+//   cull    view depth > near, det(Sigma2D) > 0, the ellipse reaches a tile of the image.
 //   radius  ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det)).
+//   tiles   the tiles the 3-sigma ellipse reaches (row spans, row_span32).
 //   key     (global tile id << 32) | float bits of the view depth.
 #include "oracle_internal.h"
 
@@ -54,8 +55,84 @@ struct Rec32 {
     float px, py;
     float A, B, C;  // conic
     float r;
-    int x0, y0, x1, y1;
+    int x0, y0, x1, y1;  // candidate rectangle (inclusive tile coordinates)
+    int tiles;           // tiles the ellipse reaches (row spans)
 };
+
+// Tiles the Gaussian's 3-sigma ellipse reaches, row by row.  E = {d : Q(d) <= k} with
+// Q(d) = A dx^2 + 2 B dx dy + C dy^2 (the conic), k = 9.01 (the support is Q <= 9; the
+// 0.1 % slack and a 1/64-pixel pad cover rounding, so no tile holding a supported pixel
+// centre is lost).  For a row of tiles, the band of pixel-centre rows [ly, hy] cuts E in a
+// convex set whose x-extent is
+//   max: the ellipse's rightmost point (dx = sqrt(kC/det), dy = -B sqrt(k/(det C))) if
+//        its dy lies in the band, else the larger of dx_hi(dy) at the band ends, where
+//        dx_hi/lo(dy) = (-B dy +/- sqrt(A k - det dy^2)) / A, det = AC - B^2;
+//   min: symmetrically (leftmost point at -dy).
+// The row keeps the tiles whose pixel-centre columns meet that x-extent.
+struct RowSpans {
+    int ty0, ty1;       // rows to visit (inclusive)
+    float ex, ey, dyr, det, invA, Ak;
+    bool ok;
+};
+
+const float kSpanQ = 9.01f;
+const float kSpanPad = 0.015625f;
+
+RowSpans row_setup32(float px, float py, float A, float B, float C, int th, int TH) {
+    RowSpans r;
+    r.ok = false;
+    r.det = A * C - B * B;
+    if (!(r.det > 0.0f)) return r;
+    r.ex = std::sqrt((kSpanQ * C) / r.det);
+    r.ey = std::sqrt((kSpanQ * A) / r.det);
+    r.dyr = -(B * std::sqrt(kSpanQ / (r.det * C)));
+    r.invA = 1.0f / A;
+    r.Ak = A * kSpanQ;
+    float t0 = py - r.ey;
+    t0 = t0 - kSpanPad;
+    t0 = t0 - 0.5f;
+    float t1 = py + r.ey;
+    t1 = t1 + kSpanPad;
+    t1 = t1 - 0.5f;
+    // first and last pixel rows whose centre y + 1/2 lies in [py - ey - pad, py + ey + pad]
+    const float y0 = std::ceil(t0), y1 = std::floor(t1);
+    if (!(y0 <= y1)) return r;
+    const float f0 = std::fmax(std::floor(y0 / (float)th), 0.0f);
+    const float f1 = std::fmin(std::floor(y1 / (float)th), (float)(TH - 1));
+    if (!(f0 <= f1)) return r;
+    r.ty0 = (int)f0;
+    r.ty1 = (int)f1;
+    r.ok = true;
+    return r;
+}
+
+// Columns [tx0, tx1] of row ty; false if the row holds none.
+bool row_span32(const RowSpans& r, float px, float py, float B, int ty, int tw, int th, int TW,
+                int* tx0, int* tx1) {
+    const float ly = (float)(ty * th) + 0.5f, hy = (float)(ty * th + th) - 0.5f;
+    const float eyp = r.ey + kSpanPad;
+    const float u0 = std::fmax(ly - py, -eyp);
+    const float u1 = std::fmin(hy - py, eyp);
+    if (!(u0 <= u1)) return false;
+    const float s0 = std::sqrt(std::fmax(0.0f, r.Ak - (r.det * u0) * u0));
+    const float s1 = std::sqrt(std::fmax(0.0f, r.Ak - (r.det * u1) * u1));
+    const float b0 = B * u0, b1 = B * u1;
+    const float hi0 = (s0 - b0) * r.invA, hi1 = (s1 - b1) * r.invA;
+    const float lo0 = (-(b0 + s0)) * r.invA, lo1 = (-(b1 + s1)) * r.invA;
+    const float xmax = (u0 <= r.dyr && r.dyr <= u1) ? r.ex : std::fmax(hi0, hi1);
+    const float xmin = (u0 <= -r.dyr && -r.dyr <= u1) ? -r.ex : std::fmin(lo0, lo1);
+    const float xs0 = (px + xmin) - kSpanPad;
+    const float xs1 = (px + xmax) + kSpanPad;
+    // first and last pixel columns whose centre x + 1/2 lies in [xs0, xs1]
+    const float x0 = std::ceil(xs0 - 0.5f), x1 = std::floor(xs1 - 0.5f);
+    if (!(x0 <= x1)) return false;
+    const float f0 = std::fmax(std::floor(x0 / (float)tw), 0.0f);
+    const float f1 = std::fmin(std::floor(x1 / (float)tw), (float)(TW - 1));
+    if (!(f0 <= f1)) return false;
+    *tx0 = (int)f0;
+    *tx1 = (int)f1;
+    return true;
+}
 
 // One Gaussian seen from one camera, every operation rounded to float on its own.
 Rec32 project32(const orc_scene* s, int64_t i, const Cam32& k, int tile_w, int tile_h) {
@@ -180,7 +257,15 @@ Rec32 project32(const orc_scene* s, int64_t i, const Cam32& k, int tile_w, int t
     o.x1 = (int)x1;
     o.y0 = (int)y0;
     o.y1 = (int)y1;
-    o.visible = true;
+    const RowSpans rs = row_setup32(px, py, o.A, o.B, o.C, tile_h, TH);
+    int hits = 0;
+    if (rs.ok)
+        for (int ty = rs.ty0; ty <= rs.ty1; ++ty) {
+            int a0, a1;
+            if (row_span32(rs, px, py, o.B, ty, tile_w, tile_h, TW, &a0, &a1)) hits += a1 - a0 + 1;
+        }
+    o.tiles = hits;
+    o.visible = hits > 0;
     return o;
 }
 
@@ -242,8 +327,7 @@ void orc_mirror_preprocess(const orc_scene* s, const float* cams, int32_t B, int
             rect[4 * r + 1] = o.y0;
             rect[4 * r + 2] = o.x1;
             rect[4 * r + 3] = o.y1;
-            tiles_touched[r] =
-                o.visible ? (uint32_t)((o.x1 - o.x0 + 1) * (o.y1 - o.y0 + 1)) : 0u;
+            tiles_touched[r] = o.visible ? (uint32_t)o.tiles : 0u;
         }
     }
 }
@@ -264,7 +348,7 @@ int64_t orc_mirror_count(const orc_scene* s, const float* cams, int32_t B, int32
         const Cam32 k = cam32(cams + 22 * v);
         for (int64_t i = 0; i < s->n; ++i) {
             const Rec32 o = project32(s, i, k, tile_w, tile_h);
-            if (o.visible) m += (int64_t)(o.x1 - o.x0 + 1) * (o.y1 - o.y0 + 1);
+            if (o.visible) m += o.tiles;
         }
     }
     return m;
@@ -288,7 +372,8 @@ void orc_stable_sort_pairs(int64_t m, uint64_t* keys, uint32_t* vals) {
 void orc_mirror_bin(const orc_scene* s, const float* cams, int32_t B, int32_t tile_w,
                     int32_t tile_h, uint64_t* keys_in, uint32_t* vals_in, uint64_t* keys_out,
                     uint32_t* vals_out, uint32_t* ranges) {
-    // Instances in record order (record r = v*n + i), tiles of a rectangle row-major.
+    // Instances in record order (record r = v*n + i), the tiles the ellipse reaches in
+// row-major order.
     int64_t m = 0;
     uint64_t tile_base = 0;
     for (int v = 0; v < B; ++v) {
@@ -297,13 +382,17 @@ void orc_mirror_bin(const orc_scene* s, const float* cams, int32_t B, int32_t ti
         for (int64_t i = 0; i < s->n; ++i) {
             const Rec32 o = project32(s, i, k, tile_w, tile_h);
             if (!o.visible) continue;
-            for (int ty = o.y0; ty <= o.y1; ++ty)
-                for (int tx = o.x0; tx <= o.x1; ++tx) {
+            const RowSpans rs = row_setup32(o.px, o.py, o.A, o.B, o.C, tile_h, ceil_div(k.H, tile_h));
+            for (int ty = rs.ty0; ty <= rs.ty1; ++ty) {
+                int a0, a1;
+                if (!row_span32(rs, o.px, o.py, o.B, ty, tile_w, tile_h, TW, &a0, &a1)) continue;
+                for (int tx = a0; tx <= a1; ++tx) {
                     const uint64_t tile = tile_base + (uint64_t)ty * TW + tx;
                     keys_in[m] = (tile << 32) | o.depth_bits;
                     vals_in[m] = (uint32_t)((int64_t)v * s->n + i);
                     ++m;
                 }
+            }
         }
         tile_base += (uint64_t)TW * ceil_div(k.H, tile_h);
     }

@@ -15,7 +15,7 @@ namespace {
 
 enum Region {
     O_STATUS, O_REC0, O_REC1, O_REC2, O_RECT, O_TILES, O_OFFS, O_K0, O_V0, O_K1, O_V1,
-    O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
+    O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SPANS, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
     O_COUNTERS, O_END
 };
 
@@ -101,6 +101,7 @@ RecordPtrs records(const sgs_plan* p) {
     r.rec2 = region<float4>(p, O_REC2);
     r.rect = region<uint2>(p, O_RECT);
     r.tiles = region<uint32_t>(p, O_TILES);
+    r.spans = region<uint4>(p, O_SPANS);
     return r;
 }
 
@@ -198,6 +199,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_PIXT] = sz[O_PIXLAST] = 4 * (size_t)pixels;
     sz[O_GRAD2D] = 48 * (size_t)R;
     sz[O_PIXCOUNT] = 8 * (size_t)pixels;
+    sz[O_SPANS] = 64 * (size_t)R;
     sz[O_SCANLB] = 8 * (size_t)((R + kScanTile - 1) / kScanTile + 1);
     sz[O_HIST] = sz[O_GOFF] = 4 * (size_t)kMaxSortPasses * 256;
     sz[O_SORTLB] = 8 * sort_lookback_entries(instance_capacity, settings->digit_bits);
@@ -244,7 +246,9 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     SGS_TRY(launch_scan(rp.tiles, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));
     SGS_TRY(probe(plan, SGS_EV_SCAN_END, stream));
     SGS_TRY(launch_duplicate(vt, rp, region<uint32_t>(plan, O_OFFS), plan->n, R, st, cap,
-                             region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0), stream));
+                             region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
+                             plan->settings.digit_bits, plan->sort_passes, region<uint32_t>(plan, O_HIST),
+                             stream));
     SGS_TRY(probe(plan, SGS_EV_DUP_END, stream));
     cudaEvent_t hist_end = plan->events ? plan->events[SGS_EV_HIST_END] : nullptr;
     SGS_TRY(launch_sort(region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
@@ -252,7 +256,7 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
                         &st->m_clamped, cap, plan->key_bits, plan->settings.digit_bits,
                         region<uint32_t>(plan, O_HIST), region<uint32_t>(plan, O_GOFF),
                         region<uint32_t>(plan, O_COUNTERS), region<unsigned long long>(plan, O_SORTLB),
-                        st, stream, hist_end));
+                        st, stream, hist_end, /*histogram_ready=*/true));
     SGS_TRY(probe(plan, SGS_EV_SORT_END, stream));
     const int kreg = (plan->sort_passes & 1) ? O_K1 : O_K0;
     SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));

@@ -61,6 +61,80 @@ __device__ __forceinline__ float support_power(float qa, float qb, float qc, flo
     return __fmaf_rn(dx, u, w);
 }
 
+// Tiles the Gaussian's 3-sigma ellipse reaches, row by row.  E = {d : Q(d) <= k} with
+// Q(d) = A dx^2 + 2 B dx dy + C dy^2 (the conic), k = 9.01: the support is Q <= 9, and the
+// 0.1 % slack plus a 1/64-pixel pad cover rounding, so no tile holding a supported pixel
+// centre is dropped.  In a tile row, the band of pixel-centre rows [ly, hy] cuts E in a
+// convex set whose x-extent is bounded by the ellipse's rightmost point
+// (dx = sqrt(kC/det), dy = -B sqrt(k/(det C)), det = AC - B^2) when that lies in the band,
+// else by dx_hi(dy) = (-B dy + sqrt(A k - det dy^2)) / A at the band ends (and
+// symmetrically for the left end).  The row keeps the tiles holding a pixel-centre column
+// inside that extent.  One fixed order of correctly rounded operations: the count in
+// preprocess and the keys in duplicate agree exactly.
+constexpr int kSpanRows = 15;                // rows kept in a record's packed table
+constexpr uint32_t kSpanRowsOverflow = 0xffffu;
+constexpr float kSpanQ = 9.01f;
+constexpr float kSpanPad = 0.015625f;
+
+struct RowSpans {
+    int ty0, ty1;  // rows to visit
+    float ex, ey, dyr, det, invA, Ak;
+    bool ok;
+};
+
+__device__ __forceinline__ RowSpans row_setup(float px, float py, float A, float B, float C, int th,
+                                              int TH) {
+    RowSpans r;
+    r.ok = false;
+    r.ty0 = 0;
+    r.ty1 = -1;
+    r.det = sub_rn(mul_rn(A, C), mul_rn(B, B));
+    if (!(r.det > 0.0f)) return r;
+    r.ex = sqrt_rn(div_rn(mul_rn(kSpanQ, C), r.det));
+    r.ey = sqrt_rn(div_rn(mul_rn(kSpanQ, A), r.det));
+    r.dyr = -mul_rn(B, sqrt_rn(div_rn(kSpanQ, mul_rn(r.det, C))));
+    r.invA = div_rn(1.0f, A);
+    r.Ak = mul_rn(A, kSpanQ);
+    const float t0 = sub_rn(sub_rn(sub_rn(py, r.ey), kSpanPad), 0.5f);
+    const float t1 = sub_rn(add_rn(add_rn(py, r.ey), kSpanPad), 0.5f);
+    const float y0 = ceilf(t0), y1 = floorf(t1);  // pixel rows with centres in the extent
+    if (!(y0 <= y1)) return r;
+    const float f0 = fmaxf(floorf(div_rn(y0, (float)th)), 0.0f);
+    const float f1 = fminf(floorf(div_rn(y1, (float)th)), (float)(TH - 1));
+    if (!(f0 <= f1)) return r;
+    r.ty0 = (int)f0;
+    r.ty1 = (int)f1;
+    r.ok = true;
+    return r;
+}
+
+// Tile columns [tx0, tx1] of row ty (false: none).
+__device__ __forceinline__ bool row_span(const RowSpans& r, float px, float py, float B, int ty, int tw,
+                                         int th, int TW, int& tx0, int& tx1) {
+    const float ly = add_rn((float)(ty * th), 0.5f), hy = sub_rn((float)(ty * th + th), 0.5f);
+    const float eyp = add_rn(r.ey, kSpanPad);
+    const float u0 = fmaxf(sub_rn(ly, py), -eyp);
+    const float u1 = fminf(sub_rn(hy, py), eyp);
+    if (!(u0 <= u1)) return false;
+    const float s0 = sqrt_rn(fmaxf(0.0f, sub_rn(r.Ak, mul_rn(mul_rn(r.det, u0), u0))));
+    const float s1 = sqrt_rn(fmaxf(0.0f, sub_rn(r.Ak, mul_rn(mul_rn(r.det, u1), u1))));
+    const float b0 = mul_rn(B, u0), b1 = mul_rn(B, u1);
+    const float hi0 = mul_rn(sub_rn(s0, b0), r.invA), hi1 = mul_rn(sub_rn(s1, b1), r.invA);
+    const float lo0 = mul_rn(-add_rn(b0, s0), r.invA), lo1 = mul_rn(-add_rn(b1, s1), r.invA);
+    const float xmax = (u0 <= r.dyr && r.dyr <= u1) ? r.ex : fmaxf(hi0, hi1);
+    const float xmin = (u0 <= -r.dyr && -r.dyr <= u1) ? -r.ex : fminf(lo0, lo1);
+    const float xs0 = sub_rn(add_rn(px, xmin), kSpanPad);
+    const float xs1 = add_rn(add_rn(px, xmax), kSpanPad);
+    const float x0 = ceilf(sub_rn(xs0, 0.5f)), x1 = floorf(sub_rn(xs1, 0.5f));
+    if (!(x0 <= x1)) return false;
+    const float f0 = fmaxf(floorf(div_rn(x0, (float)tw)), 0.0f);
+    const float f1 = fminf(floorf(div_rn(x1, (float)tw)), (float)(TW - 1));
+    if (!(f0 <= f1)) return false;
+    tx0 = (int)f0;
+    tx1 = (int)f1;
+    return true;
+}
+
 constexpr float kSupportPower = -4.5f;     // Mahalanobis distance 3
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;

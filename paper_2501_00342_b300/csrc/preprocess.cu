@@ -5,7 +5,8 @@
 //   Sigma = R S S^T R^T from q/|q| and s (Eq. 3)
 //   Sigma2D = J W Sigma W^T J^T + 0.3 I, J the EWA Jacobian at t with x/z, y/z clamped
 //             to 1.3x the half field of view (the projection of Sec. "Preliminaries")
-//   conic = Sigma2D^-1, radius = ceil(3 sqrt(lambda_max)), screen mean, tile rectangle
+//   conic = Sigma2D^-1, radius = ceil(3 sqrt(lambda_max)), screen mean, tile rectangle,
+//   and how many tiles the 3-sigma ellipse reaches (row spans)
 //   colour = max(0, SH(d) + 0.5 + sum_k SG_k(d)), d = (X - campos)/|X - campos| (Eq. 4-9)
 // Everything up to the tile rectangle and the conic uses correctly rounded operations in
 // one fixed order (mul_rn/add_rn/...), so the cull, depth bits, radius and rectangle are
@@ -170,6 +171,32 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
     P.visible = true;
 }
 
+// Tiles the ellipse reaches (0: the Gaussian is culled), and the packed row table the
+// duplicate kernel reads (16 words): word 0 = first row | rows << 16; words 1..15 = first
+// column | (tiles in the earlier rows) << 16 per row.  More than kSpanRows rows or more
+// than 65535 tiles mark a table the kernel recomputes instead.
+__device__ __forceinline__ uint32_t count_tiles(const Projected& P, const View& cam, int tw, int th,
+                                                uint32_t table[16]) {
+    const RowSpans rs = row_setup(P.px, P.py, P.A, P.B, P.C, th, cam.tiles_y);
+    uint32_t hits = 0;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) table[k] = 0xffff0000u;
+    for (int ty = rs.ty0; ty <= rs.ty1; ++ty) {
+        int a0 = 0, a1 = -1;
+        row_span(rs, P.px, P.py, P.B, ty, tw, th, cam.tiles_x, a0, a1);
+        const int k = ty - rs.ty0;
+        const uint32_t word = (uint32_t)(a1 >= a0 ? a0 : 0) | (min(hits, 0xffffu) << 16);
+#pragma unroll
+        for (int j = 0; j < kSpanRows; ++j)
+            if (j == k) table[1 + j] = word;
+        if (a1 >= a0) hits += (uint32_t)(a1 - a0 + 1);
+    }
+    const int rows = rs.ty1 - rs.ty0 + 1;
+    const bool fits = rows <= kSpanRows && hits <= 0xffffu;
+    table[0] = (uint32_t)rs.ty0 | ((fits ? (uint32_t)rows : kSpanRowsOverflow) << 16);
+    return hits;
+}
+
 __device__ __forceinline__ void view_direction(const View& cam, const float X[3], float d[3],
                                                float& len) {
     const float dx = X[0] - cam.campos[0], dy = X[1] - cam.campos[1], dz = X[2] - cam.campos[2];
@@ -186,7 +213,8 @@ __global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, 
                                                          float4* __restrict__ rec1,
                                                          float4* __restrict__ rec2,
                                                          uint2* __restrict__ rect,
-                                                         uint32_t* __restrict__ tiles) {
+                                                         uint32_t* __restrict__ tiles,
+                                                         uint4* __restrict__ spans) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int64_t S = g.stride;
@@ -201,7 +229,9 @@ __global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, 
         const int64_t r = (int64_t)v * g.n + i;
         Projected P;
         project_exact(cam, X, G, vt.tile_w, vt.tile_h, P);
-        if (!P.visible) {
+        uint32_t table[16];
+        const uint32_t hits = P.visible ? count_tiles(P, cam, vt.tile_w, vt.tile_h, table) : 0u;
+        if (hits == 0u) {
             rect[r] = make_uint2(0u, 0u);
             tiles[r] = 0u;
             continue;
@@ -222,7 +252,10 @@ __global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, 
         rec2[r] = make_float4(pre[0], pre[1], pre[2], __uint_as_float(mask));
         rect[r] = make_uint2((uint32_t)P.x0 | ((uint32_t)P.y0 << 16),
                              (uint32_t)P.x1 | ((uint32_t)P.y1 << 16));
-        tiles[r] = (uint32_t)((P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1));
+        tiles[r] = hits;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            spans[4 * r + k] = make_uint4(table[4 * k], table[4 * k + 1], table[4 * k + 2], table[4 * k + 3]);
     }
 }
 
@@ -365,7 +398,7 @@ cudaError_t launch_pre(const sgs_gaussians& g, const ViewTable& vt, const Record
     const int blocks = (int)((g.n + threads - 1) / threads);
     if (blocks > 0)
         preprocess_kernel<L, K, FIXED><<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.rec2, p.rect,
-                                                                 p.tiles);
+                                                                 p.tiles, p.spans);
     return cudaGetLastError();
 }
 

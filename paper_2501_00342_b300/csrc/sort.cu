@@ -261,11 +261,12 @@ template <int RB>
 cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
                       const uint32_t* m_ptr, int64_t capacity, int key_bits, uint32_t* hist,
                       uint32_t* goff, uint32_t* counters, unsigned long long* lookback,
-                      DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end) {
+                      DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready) {
     constexpr int RADIX = 1 << RB;
     const int passes = (key_bits + RB - 1) / RB;
     cudaError_t e;
-    if ((e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s)) != cudaSuccess) return e;
+    if (!histogram_ready && (e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s)) != cudaSuccess)
+        return e;
     if ((e = launch_fill_u32(counters, 0u, kMaxSortPasses, s)) != cudaSuccess) return e;
     const size_t tiles = (size_t)((capacity + kSortTile - 1) / kSortTile);
     if ((e = launch_fill_u32(reinterpret_cast<uint32_t*>(lookback), 0u, tiles * RADIX * 2, s)) != cudaSuccess)
@@ -274,7 +275,7 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
     {
         const int64_t want = (capacity + 255) / 256;
         const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
-        histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, hist);
+        if (!histogram_ready) histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, hist);
         histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : RADIX, 0, s>>>(hist, goff);
     }
     if (hist_end && (e = cudaEventRecord(hist_end, s)) != cudaSuccess) return e;
@@ -305,13 +306,13 @@ cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long
                         const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
                         unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
-                        cudaEvent_t hist_end) {
+                        cudaEvent_t hist_end, bool histogram_ready) {
     switch (digit_bits) {
-        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
-        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
-        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
-        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
-        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end);
+        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -153,4 +153,6 @@ def test_rect_and_tiles_touched():
         rect = m["rect"][vis]
         assert (rect[:, 0] == x0).all() and (rect[:, 2] == x1).all()
         assert (rect[:, 1] == y0).all() and (rect[:, 3] == y1).all()
-        assert (m["tiles_touched"][vis] == (x1 - x0 + 1) * (y1 - y0 + 1)).all()
+        # the ellipse reaches at least one and at most all tiles of the rectangle
+        tt = m["tiles_touched"][vis]
+        assert (tt >= 1).all() and (tt <= (x1 - x0 + 1) * (y1 - y0 + 1)).all()
