@@ -16,7 +16,7 @@ namespace {
 enum Region {
     O_STATUS, O_REC0, O_REC1, O_REC2, O_RECT, O_TILES, O_OFFS, O_K0, O_V0, O_K1, O_V1,
     O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SPANS, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
-    O_COUNTERS, O_END
+    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_END
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -162,7 +162,8 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     int64_t tiles = 0, pixels = 0;
     for (int v = 0; v < B; ++v) {
         const sgs_camera& c = cams[v];
-        if (c.width < 1 || c.height < 1 || !(c.fx > 0.0f) || !(c.fy > 0.0f)) return SGS_ERR_INVALID;
+        if (c.width < 1 || c.height < 1 || !(c.fx > 0.0f) || !(c.fy > 0.0f) || !(c.near_plane > 0.0f))
+            return SGS_ERR_INVALID;  // depth > near > 0 keeps the depth bits ordered as values
         const int32_t tx = (c.width + settings->tile_w - 1) / settings->tile_w;
         const int32_t ty = (c.height + settings->tile_h - 1) / settings->tile_h;
         if (tx > 65535 || ty > 65535) return SGS_ERR_INVALID;
@@ -184,7 +185,9 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     plan->num_pixels = pixels;
     plan->instance_capacity = instance_capacity;
     plan->key_bits = 32 + ceil_log2(tiles < 1 ? 1 : tiles);
-    plan->sort_passes = sort_passes(plan->key_bits, settings->digit_bits);
+    // the depth half of the key is ordered by the record sort; the instance sort takes the
+    // tile bits only
+    plan->sort_passes = sort_passes(32, plan->key_bits, settings->digit_bits);
     if (plan->sort_passes > kMaxSortPasses) return SGS_ERR_INVALID;
 
     size_t sz[O_END];
@@ -204,6 +207,9 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_HIST] = sz[O_GOFF] = 4 * (size_t)kMaxSortPasses * 256;
     sz[O_SORTLB] = 8 * sort_lookback_entries(instance_capacity, settings->digit_bits);
     sz[O_COUNTERS] = 4 * (size_t)kMaxSortPasses;
+    sz[O_RK0] = sz[O_RK1] = 8 * (size_t)R;
+    sz[O_RV0] = sz[O_RV1] = 4 * (size_t)R;
+    sz[O_RLB] = 8 * sort_lookback_entries(R, settings->digit_bits);
     size_t off = 0;
     for (int k = 0; k < O_END; ++k) {
         plan->offsets[k] = off;
@@ -243,20 +249,37 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     SGS_TRY(launch_fill_u32(st->tile_counter, 0u, 16, stream));
     SGS_TRY(launch_fill_u32(reinterpret_cast<uint32_t*>(scan_lb), 0u,
                             2 * (size_t)((R + kScanTile - 1) / kScanTile + 1), stream));
-    SGS_TRY(launch_scan(rp.tiles, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));
+    // (c, depth half) stable sort of the records by view depth bits
+    const int rpasses = sort_passes(0, 32, plan->settings.digit_bits);
+    SGS_TRY(launch_record_keys(rp.tiles, rp.rec1, R, region<unsigned long long>(plan, O_RK0),
+                               region<uint32_t>(plan, O_RV0), st, stream));
+    if (R > 0)
+        SGS_TRY(launch_sort(region<unsigned long long>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
+                            region<unsigned long long>(plan, O_RK1), region<uint32_t>(plan, O_RV1),
+                            &st->num_records, R, 0, 32, plan->settings.digit_bits, region<uint32_t>(plan, O_HIST),
+                            region<uint32_t>(plan, O_GOFF), region<uint32_t>(plan, O_COUNTERS),
+                            region<unsigned long long>(plan, O_RLB), st, stream, nullptr));
+    const uint32_t* perm = region<uint32_t>(plan, (rpasses & 1) ? O_RV1 : O_RV0);
+    // (b) counts and instances in depth order
+    SGS_TRY(launch_scan(rp.tiles, perm, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));
     SGS_TRY(probe(plan, SGS_EV_SCAN_END, stream));
-    SGS_TRY(launch_duplicate(vt, rp, region<uint32_t>(plan, O_OFFS), plan->n, R, st, cap,
+    SGS_TRY(launch_duplicate(vt, rp, perm, region<uint32_t>(plan, O_OFFS), plan->n, R, st, cap,
                              region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
                              plan->settings.digit_bits, plan->sort_passes, region<uint32_t>(plan, O_HIST),
                              stream));
     SGS_TRY(probe(plan, SGS_EV_DUP_END, stream));
+    // (c, tile half) stable sort of the instances by tile id
     cudaEvent_t hist_end = plan->events ? plan->events[SGS_EV_HIST_END] : nullptr;
-    SGS_TRY(launch_sort(region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
-                        region<unsigned long long>(plan, O_K1), region<uint32_t>(plan, O_V1),
-                        &st->m_clamped, cap, plan->key_bits, plan->settings.digit_bits,
-                        region<uint32_t>(plan, O_HIST), region<uint32_t>(plan, O_GOFF),
-                        region<uint32_t>(plan, O_COUNTERS), region<unsigned long long>(plan, O_SORTLB),
-                        st, stream, hist_end, /*histogram_ready=*/true));
+    if (plan->sort_passes > 0) {
+        SGS_TRY(launch_sort(region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
+                            region<unsigned long long>(plan, O_K1), region<uint32_t>(plan, O_V1),
+                            &st->m_clamped, cap, 32, plan->key_bits, plan->settings.digit_bits,
+                            region<uint32_t>(plan, O_HIST), region<uint32_t>(plan, O_GOFF),
+                            region<uint32_t>(plan, O_COUNTERS), region<unsigned long long>(plan, O_SORTLB),
+                            st, stream, hist_end, /*histogram_ready=*/true));
+    } else if (hist_end) {
+        SGS_TRY(cudaEventRecord(hist_end, stream));
+    }
     SGS_TRY(probe(plan, SGS_EV_SORT_END, stream));
     const int kreg = (plan->sort_passes & 1) ? O_K1 : O_K0;
     SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));
@@ -393,7 +416,7 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
     unsigned long long* lb = reinterpret_cast<unsigned long long*>(take(8 * sort_lookback_entries(m, digit_bits)));
     unsigned long long* k0 = reinterpret_cast<unsigned long long*>(keys);
     SGS_TRY(launch_sort_init(st, (uint32_t)m, stream));
-    SGS_TRY(launch_sort(k0, vals, k1, v1, &st->m_clamped, m, key_bits, digit_bits, hist, goff, counters, lb,
+    SGS_TRY(launch_sort(k0, vals, k1, v1, &st->m_clamped, m, 0, key_bits, digit_bits, hist, goff, counters, lb,
                         st, stream, nullptr));
     if (sort_passes(key_bits, digit_bits) & 1) SGS_TRY(launch_copy_pairs(k1, v1, k0, vals, m, stream));
     return SGS_OK;

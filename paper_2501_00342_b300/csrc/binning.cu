@@ -31,6 +31,7 @@ __global__ void fill_u32_kernel(uint32_t* p, uint32_t value, size_t count) {
 // Single-pass exclusive scan (chained scan with decoupled look-back).  Each CTA takes
 // the next tile id from a counter, so every predecessor tile is already running.
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __restrict__ in,
+                                                             const uint32_t* __restrict__ perm,
                                                              uint32_t* __restrict__ out, int64_t R,
                                                              unsigned long long* lookback,
                                                              DeviceStatus* st, int64_t capacity) {
@@ -42,7 +43,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
     const uint32_t tile = s_tile;
     const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
-    if (base + kScanItems <= R) {
+    if (perm) {  // counts taken in the order of the depth-sorted records
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < R) ? in[perm[base + q]] : 0u;
+    } else if (base + kScanItems <= R) {
         const uint4* p4 = reinterpret_cast<const uint4*>(in + base);
 #pragma unroll
         for (int q = 0; q < kScanItems / 4; ++q) {
@@ -133,44 +137,54 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Digit counts of the passes whose digit reaches into the tile bits, for the key of tile t
-// (row of tiles [row_t0, row_end)).  Along a row the tile ids are consecutive, so such a
-// digit is constant on segments of 2^s tiles (s = the pass's first bit minus 32, or 0 if
-// the digit also holds depth bits): the key that opens a segment adds the segment length.
+// Keys of the record sort: the float bits of the view depth of a record with instances
+// (depth > near > 0, so the bits order like the values), 0xffffffff for the others.
+__global__ void record_keys_kernel(const uint32_t* __restrict__ tiles, const float4* __restrict__ rec1,
+                                   int64_t R, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
+                                   DeviceStatus* st) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) st->num_records = (uint32_t)R;
+    if (r >= R) return;
+    keys[r] = tiles[r] ? (unsigned long long)__float_as_uint(rec1[r].z) : 0xffffffffull;
+    vals[r] = (uint32_t)r;
+}
+
+// Digit counts of the tile sort (its digits cover the tile id, bits 32 and up of a key) for
+// the key of tile t in a row of tiles [row_t0, row_end).  Along a row the tile ids are
+// consecutive, so the digit of pass p (bits p*RB.. of the tile id) is constant on segments
+// of 2^(p*RB) tiles: the key that opens a segment adds the segment's length.
 template <int RB>
-__device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, unsigned long long key, uint32_t t,
-                                                  uint32_t row_t0, uint32_t row_end) {
+__device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, uint32_t t, uint32_t row_t0,
+                                                  uint32_t row_end) {
     constexpr int RADIX = 1 << RB;
-    constexpr int MAXP = (64 + RB - 1) / RB;
-    // pass 32 / RB is the first whose digit reaches past bit 31
+    constexpr int MAXP = (32 + RB - 1) / RB;
 #pragma unroll
-    for (int p = 32 / RB; p < MAXP; ++p) {
+    for (int p = 0; p < MAXP; ++p) {
         if (p >= passes) break;
-        const int lo = p * RB;
-        const int sh = lo > 32 ? lo - 32 : 0;
-        const uint32_t mask = (1u << sh) - 1u;
-        if (sh > 0 && t != row_t0 && (t & mask) != 0u) continue;  // not the first key of its segment
+        const int sh = p * RB;
+        if (sh > 0 && t != row_t0 && (t & ((1u << sh) - 1u)) != 0u) continue;  // inside a segment
         const uint32_t seg_end = sh > 0 ? min(row_end, ((t >> sh) + 1u) << sh) : t + 1u;
-        const uint32_t d = (uint32_t)(key >> lo) & (RADIX - 1);
-        atomicAdd(&h[p * RADIX + d], seg_end - t);
+        atomicAdd(&h[p * RADIX + ((t >> sh) & (RADIX - 1))], seg_end - t);
     }
 }
 
-// One warp per group of 32 consecutive records.  Their instances occupy one contiguous
-// output range (the scan's offsets are consecutive), so the warp fills it 32 slots at a
-// time: for slot e a 5-step shuffle search finds the record (inclusive scan of the counts);
-// the record's packed row table (written by preprocess: first column and tiles-before per
-// row) gives the row by a branch-free count, and consecutive lanes write consecutive slots.
-// A record whose table overflowed is filled afterwards by the whole warp, recomputing its
-// rows with row_span.  The pre-sort order is (record, tile row-major).
-// The radix sort's digit histograms are counted here too: digits wholly inside the depth
-// bits are the same for all of a record's keys and are counted once per record (weighted by
-// its count); the others per segment of consecutive tiles (count_tile_digits).
+// Writes the (tile | depth, record) instances in the order of the depth-sorted records
+// (perm): sorted position j emits its record's tiles at offsets[j] (the scan taken in that
+// order), tiles row-major.  One warp per 32 consecutive sorted positions, whose instances
+// fill one contiguous output range 32 slots at a time: for slot e a 5-step shuffle search
+// finds the record (inclusive scan of the counts), its packed row table (written by
+// preprocess, staged in shared memory) gives the row, and consecutive lanes write
+// consecutive slots.  A record whose table overflowed is filled afterwards by the whole
+// warp, recomputing its rows with row_span.  Since every key of a record carries the same
+// depth, this order is (depth bits, record) -- what the low 32 bits of a stable LSD radix
+// sort would produce -- and only the tile bits are left to sort.  The digit histograms of
+// that tile sort are counted here (count_tile_digits).
 template <int RB>
 __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, const uint4* __restrict__ spans,
                                                          const uint32_t* __restrict__ tiles,
                                                          const float4* __restrict__ rec0,
                                                          const float4* __restrict__ rec1,
+                                                         const uint32_t* __restrict__ perm,
                                                          const uint32_t* __restrict__ offsets,
                                                          int64_t n, int64_t R, const DeviceStatus* st,
                                                          int64_t capacity,
@@ -189,29 +203,23 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
     const uint32_t n32 = (uint32_t)n;
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < R;
          base += warps * 32) {
-        const int64_t r = base + lane;
-        const uint32_t cnt = (r < R && !overflow) ? tiles[r] : 0u;
+        const int64_t j = base + lane;
+        const uint32_t r = j < R ? perm[j] : 0u;
+        const uint32_t cnt = (j < R && !overflow && r < (uint32_t)R) ? tiles[r] : 0u;
         if (!__ballot_sync(kFullMask, cnt != 0u)) continue;
         uint32_t zbits = 0, tbase = 0, hdr = 0;
         int TW = 0;
         if (cnt) {
             zbits = __float_as_uint(rec1[r].z);
-            const int v = (int)((uint32_t)r / n32);
+            const int v = (int)(r / n32);
             tbase = vt.v[v].tile_base;
             TW = vt.v[v].tiles_x;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) tab[lane][k] = spans[4 * r + k];
+            for (int k = 0; k < 4; ++k) tab[lane][k] = spans[4 * (size_t)r + k];
             hdr = tab[lane][0].x;
         }
         __syncwarp();
         const bool slow = cnt && (hdr >> 16) == kSpanRowsOverflow;
-        // digits inside the depth bits: once per record, weighted by its instance count
-        for (int p = 0; p < passes && (p + 1) * RB <= 32; ++p) {
-            const uint32_t d = cnt ? (zbits >> (p * RB)) & (RADIX - 1) : RADIX;
-            const uint32_t peers = __match_any_sync(kFullMask, d);
-            const uint32_t group = __reduce_add_sync(peers, cnt);
-            if (cnt && lane == 31 - __clz(peers)) atomicAdd(&h[p * RADIX + d], group);
-        }
         uint32_t incl = cnt;  // inclusive warp scan of the counts
 #pragma unroll
         for (int k = 1; k < 32; k <<= 1) {
@@ -233,6 +241,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
             const uint32_t cq = __shfl_sync(kFullMask, cnt, q);
             const uint32_t zb = __shfl_sync(kFullMask, zbits, q);
             const uint32_t tb = __shfl_sync(kFullMask, tbase, q);
+            const uint32_t rq = __shfl_sync(kFullMask, r, q);
             const int TWq = __shfl_sync(kFullMask, TW, q);
             const bool slow_q = __shfl_sync(kFullMask, (uint32_t)slow, q) != 0u;
             if (e < total && !slow_q) {
@@ -248,28 +257,28 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
                 const int ty = (int)(tq[0] & 0xffffu) + k;
                 const uint32_t row_t0 = tb + (uint32_t)(ty * TWq) + (rw & 0xffffu);
                 const uint32_t t = row_t0 + (local - before);
-                const unsigned long long key = ((unsigned long long)t << 32) | zb;
                 const uint32_t pos = obase + e;
                 if ((int64_t)pos < capacity) {  // only false after a failed scan
-                    keys[pos] = key;
-                    vals[pos] = (uint32_t)(base + q);
+                    keys[pos] = ((unsigned long long)t << 32) | zb;
+                    vals[pos] = rq;
                 }
-                count_tile_digits<RB>(h, passes, key, t, row_t0, row_t0 + (after - before));
+                count_tile_digits<RB>(h, passes, t, row_t0, row_t0 + (after - before));
             }
         }
         // records whose row table overflowed: the whole warp recomputes their rows
         uint32_t todo = __ballot_sync(kFullMask, slow);
         while (todo) {
-            const int j = __ffs(todo) - 1;
+            const int jj = __ffs(todo) - 1;
             todo &= todo - 1;
-            const float4 aj = rec0[base + j];
-            const float qc = rec1[base + j].x;
+            const uint32_t rj = __shfl_sync(kFullMask, r, jj);
+            const float4 aj = rec0[rj];
+            const float qc = rec1[rj].x;
             const float px = aj.x, py = aj.y, A = -2.0f * aj.z, B = -aj.w, C = -2.0f * qc;
-            const uint32_t zb = __shfl_sync(kFullMask, zbits, j);
-            const uint32_t tb = __shfl_sync(kFullMask, tbase, j);
-            const int TWj = __shfl_sync(kFullMask, TW, j);
-            const int v = (int)((uint32_t)(base + j) / n32);
-            uint32_t oj = obase + __shfl_sync(kFullMask, incl - cnt, j);
+            const uint32_t zb = __shfl_sync(kFullMask, zbits, jj);
+            const uint32_t tb = __shfl_sync(kFullMask, tbase, jj);
+            const int TWj = __shfl_sync(kFullMask, TW, jj);
+            const int v = (int)(rj / n32);
+            uint32_t oj = obase + __shfl_sync(kFullMask, incl - cnt, jj);
             const RowSpans rs = row_setup(px, py, A, B, C, vt.tile_h, vt.v[v].tiles_y);
             for (int row0 = rs.ty0; row0 <= rs.ty1; row0 += 32) {
                 const int ty = row0 + lane;
@@ -298,13 +307,12 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
                     if (e < rtotal) {
                         const uint32_t row_t0 = tb + (uint32_t)((row0 + q) * TWj + cq);
                         const uint32_t t = row_t0 + (e - rfirst);
-                        const unsigned long long key = ((unsigned long long)t << 32) | zb;
                         const uint32_t pos = oj + e;
                         if ((int64_t)pos < capacity) {
-                            keys[pos] = key;
-                            vals[pos] = (uint32_t)(base + j);
+                            keys[pos] = ((unsigned long long)t << 32) | zb;
+                            vals[pos] = rj;
                         }
-                        count_tile_digits<RB>(h, passes, key, t, row_t0, row_t0 + lq);
+                        count_tile_digits<RB>(h, passes, t, row_t0, row_t0 + lq);
                     }
                 }
                 oj += rtotal;
@@ -340,20 +348,20 @@ cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const uint32_t* tiles, uint32_t* offsets, int64_t R,
+cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
                         cudaStream_t s) {
     const int64_t num_tiles = (R + kScanTile - 1) / kScanTile;
     if (num_tiles == 0) return cudaSuccess;
-    scan_kernel<<<(unsigned)num_tiles, kScanThreads, 0, s>>>(tiles, offsets, R, scan_lookback, st,
+    scan_kernel<<<(unsigned)num_tiles, kScanThreads, 0, s>>>(tiles, perm, offsets, R, scan_lookback, st,
                                                              capacity);
     return cudaGetLastError();
 }
 
-cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* offsets,
-                             int64_t n, int64_t R, DeviceStatus* st, int64_t capacity,
-                             unsigned long long* keys, uint32_t* vals, int digit_bits, int passes,
-                             uint32_t* hist, cudaStream_t s) {
+cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* perm,
+                             const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
+                             int64_t capacity, unsigned long long* keys, uint32_t* vals, int digit_bits,
+                             int passes, uint32_t* hist, cudaStream_t s) {
     cudaError_t e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s);
     if (e != cudaSuccess || R == 0) return e;
     const int threads = 256;
@@ -361,7 +369,7 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
     const unsigned blocks = (unsigned)(want < 148 * 8 ? want : 148 * 8);
     switch (digit_bits) {
 #define SGS_DUP(RB) case RB: duplicate_kernel<RB><<<blocks, threads, 0, s>>>(vt, p.spans, p.tiles, p.rec0, \
-        p.rec1, offsets, n, R, st, capacity, keys, vals, passes, hist); break;
+        p.rec1, perm, offsets, n, R, st, capacity, keys, vals, passes, hist); break;
         SGS_DUP(4) SGS_DUP(5) SGS_DUP(6) SGS_DUP(7) SGS_DUP(8)
 #undef SGS_DUP
         default: return cudaErrorInvalidValue;
@@ -379,4 +387,14 @@ cudaError_t launch_ranges(const unsigned long long* keys, const DeviceStatus* st
     return cudaGetLastError();
 }
 
+}  // namespace sgs
+
+namespace sgs {
+cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, unsigned long long* keys,
+                               uint32_t* vals, DeviceStatus* st, cudaStream_t s) {
+    const int threads = 256;
+    const int64_t blocks = (R + threads - 1) / threads;
+    record_keys_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), threads, 0, s>>>(tiles, rec1, R, keys, vals, st);
+    return cudaGetLastError();
+}
 }  // namespace sgs

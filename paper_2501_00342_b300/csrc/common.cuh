@@ -37,6 +37,7 @@ struct DeviceStatus {
     uint32_t m_clamped;    // min(M, capacity): instances actually written
     unsigned long long m;  // exact instance count M
     uint32_t tile_counter[16];  // dynamic tile ids: [0] scan, [1..] sort passes
+    uint32_t num_records;       // R, the length of the record sort
 };
 
 // Correctly rounded single-precision operations that the compiler may not fuse or

@@ -27,14 +27,19 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStream_t s);
-cudaError_t launch_scan(const uint32_t* tiles, uint32_t* offsets, int64_t R,
+// Keys (view depth bits; 0xffffffff without instances) and ids of the record sort; also
+// stores R in st->num_records.
+cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, unsigned long long* keys,
+                               uint32_t* vals, DeviceStatus* st, cudaStream_t s);
+// Exclusive scan of tiles[perm[j]] (or tiles[j] when perm is null).
+cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
                         cudaStream_t s);
-// Also counts the radix sort's digit histograms (hist: kMaxSortPasses*256 u32, cleared here).
-cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* offsets,
-                             int64_t n, int64_t R, DeviceStatus* st, int64_t capacity,
-                             unsigned long long* keys, uint32_t* vals, int digit_bits, int passes,
-                             uint32_t* hist, cudaStream_t s);
+// Also counts the tile sort's digit histograms (hist: kMaxSortPasses*256 u32, cleared here).
+cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* perm,
+                             const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
+                             int64_t capacity, unsigned long long* keys, uint32_t* vals, int digit_bits,
+                             int passes, uint32_t* hist, cudaStream_t s);
 cudaError_t launch_ranges(const unsigned long long* keys, const DeviceStatus* st, int64_t capacity,
                           int64_t num_tiles, uint2* ranges, cudaStream_t s);
 
@@ -44,16 +49,18 @@ constexpr int kSortItems = 15;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxSortPasses = 16;
 size_t sort_lookback_entries(int64_t capacity, int digit_bits);
-// Sorts m = *m_ptr pairs (m <= capacity) on bits [0, key_bits); result in (k0,v0) if the
-// pass count is even, else in (k1,v1).  With histogram_ready the digit histograms in hist
-// were already counted (by the duplicate kernel).  hist/goff: kMaxSortPasses*256 u32 each;
-// counters: kMaxSortPasses u32 (zeroed here); lookback: sort_lookback_entries u64.
+// Sorts m = *m_ptr pairs (m <= capacity) stably on key bits [first_bit, key_bits); result in
+// (k0,v0) if the pass count is even, else in (k1,v1).  With histogram_ready the digit
+// histograms in hist were already counted (by the duplicate kernel).  hist/goff:
+// kMaxSortPasses*256 u32 each; counters: kMaxSortPasses u32 (zeroed here); lookback:
+// sort_lookback_entries u64.
 cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
-                        const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
+                        const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, int digit_bits,
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
                         unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
                         cudaEvent_t hist_end, bool histogram_ready = false);
 int sort_passes(int key_bits, int digit_bits);
+int sort_passes(int first_bit, int key_bits, int digit_bits);
 
 // (e) blend and its backward
 cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,

@@ -35,7 +35,7 @@ constexpr unsigned long long kCountMask = (1ull << 56) - 1;
 
 template <int RB>
 __global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long* __restrict__ keys,
-                                                        const uint32_t* m_ptr, int passes,
+                                                        const uint32_t* m_ptr, int passes, int first_bit,
                                                         uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
     __shared__ uint32_t h[kMaxSortPasses * RADIX];
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long
         const unsigned long long k = valid ? keys[idx] : 0ull;
         const uint32_t active = __ballot_sync(kFullMask, valid);
         for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (p * RB)) & (RADIX - 1) : RADIX;
+            const uint32_t d = valid ? (uint32_t)(k >> (first_bit + p * RB)) & (RADIX - 1) : RADIX;
             const uint32_t peers = __match_any_sync(kFullMask, d) & active;
             if (valid && (threadIdx.x & 31) == 31 - __clz(peers))
                 atomicAdd(&h[p * RADIX + d], (uint32_t)__popc(peers));
@@ -259,11 +259,11 @@ __global__ void sort_init_kernel(DeviceStatus* st, uint32_t m) {
 
 template <int RB>
 cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
-                      const uint32_t* m_ptr, int64_t capacity, int key_bits, uint32_t* hist,
+                      const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, uint32_t* hist,
                       uint32_t* goff, uint32_t* counters, unsigned long long* lookback,
                       DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready) {
     constexpr int RADIX = 1 << RB;
-    const int passes = (key_bits + RB - 1) / RB;
+    const int passes = (key_bits - first_bit + RB - 1) / RB;
     cudaError_t e;
     if (!histogram_ready && (e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s)) != cudaSuccess)
         return e;
@@ -275,7 +275,7 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
     {
         const int64_t want = (capacity + 255) / 256;
         const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
-        if (!histogram_ready) histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, hist);
+        if (!histogram_ready) histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, first_bit, hist);
         histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : RADIX, 0, s>>>(hist, goff);
     }
     if (hist_end && (e = cudaEventRecord(hist_end, s)) != cudaSuccess) return e;
@@ -289,7 +289,7 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
         unsigned long long* kout = (p & 1) ? k0 : k1;
         uint32_t* vout = (p & 1) ? v0 : v1;
         onesweep_kernel<RB><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-            kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, p * RB, p, st);
+            kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, p, st);
     }
     return cudaGetLastError();
 }
@@ -298,21 +298,25 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
 
 int sort_passes(int key_bits, int digit_bits) { return (key_bits + digit_bits - 1) / digit_bits; }
 
+int sort_passes(int first_bit, int key_bits, int digit_bits) {
+    return (key_bits - first_bit + digit_bits - 1) / digit_bits;
+}
+
 size_t sort_lookback_entries(int64_t capacity, int digit_bits) {
     return (size_t)((capacity + kSortTile - 1) / kSortTile) * ((size_t)1 << digit_bits);
 }
 
 cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
-                        const uint32_t* m_ptr, int64_t capacity, int key_bits, int digit_bits,
+                        const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, int digit_bits,
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
                         unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
                         cudaEvent_t hist_end, bool histogram_ready) {
     switch (digit_bits) {
-        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
         default: return cudaErrorInvalidValue;
     }
 }

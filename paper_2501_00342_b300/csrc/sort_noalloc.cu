@@ -76,7 +76,7 @@ extern "C" sgs_status sgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int
     // the status word, histograms, counters and look-back entries the sort reads are
     // written or cleared by launch_sort_init / launch_sort on every call
     if (sgs::launch_sort_init(st, (uint32_t)m, stream) != cudaSuccess) return SGS_ERR_CUDA;
-    if (sgs::launch_sort(k0, vals, k1, v1, &st->m_clamped, m, key_bits, digit_bits, hist, goff, counters, lb,
+    if (sgs::launch_sort(k0, vals, k1, v1, &st->m_clamped, m, 0, key_bits, digit_bits, hist, goff, counters, lb,
                          st, stream, nullptr) != cudaSuccess)
         return SGS_ERR_CUDA;
     if (sgs::sort_passes(key_bits, digit_bits) & 1)
