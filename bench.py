@@ -452,7 +452,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--tile", type=int, nargs=2, default=(16, 16))
     ap.add_argument("--batch-depth", type=int, default=256)
-    ap.add_argument("--digit-bits", type=int, default=8)
+    ap.add_argument("--digit-bits", type=int, default=9)
     ap.add_argument("--workload", default="batched", choices=("batched", "single"),
                     help="single: 1M Gaussians, one 1280x720 view (a small case for profilers)")
     ap.add_argument("--no-extras", dest="extras", action="store_false")

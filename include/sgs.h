@@ -104,7 +104,8 @@ typedef struct {
 typedef struct {
     int32_t tile_w, tile_h; /* screen tile, pixels; tile_w * tile_h in {64,128,256,512} */
     int32_t batch_depth;    /* Gaussians staged in shared memory per blend batch: 32..1024 */
-    int32_t digit_bits;     /* radix-sort digit width, 4..8 */
+    int32_t digit_bits;     /* widest radix-sort digit, 4..10: a sort of b bits takes
+                               ceil(b / digit_bits) passes of equal, narrowest width */
     int32_t memory_mode;    /* 0: backward recomputes per tile from the sorted list
                                (no per-pixel contributor lists are ever stored) */
     float bg[3];            /* background colour added as T_final * bg */
@@ -219,7 +220,8 @@ typedef enum {
 sgs_status sgs_region_info(const sgs_plan* plan, int32_t which, size_t* offset, size_t* bytes);
 
 /* Stable LSD radix sort of m (uint64 key, uint32 value) pairs in place on their low
- * key_bits bits (1..64), the same onesweep kernels sgs_bin_sort uses.  `temp` is device
+ * key_bits bits (1..64), the same onesweep kernels sgs_bin_sort uses; digit_bits (4..10)
+ * is the widest digit.  `temp` is device
  * scratch of at least sgs_sort_temp_bytes(m, key_bits, digit_bits) bytes.  Exposed for
  * tests of the sort alone. */
 sgs_status sgs_sort_temp_bytes(int64_t m, int32_t key_bits, int32_t digit_bits, size_t* bytes);

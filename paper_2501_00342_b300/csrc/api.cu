@@ -148,7 +148,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     if (B < 1 || B > SGS_MAX_VIEWS) return SGS_ERR_INVALID;
     if (!valid_tile(settings->tile_w, settings->tile_h)) return SGS_ERR_INVALID;
     if (settings->batch_depth < 32 || settings->batch_depth > 1024) return SGS_ERR_INVALID;
-    if (settings->digit_bits < 4 || settings->digit_bits > 8) return SGS_ERR_INVALID;
+    if (settings->digit_bits < kMinDigitBits || settings->digit_bits > kMaxDigitBits) return SGS_ERR_INVALID;
     if (settings->memory_mode != 0) return SGS_ERR_INVALID;
     if (instance_capacity < 0 || instance_capacity > 0xffffffffll) return SGS_ERR_INVALID;
     std::memset(plan, 0, sizeof(*plan));
@@ -204,12 +204,15 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_PIXCOUNT] = 8 * (size_t)pixels;
     sz[O_SPANS] = 64 * (size_t)R;
     sz[O_SCANLB] = 8 * (size_t)((R + kScanTile - 1) / kScanTile + 1);
-    sz[O_HIST] = sz[O_GOFF] = 4 * (size_t)kMaxSortPasses * 256;
-    sz[O_SORTLB] = 8 * sort_lookback_entries(instance_capacity, settings->digit_bits);
+    sz[O_HIST] = sz[O_GOFF] = 4 * (size_t)kHistEntries;
+    int ipasses, irb, rpasses, rrb;
+    sort_digit_plan(32, plan->key_bits, settings->digit_bits, &ipasses, &irb);
+    sort_digit_plan(0, 32, settings->digit_bits, &rpasses, &rrb);
+    sz[O_SORTLB] = 8 * sort_lookback_entries(instance_capacity, irb);
     sz[O_COUNTERS] = 4 * (size_t)kMaxSortPasses;
     sz[O_RK0] = sz[O_RK1] = 8 * (size_t)R;
     sz[O_RV0] = sz[O_RV1] = 4 * (size_t)R;
-    sz[O_RLB] = 8 * sort_lookback_entries(R, settings->digit_bits);
+    sz[O_RLB] = 8 * sort_lookback_entries(R, rrb);
     size_t off = 0;
     for (int k = 0; k < O_END; ++k) {
         plan->offsets[k] = off;
@@ -263,10 +266,11 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     // (b) counts and instances in depth order
     SGS_TRY(launch_scan(rp.tiles, perm, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));
     SGS_TRY(probe(plan, SGS_EV_SCAN_END, stream));
+    int ipasses, irb;
+    sort_digit_plan(32, plan->key_bits, plan->settings.digit_bits, &ipasses, &irb);
     SGS_TRY(launch_duplicate(vt, rp, perm, region<uint32_t>(plan, O_OFFS), plan->n, R, st, cap,
-                             region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
-                             plan->settings.digit_bits, plan->sort_passes, region<uint32_t>(plan, O_HIST),
-                             stream));
+                             region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0), irb,
+                             ipasses, region<uint32_t>(plan, O_HIST), stream));
     SGS_TRY(probe(plan, SGS_EV_DUP_END, stream));
     // (c, tile half) stable sort of the instances by tile id
     cudaEvent_t hist_end = plan->events ? plan->events[SGS_EV_HIST_END] : nullptr;
@@ -386,11 +390,13 @@ sgs_status sgs_region_info(const sgs_plan* plan, int32_t which, size_t* offset, 
 }
 
 sgs_status sgs_sort_temp_bytes(int64_t m, int32_t key_bits, int32_t digit_bits, size_t* bytes) {
-    if (!bytes || m < 0 || m > 0xffffffffll || key_bits < 1 || key_bits > 64 || digit_bits < 4 ||
-        digit_bits > 8 || sort_passes(key_bits, digit_bits) > kMaxSortPasses)
+    if (!bytes || m < 0 || m > 0xffffffffll || key_bits < 1 || key_bits > 64 || digit_bits < kMinDigitBits ||
+        digit_bits > kMaxDigitBits || sort_passes(key_bits, digit_bits) > kMaxSortPasses)
         return SGS_ERR_INVALID;
-    *bytes = 256 + align256(8 * (size_t)m) + align256(4 * (size_t)m) + 2 * align256(4 * kMaxSortPasses * 256) +
-             align256(4 * kMaxSortPasses) + align256(8 * sort_lookback_entries(m, digit_bits));
+    int passes, rb;
+    sort_digit_plan(0, key_bits, digit_bits, &passes, &rb);
+    *bytes = 256 + align256(8 * (size_t)m) + align256(4 * (size_t)m) + 2 * align256(4 * (size_t)kHistEntries) +
+             align256(4 * kMaxSortPasses) + align256(8 * sort_lookback_entries(m, rb));
     return SGS_OK;
 }
 
@@ -410,10 +416,12 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
     };
     unsigned long long* k1 = reinterpret_cast<unsigned long long*>(take(8 * (size_t)m));
     uint32_t* v1 = reinterpret_cast<uint32_t*>(take(4 * (size_t)m));
-    uint32_t* hist = reinterpret_cast<uint32_t*>(take(4 * kMaxSortPasses * 256));
-    uint32_t* goff = reinterpret_cast<uint32_t*>(take(4 * kMaxSortPasses * 256));
+    int passes, rb;
+    sort_digit_plan(0, key_bits, digit_bits, &passes, &rb);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(take(4 * (size_t)kHistEntries));
+    uint32_t* goff = reinterpret_cast<uint32_t*>(take(4 * (size_t)kHistEntries));
     uint32_t* counters = reinterpret_cast<uint32_t*>(take(4 * kMaxSortPasses));
-    unsigned long long* lb = reinterpret_cast<unsigned long long*>(take(8 * sort_lookback_entries(m, digit_bits)));
+    unsigned long long* lb = reinterpret_cast<unsigned long long*>(take(8 * sort_lookback_entries(m, rb)));
     unsigned long long* k0 = reinterpret_cast<unsigned long long*>(keys);
     SGS_TRY(launch_sort_init(st, (uint32_t)m, stream));
     SGS_TRY(launch_sort(k0, vals, k1, v1, &st->m_clamped, m, 0, key_bits, digit_bits, hist, goff, counters, lb,

@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
                                                          uint32_t* __restrict__ vals, int passes,
                                                          uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
-    __shared__ uint32_t h[kMaxSortPasses * RADIX];
+    constexpr int MAXP = (32 + RB - 1) / RB;  // passes of a tile-id sort
+    __shared__ uint32_t h[MAXP * RADIX];
     __shared__ uint4 tab_all[8][32][4];  // the row tables of each warp's 32 records
     for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) h[j] = 0;
     __syncthreads();
@@ -362,15 +363,16 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
                              const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
                              int64_t capacity, unsigned long long* keys, uint32_t* vals, int digit_bits,
                              int passes, uint32_t* hist, cudaStream_t s) {
-    cudaError_t e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s);
+    cudaError_t e = launch_fill_u32(hist, 0u, (size_t)kHistEntries, s);
     if (e != cudaSuccess || R == 0) return e;
+    if (passes > (32 + digit_bits - 1) / digit_bits) return cudaErrorInvalidValue;
     const int threads = 256;
     const int64_t want = (R + threads - 1) / threads;
     const unsigned blocks = (unsigned)(want < 148 * 8 ? want : 148 * 8);
     switch (digit_bits) {
 #define SGS_DUP(RB) case RB: duplicate_kernel<RB><<<blocks, threads, 0, s>>>(vt, p.spans, p.tiles, p.rec0, \
         p.rec1, perm, offsets, n, R, st, capacity, keys, vals, passes, hist); break;
-        SGS_DUP(4) SGS_DUP(5) SGS_DUP(6) SGS_DUP(7) SGS_DUP(8)
+        SGS_DUP(4) SGS_DUP(5) SGS_DUP(6) SGS_DUP(7) SGS_DUP(8) SGS_DUP(9) SGS_DUP(10)
 #undef SGS_DUP
         default: return cudaErrorInvalidValue;
     }

@@ -129,6 +129,30 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sums 8 values over the warp with 9 shuffles (reduce-scatter): after halving steps at
+// lane offsets 16, 8, 4 each lane holds one of the 8 values summed over 8 lanes, and two
+// butterfly steps finish the sum.  Returns the total of value ((lane >> 2) & 7), complete
+// in the lanes whose two low bits are 0.
+__device__ __forceinline__ float warp_sum8(const float v[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = b4 ? v[4 + i] : v[i], send = b4 ? v[i] : v[4 + i];
+        w[i] = keep + __shfl_xor_sync(kFullMask, send, 16);
+    }
+    float u[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = b3 ? w[2 + i] : w[i], send = b3 ? w[i] : w[2 + i];
+        u[i] = keep + __shfl_xor_sync(kFullMask, send, 8);
+    }
+    float x = (b2 ? u[1] : u[0]) + __shfl_xor_sync(kFullMask, b2 ? u[0] : u[1], 4);
+    x += __shfl_xor_sync(kFullMask, x, 2);
+    x += __shfl_xor_sync(kFullMask, x, 1);
+    return x;
+}
+
 __global__ void __launch_bounds__(512) blend_backward_kernel(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, uint32_t R32,
     const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
@@ -168,6 +192,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     const int top = (int)s_max_last;
     float acc0 = bg0, acc1 = bg1, acc2 = bg2;
     const int lane = threadIdx.x & 31;
+    const int warp_last = (int)wmax;  // no lane of this warp blends an entry at or past it
     for (int hi = top; hi > 0; hi -= batch) {
         const int lo = max(0, hi - batch);
         __syncthreads();
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
             s2[j] = rec2[id];
         }
         __syncthreads();
-        for (int k = hi - 1; k >= lo; --k) {
+        for (int k = min(hi, warp_last) - 1; k >= lo; --k) {
             const float4 a = s0[k - lo];
             const float4 b = s1[k - lo];
             float d[9];
@@ -195,7 +220,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                 contrib = power >= kSupportPower && alpha >= kAlphaMin;
                 if (contrib) {
                     const float4 c = s2[k - lo];
-                    T = T / (1.0f - alpha);
+                    T = __fdividef(T, 1.0f - alpha);
                     const float w = alpha * T;
                     d[6] = g0 * w;
                     d[7] = g1 * w;
@@ -217,14 +242,15 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                 }
             }
             if (__any_sync(kFullMask, contrib)) {
-#pragma unroll
-                for (int q = 0; q < 9; ++q) d[q] = warp_sum(d[q]);
-                if (lane == 0) {
-                    const uint32_t id = sid[k - lo];
-                    atomicAdd(grad2d + id, make_float4(d[0], d[1], d[2], d[3]));
-                    atomicAdd(grad2d + R + id, make_float4(d[4], d[5], d[6], d[7]));
-                    atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), d[8]);
+                const float s8 = warp_sum8(d, lane);
+                const float s9 = warp_sum(d[8]);
+                const uint32_t id = sid[k - lo];
+                if ((lane & 3) == 0) {  // lanes 0, 4, ..., 28 hold values 0..7
+                    const int vi = (lane >> 2) & 7;
+                    float* dst = reinterpret_cast<float*>(grad2d + (vi >> 2) * R + id) + (vi & 3);
+                    atomicAdd(dst, s8);
                 }
+                if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
             }
         }
     }

@@ -35,7 +35,8 @@ cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
                         cudaStream_t s);
-// Also counts the tile sort's digit histograms (hist: kMaxSortPasses*256 u32, cleared here).
+// Also counts the tile sort's digit histograms for digits of digit_bits bits over `passes`
+// passes (hist: kHistEntries u32, cleared here).
 cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* perm,
                              const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
                              int64_t capacity, unsigned long long* keys, uint32_t* vals, int digit_bits,
@@ -48,12 +49,19 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 15;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxSortPasses = 16;
+constexpr int kMinDigitBits = 4;
+constexpr int kMaxDigitBits = 10;
+constexpr int kHistEntries = kMaxSortPasses * (1 << kMaxDigitBits);  // hist / goff length
+// Passes and uniform digit width of a sort of key bits [first_bit, key_bits) with digits of
+// at most max_digit_bits: the fewest passes, then the narrowest width for them.
+void sort_digit_plan(int first_bit, int key_bits, int max_digit_bits, int* passes, int* digit_bits);
 size_t sort_lookback_entries(int64_t capacity, int digit_bits);
 // Sorts m = *m_ptr pairs (m <= capacity) stably on key bits [first_bit, key_bits); result in
-// (k0,v0) if the pass count is even, else in (k1,v1).  With histogram_ready the digit
-// histograms in hist were already counted (by the duplicate kernel).  hist/goff:
-// kMaxSortPasses*256 u32 each; counters: kMaxSortPasses u32 (zeroed here); lookback:
-// sort_lookback_entries u64.
+// (k0,v0) if the pass count is even, else in (k1,v1).  digit_bits is the widest digit
+// allowed (see sort_digit_plan).  With histogram_ready the digit histograms in hist were
+// already counted (by the duplicate kernel).  hist/goff: kHistEntries u32 each; counters:
+// kMaxSortPasses u32 (zeroed here); lookback: sort_lookback_entries u64 for the planned
+// digit width.
 cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
                         const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, int digit_bits,
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,

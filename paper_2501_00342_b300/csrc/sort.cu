@@ -1,12 +1,16 @@
 // Stage (c): stable LSD radix sort of (uint64 key, uint32 value) pairs, onesweep style.
 //
-//   1. one read of all keys builds the digit histograms of every pass at once;
+//   1. digit histograms of every pass at once (one read of the keys), unless the caller
+//      counted them already;
 //   2. an exclusive scan per pass turns them into global bucket offsets;
 //   3. per pass, one kernel: each CTA takes the next tile of kSortTile keys (dynamic tile
-//      id), ranks its keys by digit with warp match-any (stable: input order within
-//      the tile), publishes its per-digit counts and resolves its global per-digit
-//      offsets by decoupled look-back over the preceding tiles, then scatters through
-//      shared memory so that each digit's run leaves the CTA as contiguous stores.
+//      id, so every earlier tile is already running), ranks its keys by digit with warp
+//      match-any (stable: input order within the tile), publishes its per-digit counts
+//      and resolves its global per-digit offsets by decoupled look-back over the earlier
+//      tiles, then scatters through shared memory so that each digit's run leaves the CTA
+//      as consecutive stores.
+// Digits are 4..10 bits; a sort of n bits uses the fewest passes of at most the requested
+// width and the narrowest uniform width for that many passes (17 bits: 2 passes of 9).
 // Look-back words are 64 bits: an 8-bit tag (2p+1 aggregate, 2p+2 inclusive for pass p)
 // and a 56-bit count, so one table serves all passes of a sort after a single clear.
 #include <cuda_runtime.h>
@@ -33,12 +37,19 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 constexpr unsigned long long kCountMask = (1ull << 56) - 1;
 
+// Digit of pass p: bits [first_bit + p*RB, first_bit + p*RB + width_p) of the key, where
+// the last pass may be narrower so that no bit at or above key_bits is used.
+__host__ __device__ __forceinline__ int pass_width(int p, int RB, int first_bit, int key_bits) {
+    const int lo = first_bit + p * RB;
+    return key_bits - lo < RB ? key_bits - lo : RB;
+}
+
 template <int RB>
 __global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long* __restrict__ keys,
                                                         const uint32_t* m_ptr, int passes, int first_bit,
-                                                        uint32_t* __restrict__ hist) {
+                                                        int key_bits, uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
-    __shared__ uint32_t h[kMaxSortPasses * RADIX];
+    extern __shared__ uint32_t h[];  // [passes][RADIX]
     for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) h[j] = 0;
     __syncthreads();
     const uint32_t m = *m_ptr;
@@ -49,7 +60,8 @@ __global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long
         const unsigned long long k = valid ? keys[idx] : 0ull;
         const uint32_t active = __ballot_sync(kFullMask, valid);
         for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (first_bit + p * RB)) & (RADIX - 1) : RADIX;
+            const uint32_t mask = (1u << pass_width(p, RB, first_bit, key_bits)) - 1u;
+            const uint32_t d = valid ? (uint32_t)(k >> (first_bit + p * RB)) & mask : RADIX;
             const uint32_t peers = __match_any_sync(kFullMask, d) & active;
             if (valid && (threadIdx.x & 31) == 31 - __clz(peers))
                 atomicAdd(&h[p * RADIX + d], (uint32_t)__popc(peers));
@@ -66,10 +78,9 @@ __global__ void histogram_scan_kernel(const uint32_t* __restrict__ hist, uint32_
     constexpr int RADIX = 1 << RB;
     __shared__ uint32_t s[RADIX];
     const int p = blockIdx.x;
-    const int d = threadIdx.x;
-    if (d < RADIX) s[d] = hist[p * RADIX + d];
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) s[d] = hist[p * RADIX + d];
     __syncthreads();
-    if (d == 0) {
+    if (threadIdx.x == 0) {
         uint32_t acc = 0;
         for (int j = 0; j < RADIX; ++j) {
             const uint32_t c = s[j];
@@ -78,16 +89,20 @@ __global__ void histogram_scan_kernel(const uint32_t* __restrict__ hist, uint32_
         }
     }
     __syncthreads();
-    if (d < RADIX) goff[p * RADIX + d] = s[d];
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) goff[p * RADIX + d] = s[d];
 }
 
 template <int RB>
 struct OnesweepSmem {
     static constexpr int RADIX = 1 << RB;
     static constexpr int WARPS = kSortThreads / 32;
-    unsigned long long keys[kSortTile];
-    uint32_t vals[kSortTile];
-    uint32_t warp_hist[WARPS][RADIX + 1];  // +1: sentinel bucket of the ragged tail
+    union {
+        uint32_t warp_hist[WARPS][RADIX + 1];  // ranking; +1: sentinel bucket of the ragged tail
+        struct {
+            unsigned long long keys[kSortTile];  // staging, after the positions are in registers
+            uint32_t vals[kSortTile];
+        } stage;
+    } u;
     uint32_t digit_start[RADIX];
     uint32_t gbase[RADIX];
     uint32_t wsum[WARPS];
@@ -95,19 +110,20 @@ struct OnesweepSmem {
 };
 
 template <int RB>
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
     unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* m_ptr,
     const uint32_t* __restrict__ goff, unsigned long long* lookback, uint32_t* counter, int shift,
-    int pass, DeviceStatus* st) {
+    int width, int pass, DeviceStatus* st) {
     constexpr int RADIX = 1 << RB;
     constexpr int WARPS = kSortThreads / 32;
+    constexpr int DPT = (RADIX + kSortThreads - 1) / kSortThreads;  // digits per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem<RB>& sm = *reinterpret_cast<OnesweepSmem<RB>*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t dmask = (1u << width) - 1u;
     if (threadIdx.x == 0) sm.tile = atomicAdd(counter, 1u);
-    for (int j = threadIdx.x; j < WARPS * (RADIX + 1); j += kSortThreads)
-        (&sm.warp_hist[0][0])[j] = 0;
+    for (int j = threadIdx.x; j < WARPS * (RADIX + 1); j += kSortThreads) (&sm.u.warp_hist[0][0])[j] = 0;
     __syncthreads();
     const uint32_t m = *m_ptr;
     const uint32_t tile = sm.tile;
@@ -115,57 +131,54 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     if (tile_start >= m) return;  // whole CTA: nothing in this tile
     const uint32_t count = (uint32_t)(m - tile_start < (uint64_t)kSortTile ? m - tile_start : kSortTile);
 
-    // load warp-striped: item k of lane l of warp w is element w*32*ITEMS + k*32 + l
+    // load keys warp-striped: item k of lane l of warp w is element w*32*ITEMS + k*32 + l
     unsigned long long key[kSortItems];
-    uint32_t val[kSortItems];
     uint32_t rank[kSortItems];
-    uint32_t dig[kSortItems];
     const uint32_t wbase = warp * 32 * kSortItems;
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t e = wbase + k * 32 + lane;
-        if (e < count) {
-            key[k] = kin[tile_start + e];
-            val[k] = vin[tile_start + e];
-            dig[k] = (uint32_t)(key[k] >> shift) & (RADIX - 1);
-        } else {
-            key[k] = 0;
-            val[k] = 0;
-            dig[k] = RADIX;
-        }
+        key[k] = e < count ? kin[tile_start + e] : 0ull;
     }
-    // stable warp-level ranking
+    // stable warp-level ranking (items past the end go to the sentinel bucket RADIX)
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        const uint32_t peers = __match_any_sync(kFullMask, dig[k]);
+        const uint32_t e = wbase + k * 32 + lane;
+        const uint32_t d = e < count ? (uint32_t)(key[k] >> shift) & dmask : RADIX;
+        const uint32_t peers = __match_any_sync(kFullMask, d);
         const int leader = 31 - __clz(peers);
         uint32_t prior = 0;
         if (lane == leader) {
-            prior = sm.warp_hist[warp][dig[k]];
-            sm.warp_hist[warp][dig[k]] = prior + __popc(peers);
+            prior = sm.u.warp_hist[warp][d];
+            sm.u.warp_hist[warp][d] = prior + __popc(peers);
         }
         prior = __shfl_sync(kFullMask, prior, leader);
         rank[k] = prior + __popc(peers & lt);
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps and the tile total
-    uint32_t total = 0;
-    if (threadIdx.x < RADIX) {
-        const int d = threadIdx.x;
-        uint32_t acc = 0;
+    // per digit: exclusive prefix over warps (in place) and the tile total
+    uint32_t total[DPT];
+    uint32_t tsum = 0;
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-            const uint32_t c = sm.warp_hist[w][d];
-            sm.warp_hist[w][d] = acc;
-            acc += c;
+    for (int i = 0; i < DPT; ++i) {
+        const int d = threadIdx.x * DPT + i;
+        uint32_t acc = 0;
+        if (d < RADIX) {
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) {
+                const uint32_t c = sm.u.warp_hist[w][d];
+                sm.u.warp_hist[w][d] = acc;
+                acc += c;
+            }
         }
-        total = acc;
+        total[i] = acc;
+        tsum += acc;
     }
-    // exclusive scan of the digit totals over the CTA -> CTA-local digit start
+    // exclusive scan of the digit totals over the CTA -> CTA-local digit starts
     {
-        uint32_t x = total;
+        uint32_t x = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFullMask, x, o);
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
         if (lane == 31) sm.wsum[warp] = x;
         __syncthreads();
         if (warp == 0) {
-            uint32_t w = lane < WARPS ? sm.wsum[lane] : 0u;
+            const uint32_t w = lane < WARPS ? sm.wsum[lane] : 0u;
             uint32_t inc = w;
 #pragma unroll
             for (int o = 1; o < WARPS; o <<= 1) {
@@ -184,19 +197,29 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
             if (lane < WARPS) sm.wsum[lane] = inc - w;
         }
         __syncthreads();
-        if (threadIdx.x < RADIX) sm.digit_start[threadIdx.x] = x - total + sm.wsum[warp];
+        uint32_t run = x - tsum + sm.wsum[warp];
+#pragma unroll
+        for (int i = 0; i < DPT; ++i) {
+            const int d = threadIdx.x * DPT + i;
+            if (d < RADIX) sm.digit_start[d] = run;
+            run += total[i];
+        }
     }
-    // publish this tile's per-digit counts, then look back for the global prefix
-    if (threadIdx.x < RADIX) {
-        const int d = threadIdx.x;
-        unsigned long long* row = lookback + (size_t)tile * RADIX;
-        const unsigned long long tag_agg = (unsigned long long)(2 * pass + 1) << 56;
-        const unsigned long long tag_inc = (unsigned long long)(2 * pass + 2) << 56;
+    // publish this tile's per-digit counts, then look back for the global prefixes
+    const unsigned long long tag_agg = (unsigned long long)(2 * pass + 1) << 56;
+    const unsigned long long tag_inc = (unsigned long long)(2 * pass + 2) << 56;
+    unsigned long long* row = lookback + (size_t)tile * RADIX;
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int d = threadIdx.x * DPT + i;
+        if (d < RADIX) st_relaxed(row + d, tile == 0 ? (tag_inc | (goff[d] + total[i])) : (tag_agg | total[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int d = threadIdx.x * DPT + i;
+        if (d >= RADIX) continue;
         unsigned long long prefix = goff[d];
-        if (tile == 0) {
-            st_relaxed(row + d, tag_inc | (prefix + total));
-        } else {
-            st_relaxed(row + d, tag_agg | total);
+        if (tile != 0) {
             int64_t j = (int64_t)tile - 1;
             uint32_t spins = 0;
             unsigned long long acc = 0;
@@ -215,28 +238,35 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
                 }
             }
             prefix = acc;  // the inclusive prefix of a tile includes goff[d]
-            st_relaxed(row + d, tag_inc | (prefix + total));
+            st_relaxed(row + d, tag_inc | (prefix + total[i]));
         }
         sm.gbase[d] = (uint32_t)prefix;
     }
     __syncthreads();
-    // place keys in CTA-local sorted order
+    // CTA-local sorted position of every item (the warp histograms are read for the last
+    // time here; the staging buffer that aliases them is written after the barrier)
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        if (dig[k] < RADIX) {
-            const uint32_t pos = sm.digit_start[dig[k]] + sm.warp_hist[warp][dig[k]] + rank[k];
-            sm.keys[pos] = key[k];
-            sm.vals[pos] = val[k];
+        const uint32_t e = wbase + k * 32 + lane;
+        const uint32_t d = (uint32_t)(key[k] >> shift) & dmask;
+        rank[k] = e < count ? sm.digit_start[d] + sm.u.warp_hist[warp][d] + rank[k] : 0xffffffffu;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        if (rank[k] != 0xffffffffu) {
+            sm.u.stage.keys[rank[k]] = key[k];
+            sm.u.stage.vals[rank[k]] = vin[tile_start + wbase + k * 32 + lane];
         }
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
-        const unsigned long long kk = sm.keys[j];
-        const uint32_t d = (uint32_t)(kk >> shift) & (RADIX - 1);
+        const unsigned long long kk = sm.u.stage.keys[j];
+        const uint32_t d = (uint32_t)(kk >> shift) & dmask;
         const uint32_t dest = sm.gbase[d] + (j - sm.digit_start[d]);
         if (dest < m) {
             kout[dest] = kk;
-            vout[dest] = sm.vals[j];
+            vout[dest] = sm.u.stage.vals[j];
         }
     }
 }
@@ -265,19 +295,26 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
     constexpr int RADIX = 1 << RB;
     const int passes = (key_bits - first_bit + RB - 1) / RB;
     cudaError_t e;
-    if (!histogram_ready && (e = launch_fill_u32(hist, 0u, (size_t)kMaxSortPasses * 256, s)) != cudaSuccess)
+    if (!histogram_ready && (e = launch_fill_u32(hist, 0u, (size_t)passes * RADIX, s)) != cudaSuccess)
         return e;
     if ((e = launch_fill_u32(counters, 0u, kMaxSortPasses, s)) != cudaSuccess) return e;
     const size_t tiles = (size_t)((capacity + kSortTile - 1) / kSortTile);
     if ((e = launch_fill_u32(reinterpret_cast<uint32_t*>(lookback), 0u, tiles * RADIX * 2, s)) != cudaSuccess)
         return e;
-    if (capacity == 0 || tiles == 0) return cudaSuccess;
-    {
+    if (capacity == 0 || tiles == 0 || passes <= 0) {
+        if (hist_end) return cudaEventRecord(hist_end, s);
+        return cudaSuccess;
+    }
+    if (!histogram_ready) {
         const int64_t want = (capacity + 255) / 256;
         const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
-        if (!histogram_ready) histogram_kernel<RB><<<blocks, 256, 0, s>>>(k0, m_ptr, passes, first_bit, hist);
-        histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : RADIX, 0, s>>>(hist, goff);
+        const size_t hs = (size_t)passes * RADIX * sizeof(uint32_t);
+        if ((e = cudaFuncSetAttribute(histogram_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)hs)) != cudaSuccess)
+            return e;
+        histogram_kernel<RB><<<blocks, 256, hs, s>>>(k0, m_ptr, passes, first_bit, key_bits, hist);
     }
+    histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : (RADIX > 1024 ? 1024 : RADIX), 0, s>>>(hist, goff);
     if (hist_end && (e = cudaEventRecord(hist_end, s)) != cudaSuccess) return e;
     const size_t smem = sizeof(OnesweepSmem<RB>);
     if ((e = cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -289,17 +326,29 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
         unsigned long long* kout = (p & 1) ? k0 : k1;
         uint32_t* vout = (p & 1) ? v0 : v1;
         onesweep_kernel<RB><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-            kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, p, st);
+            kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, first_bit + p * RB,
+            pass_width(p, RB, first_bit, key_bits), p, st);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int sort_passes(int key_bits, int digit_bits) { return (key_bits + digit_bits - 1) / digit_bits; }
+void sort_digit_plan(int first_bit, int key_bits, int max_digit_bits, int* passes, int* digit_bits) {
+    const int nbits = key_bits - first_bit;
+    const int p = nbits <= 0 ? 0 : (nbits + max_digit_bits - 1) / max_digit_bits;
+    int rb = p == 0 ? kMinDigitBits : (nbits + p - 1) / p;
+    if (rb < kMinDigitBits) rb = kMinDigitBits;
+    *passes = p;
+    *digit_bits = rb;
+}
+
+int sort_passes(int key_bits, int digit_bits) { return sort_passes(0, key_bits, digit_bits); }
 
 int sort_passes(int first_bit, int key_bits, int digit_bits) {
-    return (key_bits - first_bit + digit_bits - 1) / digit_bits;
+    int p, rb;
+    sort_digit_plan(first_bit, key_bits, digit_bits, &p, &rb);
+    return p;
 }
 
 size_t sort_lookback_entries(int64_t capacity, int digit_bits) {
@@ -311,12 +360,15 @@ cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
                         unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
                         cudaEvent_t hist_end, bool histogram_ready) {
-    switch (digit_bits) {
-        case 4: return sort_impl<4>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 5: return sort_impl<5>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 6: return sort_impl<6>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 7: return sort_impl<7>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
-        case 8: return sort_impl<8>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, lookback, st, s, hist_end, histogram_ready);
+    int passes, rb;
+    sort_digit_plan(first_bit, key_bits, digit_bits, &passes, &rb);
+    switch (rb) {
+#define SGS_SORT(RB)                                                                                        \
+    case RB:                                                                                                \
+        return sort_impl<RB>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters,  \
+                             lookback, st, s, hist_end, histogram_ready);
+        SGS_SORT(4) SGS_SORT(5) SGS_SORT(6) SGS_SORT(7) SGS_SORT(8) SGS_SORT(9) SGS_SORT(10)
+#undef SGS_SORT
         default: return cudaErrorInvalidValue;
     }
 }

@@ -20,7 +20,7 @@ class RenderSettings:
     tile_w: int = 16
     tile_h: int = 16
     batch_depth: int = 256
-    digit_bits: int = 8
+    digit_bits: int = 9
     bg: tuple = (0.0, 0.0, 0.0)
 
     def struct(self) -> B.Settings:

@@ -55,6 +55,8 @@ def test_plan_sizes_and_key_bits():
     assert plan.key_bits == 32 + (tiles - 1).bit_length()
     # the record sort orders the depth half; the instance sort takes the tile bits only
     assert plan.sort_passes == -(-(plan.key_bits - 32) // 8)
+    plan9, _ = B.workspace_size(_g(1000), cams, _s(digit=9), 50_000)
+    assert plan9.sort_passes == -(-(plan9.key_bits - 32) // 9)
     assert [plan.pixel_base[v] for v in range(4)] == [0, 1280 * 720, 1280 * 720 + 640 * 360,
                                                       1280 * 720 + 640 * 360 + 1920 * 1080]
     assert nbytes % 256 == 0 and nbytes == plan.workspace_bytes
@@ -66,7 +68,7 @@ def test_plan_sizes_and_key_bits():
 
 @pytest.mark.parametrize("bad", [
     dict(tw=16, th=12), dict(tw=0, th=16), dict(batch=16), dict(batch=4096), dict(digit=3),
-    dict(digit=9),
+    dict(digit=11),
 ])
 def test_invalid_settings_rejected(bad):
     cams = [I.look_at((0, 0, 4), (0, 0, 0), 64, 64, 60)]
@@ -102,6 +104,8 @@ def test_sort_temp_bytes_validation():
         B.sort_temp_bytes(1000, 65, 8)
     with pytest.raises(B.SgsError):
         B.sort_temp_bytes(1000, 64, 3)
+    with pytest.raises(B.SgsError):
+        B.sort_temp_bytes(1000, 64, 11)
 
 
 def test_status_strings():

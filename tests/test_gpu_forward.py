@@ -117,7 +117,7 @@ def test_batch_depth_does_not_change_image(batch):
     assert torch.equal(img, ref_img)
 
 
-@pytest.mark.parametrize("digit", [4, 5, 6, 7])
+@pytest.mark.parametrize("digit", [4, 5, 6, 7, 9, 10])
 def test_digit_width_gives_identical_sort(digit):
     sc, cams = I.workload(0)
     rast, _, img, _ = _run(sc, cams, RenderSettings(digit_bits=digit))

@@ -51,7 +51,7 @@ def test_sort_cases(case, m):
     assert (ks == ek).all() and (vs == ev).all()
 
 
-@pytest.mark.parametrize("digit", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("digit", [4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("key_bits", [1, 13, 32, 44, 57])
 def test_sort_digit_widths(digit, key_bits):
     rng = np.random.default_rng(digit * 100 + key_bits)
