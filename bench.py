@@ -16,6 +16,7 @@ path); times are the max over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -128,15 +129,22 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     settings = RenderSettings(tile_w=args.tile[0], tile_h=args.tile[1], batch_depth=args.batch_depth,
                               digit_bits=args.digit_bits)
+    from paper_2501_00342_b300.autotune import autotune
     if args.workload == "single":  # small profiling case: 1 M Gaussians, one 1280x720 view
         scene, cams = I.workload(1, sh_degree=1, num_lobes=4)
         cams = cams[:1]
+    elif args.workload == "medium":  # profiling case: the 3 M scene, two 1920x1080 views
+        scene, cams = I.workload(3)
+        cams = [c for c in cams if c.width == 1920][:2]
     else:
         scene, cams = I.workload(3)
     n, nv = scene.n, len(cams)
     model = GaussianModel.from_scene(scene)
     targets = I.target_images(cams, config=3)
     target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets])).cuda()
+    tune_log = []
+    if args.autotune:
+        settings = autotune(model, cams, base=settings, steps=2, log=tune_log)
     rast = Rasterizer(model, cams, settings)
     img = torch.empty(3 * rast.num_pixels, device="cuda")
     rast.forward(model, out_rgb=img, sync=True)  # sizes the instance capacity
@@ -152,34 +160,57 @@ def run_gpu(args):
 
     step(sync=True)
     assert rast.num_instances == M and rast.device_status() == 0
+    names = B.EVENTS
+
+    def probe_events():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in names]
+        for e in evs:  # creates the driver events before they are handed to the library
+            e.record(stream)
+        return evs, C_void_p_array(len(names))(*[e.cuda_event for e in evs])
+
+    # eager run of the same step (also the fallback source of the per-kernel times)
+    eager_evs, handles = probe_events()
+    B.set_events(rast.plan, handles)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-
-    # per-kernel probe events, one set per timed step
-    names = B.EVENTS
-    ev_sets, handle_sets = [], []
-    for _ in range(args.steps):
-        evs = [torch.cuda.Event(enable_timing=True) for _ in names]
-        for e in evs:
-            e.record(stream)
-        torch.cuda.synchronize()
-        ev_sets.append(evs)
-        handle_sets.append((C_void_p_array(len(names)))(*[e.cuda_event for e in evs]))
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = t0.elapsed_time(t1) / args.steps
+
+    # the headline: one batched step captured as a CUDA graph (probe events become graph
+    # nodes), replayed K times
+    graph_evs, handles = probe_events()
+    B.set_events(rast.plan, handles)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph(keep_graph=True)
+    with torch.cuda.graph(graph):
+        graph_loss = step()
+    B.set_events(rast.plan, None)
+    kernel_nodes = _graph_kernel_nodes(graph.raw_cuda_graph())
+    graph.instantiate()
+    for _ in range(args.warmup):
+        graph.replay()
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t0.record(stream)
-        for k in range(args.steps):
-            B.set_events(rast.plan, handle_sets[k])
-            step()
+        for _ in range(args.steps):
+            graph.replay()
         t1.record(stream)
         torch.cuda.synchronize()
-    B.set_events(rast.plan, None)
     barrier()
     ms = max_over_ranks(t0.elapsed_time(t1) / args.steps)
     value = world * nv / (ms / 1e3)
+    try:  # the probe events of the last replay of the timed loop
+        graph_evs[0].elapsed_time(graph_evs[1])
+        ev_sets, stage_source = [graph_evs], "CUDA events inside the graph, last timed replay"
+    except RuntimeError:
+        ev_sets, stage_source = [eager_evs], "CUDA events of the last eager step"
 
     def span(a, b):
         ia, ib = names.index(a), names.index(b)
@@ -211,12 +242,12 @@ def run_gpu(args):
     kernels = {
         "preprocess_kernel": dict(ms=stages["preprocess"], launches=1, bound="hbm",
                                   work=n * p_bytes + visible * 48 + n * nv * 12),
-        "onesweep_kernel": dict(ms=stages["sort_onesweep_all_passes"] / P, launches=P, bound="hbm",
-                                work=24 * M),
+        "onesweep_kernel": dict(ms=stages["sort_onesweep_all_passes"] / max(P, 1), launches=P, bound="hbm",
+                                work=16 * M),  # u32 tile id + u32 record id, read and written
         "blend_kernel": dict(ms=stages["blend"], launches=1, bound="alu",
                              work=8 * e_eval + 11 * e_contrib),
         "blend_backward_kernel": dict(ms=stages["backward_blend"], launches=1, bound="alu",
-                                      work=None),
+                                      work=8 * e_eval + 40 * e_contrib),
         "preprocess_backward_kernel": dict(ms=stages["backward_preprocess"], launches=1, bound="hbm",
                                            work=2 * n * p_bytes + visible * 48),
     }
@@ -243,19 +274,27 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; stands in for Mip-NeRF360/T&T/DB)",
-        "config": {"workload": WORKLOAD if args.workload == "batched" else
-                   "profiling case: 1M clustered Gaussians, SH-1 + 4 SG, one 1280x720 view, fwd+bwd",
+        "config": {"workload": {"batched": WORKLOAD,
+                                "single": "profiling case: 1M clustered Gaussians, SH-1 + 4 SG, one 1280x720 view",
+                                "medium": "profiling case: 3M clustered Gaussians, SH-1 + 4 SG, two 1920x1080 views",
+                                }[args.workload],
                    "gaussians": n, "views": nv,
                    "resolutions": [[c.width, c.height] for c in cams], "pixels": int(rast.num_pixels),
                    "instances": M, "sort_passes": P, "key_bits": int(rast.plan.key_bits),
-                   "tile": list(args.tile), "batch_depth": args.batch_depth, "digit_bits": args.digit_bits,
+                   "tile": [settings.tile_w, settings.tile_h], "batch_depth": settings.batch_depth,
+                   "digit_bits": settings.digit_bits,
                    "l2": f"inputs larger than L2: {n * p_bytes / 1e6:.0f} MB parameters, "
                          f"{rast.nbytes / 1e9:.2f} GB workspace",
                    "parallelism": f"view batches per rank x{world}"},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "blend_evaluations": e_eval, "blend_contributions": e_contrib, "visible_records": visible,
         "roofline": dominant, "roofline_all": roofs,
-        "gpu_launches": (19 + P) * args.steps,
+        "gpu_launches": None if kernel_nodes is None else kernel_nodes * args.steps,
+        "kernels_per_step": kernel_nodes, "cuda_graph": True, "eager_ms_per_step": round(eager_ms, 4),
+        "stage_timing": stage_source,
+        "autotune": {"chosen": {k: v for k, v in dataclasses.asdict(settings).items() if k != "bg"},
+                     "trials": [dict({k: v for k, v in t["settings"].items() if k != "bg"}, ms=round(t["ms"], 3))
+                                for t in tune_log]},
         "clocks": clk.summary(),
     }
 
@@ -323,8 +362,8 @@ def run_gpu(args):
         fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
         out["render_fps"] = fps
 
-    # ---- end to end through the public API: host (pinned) parameters and targets in,
-    # loss out, every step
+    # ---- end to end: host (pinned) parameters and targets in, loss out, every step, around
+    # the same captured step
     host_planes = {p: (None if t is None else t.cpu().pin_memory()) for p, t in model.planes.items()}
     host_target = target.cpu().pin_memory()
     h2d = sum(t.numel() * 4 for t in host_planes.values() if t is not None) + host_target.numel() * 4
@@ -335,8 +374,8 @@ def run_gpu(args):
             if t is not None:
                 model.planes[p].copy_(t, non_blocking=True)
         target.copy_(host_target, non_blocking=True)
-        loss = step()
-        loss_host.copy_(loss, non_blocking=True)
+        graph.replay()
+        loss_host.copy_(graph_loss, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -357,6 +396,19 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def _graph_kernel_nodes(raw_graph):
+    """Kernel nodes of a captured CUDA graph (every kernel the step launches)."""
+    try:
+        from cuda.bindings import runtime as rt
+        g = rt.cudaGraph_t(init_value=raw_graph)
+        err, _, count = rt.cudaGraphGetNodes(g, 0)
+        err, nodes, count = rt.cudaGraphGetNodes(g, count)
+        kinds = [rt.cudaGraphNodeGetType(nd)[1] for nd in nodes[:count]]
+        return sum(1 for k in kinds if k == rt.cudaGraphNodeType.cudaGraphNodeTypeKernel)
+    except Exception:
+        return None
 
 
 def C_void_p_array(k):
@@ -453,10 +505,12 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=(16, 16))
     ap.add_argument("--batch-depth", type=int, default=256)
     ap.add_argument("--digit-bits", type=int, default=9)
-    ap.add_argument("--workload", default="batched", choices=("batched", "single"),
-                    help="single: 1M Gaussians, one 1280x720 view (a small case for profilers)")
+    ap.add_argument("--workload", default="batched", choices=("batched", "single", "medium"),
+                    help="single: 1M Gaussians, one 1280x720 view; medium: the 3M scene, two "
+                         "1920x1080 views (smaller cases for profilers)")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -8,7 +8,8 @@
  * (Eq. 4-9).  The hot path has five stages, each a hand-written CUDA kernel:
  *   (a) per-Gaussian preprocess: EWA projection to a 2D conic, 3-sigma radius, tile
  *       rectangle, SH+SG colour                                       -> sgs_preprocess
- *   (b) tile|depth key duplication, (c) LSD radix sort of the 64-bit keys,
+ *   (b) tile|depth key duplication, (c) LSD radix sort of the 64-bit keys (its depth
+ *       half as a sort of the records, its tile half over the instances),
  *   (d) per-tile range identification                                 -> sgs_bin_sort
  *   (e) front-to-back alpha blending per pixel                        -> sgs_render
  * and a hand-written backward pass                                    -> sgs_render_backward
@@ -169,9 +170,11 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
 sgs_status sgs_preprocess(sgs_plan* plan, const sgs_gaussians* g, void* workspace,
                           size_t ws_bytes, cudaStream_t stream);
 
-/* Stages (b)-(d): exclusive scan of tiles touched, duplication of
- * (global tile id << 32 | float bits of view depth, record id) pairs, stable LSD radix
- * sort on the low plan->key_bits bits, per-tile [start, end) ranges.  With
+/* Stages (b)-(d): the (global tile id << 32 | float bits of view depth, record id) pairs in
+ * the order of a stable LSD radix sort of the keys, and per-tile [start, end) ranges.  The
+ * sort is split: the records are sorted by depth (all instances of a record share its
+ * depth), their instances are written in that order (exclusive scan of tiles touched, then
+ * duplication), and a second stable sort orders the instances by tile id.  With
  * num_instances != NULL the call synchronises `stream`, stores the instance count M
  * and returns SGS_ERR_CAPACITY if M > capacity (then nothing past the scan ran
  * correctly).  With NULL it does not synchronise (graph capture); overflow is then
@@ -203,10 +206,12 @@ typedef enum {
     SGS_REGION_RECT = 4,    /* uint2[R]:  x0 | y0 << 16, x1 | y1 << 16 (0,0 if culled) */
     SGS_REGION_TILES = 5,   /* uint32[R]: tiles touched (0 if culled) */
     SGS_REGION_OFFSETS = 6, /* uint32[R]: exclusive scan of TILES */
-    SGS_REGION_KEYS = 7,    /* uint64[capacity]: sorted keys after sgs_bin_sort */
+    SGS_REGION_KEYS = 7,    /* uint32[capacity]: global tile id of each sorted instance; the
+                               full key is (tile id << 32) | float bits of the record's depth
+                               (REC1.z of the record in VALS) */
     SGS_REGION_VALS = 8,    /* uint32[capacity]: sorted record ids */
-    SGS_REGION_KEYS_IN = 9, /* uint64[capacity]: keys before the sort (clobbered by it
-                               when the pass count is even) */
+    SGS_REGION_KEYS_IN = 9, /* uint32[capacity]: tile ids before the tile sort, in the order
+                               of the depth-sorted records (a ping-pong buffer of the sort) */
     SGS_REGION_VALS_IN = 10,
     SGS_REGION_RANGES = 11, /* uint2[num_tiles]: [start, end) per global tile */
     SGS_REGION_PIX_T = 12,  /* float[num_pixels]: final transmittance */
@@ -256,6 +261,21 @@ sgs_status sgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t m, int
  * target) / count (sign(0) = 0).  Used for the differentiable training step. */
 sgs_status sgs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
                        float* dL_dimg, cudaStream_t stream);
+
+/* Failure-detection self-test of the bounded device-side waits; the paper has no
+ * counterpart.  The scan and the radix sort find each tile's prefix by decoupled look-back,
+ * polling a predecessor's 8-byte slot until it is published; every such wait gives up
+ * after a fixed number of polls (about a second of GPU time) and sets SGS_ERR_TIMEOUT
+ * instead of hanging.  This call runs that same wait once, on one GPU thread, over
+ * `num_slots` caller-owned device slots, walking back from slots[num_slots - 1] to
+ * slots[0]; a slot is (flag << 62) | value with flag 1 = aggregate (add, keep walking),
+ * 2 = inclusive prefix (add, stop), anything else = not yet published (poll again).
+ *   sum    device uint64: the sum found (partial after a timeout)
+ *   status device int32: SGS_OK, or SGS_ERR_TIMEOUT when a slot was never published
+ * The kernel always returns, so the context stays usable.  Arguments are checked on the
+ * host (SGS_ERR_INVALID for num_slots < 0 or a null pointer); asynchronous on `stream`. */
+sgs_status sgs_selftest_lookback(const uint64_t* slots, int64_t num_slots, uint64_t* sum,
+                                 int32_t* status, cudaStream_t stream);
 
 const char* sgs_status_string(sgs_status s);
 

@@ -27,7 +27,7 @@ REGION = dict(STATUS=0, REC0=1, REC1=2, REC2=3, RECT=4, TILES=5, OFFSETS=6, KEYS
 EXPORTS = ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
            "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
            "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss", "sgs_status_string",
-           "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc")
+           "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc", "sgs_selftest_lookback")
 
 SORT_NOALLOC_MAX_PAIRS = 1 << 18
 
@@ -107,6 +107,8 @@ def lib():
         L.sgs_set_events.restype = st
         L.sgs_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, i32, vp]
         L.sgs_sort_pairs_noalloc.restype = st
+        L.sgs_selftest_lookback.argtypes = [vp, i64, vp, vp, vp]
+        L.sgs_selftest_lookback.restype = st
         for f in ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
                   "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
                   "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss"):
@@ -223,6 +225,16 @@ def sort_pairs_noalloc(keys_ptr, vals_ptr, m, key_bits, digit_bits, stream):
     """In-place sort with the library's own fixed scratch (no allocation anywhere)."""
     check("sgs_sort_pairs_noalloc",
           lib().sgs_sort_pairs_noalloc(keys_ptr, vals_ptr, int(m), int(key_bits), int(digit_bits), stream))
+
+
+# slot flags of sgs_selftest_lookback
+LOOKBACK_AGGREGATE = 1 << 62
+LOOKBACK_INCLUSIVE = 2 << 62
+
+
+def selftest_lookback(slots_ptr, num_slots, sum_ptr, status_ptr, stream):
+    check("sgs_selftest_lookback", lib().sgs_selftest_lookback(slots_ptr, int(num_slots), sum_ptr,
+                                                               status_ptr, stream))
 
 
 def l1_loss(img_ptr, target_ptr, count, loss_ptr, grad_ptr, stream):

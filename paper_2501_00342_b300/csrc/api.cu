@@ -109,7 +109,7 @@ sgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SGS_OK : SGS_E
 
 cudaError_t probe(const sgs_plan* p, int k, cudaStream_t s) {
     if (!p->events || !p->events[k]) return cudaSuccess;
-    return cudaEventRecord(p->events[k], s);
+    return record_probe(p->events[k], s);
 }
 
 #define SGS_TRY(expr)                                  \
@@ -187,7 +187,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     plan->key_bits = 32 + ceil_log2(tiles < 1 ? 1 : tiles);
     // the depth half of the key is ordered by the record sort; the instance sort takes the
     // tile bits only
-    plan->sort_passes = sort_passes(32, plan->key_bits, settings->digit_bits);
+    plan->sort_passes = sort_passes(0, plan->key_bits - 32, settings->digit_bits);
     if (plan->sort_passes > kMaxSortPasses) return SGS_ERR_INVALID;
 
     size_t sz[O_END];
@@ -196,7 +196,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_REC0] = sz[O_REC1] = sz[O_REC2] = 16 * (size_t)R;
     sz[O_RECT] = 8 * (size_t)R;
     sz[O_TILES] = sz[O_OFFS] = 4 * (size_t)R;
-    sz[O_K0] = sz[O_K1] = 8 * cap;
+    sz[O_K0] = sz[O_K1] = 4 * cap;  // tile ids
     sz[O_V0] = sz[O_V1] = 4 * cap;
     sz[O_RANGES] = 8 * (size_t)tiles;
     sz[O_PIXT] = sz[O_PIXLAST] = 4 * (size_t)pixels;
@@ -206,11 +206,11 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_SCANLB] = 8 * (size_t)((R + kScanTile - 1) / kScanTile + 1);
     sz[O_HIST] = sz[O_GOFF] = 4 * (size_t)kHistEntries;
     int ipasses, irb, rpasses, rrb;
-    sort_digit_plan(32, plan->key_bits, settings->digit_bits, &ipasses, &irb);
+    sort_digit_plan(0, plan->key_bits - 32, settings->digit_bits, &ipasses, &irb);
     sort_digit_plan(0, 32, settings->digit_bits, &rpasses, &rrb);
     sz[O_SORTLB] = 8 * sort_lookback_entries(instance_capacity, irb);
     sz[O_COUNTERS] = 4 * (size_t)kMaxSortPasses;
-    sz[O_RK0] = sz[O_RK1] = 8 * (size_t)R;
+    sz[O_RK0] = sz[O_RK1] = 4 * (size_t)R;  // depth bits
     sz[O_RV0] = sz[O_RV1] = 4 * (size_t)R;
     sz[O_RLB] = 8 * sort_lookback_entries(R, rrb);
     size_t off = 0;
@@ -254,11 +254,11 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
                             2 * (size_t)((R + kScanTile - 1) / kScanTile + 1), stream));
     // (c, depth half) stable sort of the records by view depth bits
     const int rpasses = sort_passes(0, 32, plan->settings.digit_bits);
-    SGS_TRY(launch_record_keys(rp.tiles, rp.rec1, R, region<unsigned long long>(plan, O_RK0),
+    SGS_TRY(launch_record_keys(rp.tiles, rp.rec1, R, region<uint32_t>(plan, O_RK0),
                                region<uint32_t>(plan, O_RV0), st, stream));
     if (R > 0)
-        SGS_TRY(launch_sort(region<unsigned long long>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
-                            region<unsigned long long>(plan, O_RK1), region<uint32_t>(plan, O_RV1),
+        SGS_TRY(launch_sort(region<uint32_t>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
+                            region<uint32_t>(plan, O_RK1), region<uint32_t>(plan, O_RV1),
                             &st->num_records, R, 0, 32, plan->settings.digit_bits, region<uint32_t>(plan, O_HIST),
                             region<uint32_t>(plan, O_GOFF), region<uint32_t>(plan, O_COUNTERS),
                             region<unsigned long long>(plan, O_RLB), st, stream, nullptr));
@@ -267,27 +267,28 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     SGS_TRY(launch_scan(rp.tiles, perm, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));
     SGS_TRY(probe(plan, SGS_EV_SCAN_END, stream));
     int ipasses, irb;
-    sort_digit_plan(32, plan->key_bits, plan->settings.digit_bits, &ipasses, &irb);
+    const int tile_bits = plan->key_bits - 32;
+    sort_digit_plan(0, tile_bits, plan->settings.digit_bits, &ipasses, &irb);
     SGS_TRY(launch_duplicate(vt, rp, perm, region<uint32_t>(plan, O_OFFS), plan->n, R, st, cap,
-                             region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0), irb,
+                             region<uint32_t>(plan, O_K0), region<uint32_t>(plan, O_V0), irb,
                              ipasses, region<uint32_t>(plan, O_HIST), stream));
     SGS_TRY(probe(plan, SGS_EV_DUP_END, stream));
     // (c, tile half) stable sort of the instances by tile id
     cudaEvent_t hist_end = plan->events ? plan->events[SGS_EV_HIST_END] : nullptr;
     if (plan->sort_passes > 0) {
-        SGS_TRY(launch_sort(region<unsigned long long>(plan, O_K0), region<uint32_t>(plan, O_V0),
-                            region<unsigned long long>(plan, O_K1), region<uint32_t>(plan, O_V1),
-                            &st->m_clamped, cap, 32, plan->key_bits, plan->settings.digit_bits,
+        SGS_TRY(launch_sort(region<uint32_t>(plan, O_K0), region<uint32_t>(plan, O_V0),
+                            region<uint32_t>(plan, O_K1), region<uint32_t>(plan, O_V1),
+                            &st->m_clamped, cap, 0, tile_bits, plan->settings.digit_bits,
                             region<uint32_t>(plan, O_HIST), region<uint32_t>(plan, O_GOFF),
                             region<uint32_t>(plan, O_COUNTERS), region<unsigned long long>(plan, O_SORTLB),
                             st, stream, hist_end, /*histogram_ready=*/true));
     } else if (hist_end) {
-        SGS_TRY(cudaEventRecord(hist_end, stream));
+        SGS_TRY(record_probe(hist_end, stream));
     }
     SGS_TRY(probe(plan, SGS_EV_SORT_END, stream));
     const int kreg = (plan->sort_passes & 1) ? O_K1 : O_K0;
     SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));
-    SGS_TRY(launch_ranges(region<unsigned long long>(plan, kreg), st, cap, plan->num_tiles,
+    SGS_TRY(launch_ranges(region<uint32_t>(plan, kreg), st, cap, plan->num_tiles,
                           region<uint2>(plan, O_RANGES), stream));
     SGS_TRY(probe(plan, SGS_EV_RANGES_END, stream));
     plan->stage = 2;
@@ -427,6 +428,14 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
     SGS_TRY(launch_sort(k0, vals, k1, v1, &st->m_clamped, m, 0, key_bits, digit_bits, hist, goff, counters, lb,
                         st, stream, nullptr));
     if (sort_passes(key_bits, digit_bits) & 1) SGS_TRY(launch_copy_pairs(k1, v1, k0, vals, m, stream));
+    return SGS_OK;
+}
+
+sgs_status sgs_selftest_lookback(const uint64_t* slots, int64_t num_slots, uint64_t* sum,
+                                 int32_t* status, cudaStream_t stream) {
+    if (num_slots < 0 || !sum || !status || (num_slots > 0 && !slots)) return SGS_ERR_INVALID;
+    SGS_TRY(launch_lookback_selftest(reinterpret_cast<const unsigned long long*>(slots), num_slots,
+                                     reinterpret_cast<unsigned long long*>(sum), status, stream));
     return SGS_OK;
 }
 

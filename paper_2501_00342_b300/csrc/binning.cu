@@ -8,18 +8,21 @@
 namespace sgs {
 namespace {
 
-// ---- decoupled look-back helpers (64-bit words: 2-bit flag | 62-bit value) ----
+// ---- decoupled look-back words of the scan: 2-bit flag | 62-bit value ----
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 
-__device__ __forceinline__ void store_relaxed(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+// One thread runs the scan's look-back over caller-provided slots (failure-detection test of
+// the bounded wait): the status word lives in shared memory and is copied out.
+__global__ void lookback_selftest_kernel(const unsigned long long* slots, int64_t n,
+                                         unsigned long long* sum, int32_t* status) {
+    __shared__ DeviceStatus s;
+    if (threadIdx.x == 0) {
+        s.status = 0;
+        sum[0] = lookback_sum(slots, n - 1, 1, kValueMask, kFlagAgg, kFlagInc, &s);
+        status[0] = s.status;
+    }
 }
 
 __global__ void fill_u32_kernel(uint32_t* p, uint32_t value, size_t count) {
@@ -80,26 +83,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
         // acc = tile aggregate; look back for the exclusive prefix of this tile
         unsigned long long prefix = 0;
         if (tile == 0) {
-            store_relaxed(lookback, kFlagInc | acc);
+            slot_store(lookback, kFlagInc | acc);
         } else {
-            store_relaxed(lookback + tile, kFlagAgg | acc);
-            int64_t j = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            while (j >= 0) {
-                const unsigned long long e = load_relaxed(lookback + j);
-                const unsigned long long f = e & ~kValueMask;
-                if (f == kFlagInc) {
-                    prefix += e & kValueMask;
-                    break;
-                } else if (f == kFlagAgg) {
-                    prefix += e & kValueMask;
-                    --j;
-                } else if (++spins > kSpinLimit) {
-                    set_status(st, SGS_ERR_TIMEOUT);
-                    break;
-                }
-            }
-            store_relaxed(lookback + tile, kFlagInc | (prefix + acc));
+            slot_store(lookback + tile, kFlagAgg | acc);
+            prefix = lookback_sum(lookback, (int64_t)tile - 1, 1, kValueMask, kFlagAgg, kFlagInc, st);
+            slot_store(lookback + tile, kFlagInc | (prefix + acc));
         }
         s_prefix = prefix;
         const int64_t num_tiles = (R + kScanTile - 1) / kScanTile;
@@ -140,12 +128,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // Keys of the record sort: the float bits of the view depth of a record with instances
 // (depth > near > 0, so the bits order like the values), 0xffffffff for the others.
 __global__ void record_keys_kernel(const uint32_t* __restrict__ tiles, const float4* __restrict__ rec1,
-                                   int64_t R, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
+                                   int64_t R, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                    DeviceStatus* st) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r == 0) st->num_records = (uint32_t)R;
     if (r >= R) return;
-    keys[r] = tiles[r] ? (unsigned long long)__float_as_uint(rec1[r].z) : 0xffffffffull;
+    keys[r] = tiles[r] ? __float_as_uint(rec1[r].z) : 0xffffffffu;
     vals[r] = (uint32_t)r;
 }
 
@@ -168,17 +156,18 @@ __device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, uint3
     }
 }
 
-// Writes the (tile | depth, record) instances in the order of the depth-sorted records
+// Writes the (tile id, record) instances in the order of the depth-sorted records
 // (perm): sorted position j emits its record's tiles at offsets[j] (the scan taken in that
 // order), tiles row-major.  One warp per 32 consecutive sorted positions, whose instances
 // fill one contiguous output range 32 slots at a time: for slot e a 5-step shuffle search
 // finds the record (inclusive scan of the counts), its packed row table (written by
 // preprocess, staged in shared memory) gives the row, and consecutive lanes write
 // consecutive slots.  A record whose table overflowed is filled afterwards by the whole
-// warp, recomputing its rows with row_span.  Since every key of a record carries the same
-// depth, this order is (depth bits, record) -- what the low 32 bits of a stable LSD radix
-// sort would produce -- and only the tile bits are left to sort.  The digit histograms of
-// that tile sort are counted here (count_tile_digits).
+// warp, recomputing its rows with row_span.  Since every instance of a record has the same
+// depth, this order is (depth bits, record) -- what the depth half of a stable LSD radix
+// sort of (tile | depth) keys would produce -- so only the tile id is left to sort, and the
+// depth never has to travel with the instances.  The digit histograms of that tile sort are
+// counted here (count_tile_digits).
 template <int RB>
 __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, const uint4* __restrict__ spans,
                                                          const uint32_t* __restrict__ tiles,
@@ -188,7 +177,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
                                                          const uint32_t* __restrict__ offsets,
                                                          int64_t n, int64_t R, const DeviceStatus* st,
                                                          int64_t capacity,
-                                                         unsigned long long* __restrict__ keys,
+                                                         uint32_t* __restrict__ keys,
                                                          uint32_t* __restrict__ vals, int passes,
                                                          uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
@@ -208,10 +197,9 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
         const uint32_t r = j < R ? perm[j] : 0u;
         const uint32_t cnt = (j < R && !overflow && r < (uint32_t)R) ? tiles[r] : 0u;
         if (!__ballot_sync(kFullMask, cnt != 0u)) continue;
-        uint32_t zbits = 0, tbase = 0, hdr = 0;
+        uint32_t tbase = 0, hdr = 0;
         int TW = 0;
         if (cnt) {
-            zbits = __float_as_uint(rec1[r].z);
             const int v = (int)(r / n32);
             tbase = vt.v[v].tile_base;
             TW = vt.v[v].tiles_x;
@@ -240,7 +228,6 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
             q = min(q, 31);
             const uint32_t first = __shfl_sync(kFullMask, incl - cnt, q);
             const uint32_t cq = __shfl_sync(kFullMask, cnt, q);
-            const uint32_t zb = __shfl_sync(kFullMask, zbits, q);
             const uint32_t tb = __shfl_sync(kFullMask, tbase, q);
             const uint32_t rq = __shfl_sync(kFullMask, r, q);
             const int TWq = __shfl_sync(kFullMask, TW, q);
@@ -260,7 +247,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
                 const uint32_t t = row_t0 + (local - before);
                 const uint32_t pos = obase + e;
                 if ((int64_t)pos < capacity) {  // only false after a failed scan
-                    keys[pos] = ((unsigned long long)t << 32) | zb;
+                    keys[pos] = t;
                     vals[pos] = rq;
                 }
                 count_tile_digits<RB>(h, passes, t, row_t0, row_t0 + (after - before));
@@ -275,7 +262,6 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
             const float4 aj = rec0[rj];
             const float qc = rec1[rj].x;
             const float px = aj.x, py = aj.y, A = -2.0f * aj.z, B = -aj.w, C = -2.0f * qc;
-            const uint32_t zb = __shfl_sync(kFullMask, zbits, jj);
             const uint32_t tb = __shfl_sync(kFullMask, tbase, jj);
             const int TWj = __shfl_sync(kFullMask, TW, jj);
             const int v = (int)(rj / n32);
@@ -310,7 +296,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
                         const uint32_t t = row_t0 + (e - rfirst);
                         const uint32_t pos = oj + e;
                         if ((int64_t)pos < capacity) {
-                            keys[pos] = ((unsigned long long)t << 32) | zb;
+                            keys[pos] = t;
                             vals[pos] = rj;
                         }
                         count_tile_digits<RB>(h, passes, t, row_t0, row_t0 + lq);
@@ -326,19 +312,25 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
         if (h[j]) atomicAdd(&hist[j], h[j]);
 }
 
-__global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys,
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ tile_ids,
                                                       const DeviceStatus* st, uint32_t num_tiles,
                                                       uint2* __restrict__ ranges) {
     const uint32_t m = st->m_clamped;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        const uint32_t t = (uint32_t)(keys[j] >> 32);
+        const uint32_t t = tile_ids[j];
         if (t >= num_tiles) continue;  // only after a failed sort (status is set)
-        if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = j;
-        if (j == m - 1 || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = j + 1;
+        if (j == 0 || tile_ids[j - 1] != t) ranges[t].x = j;
+        if (j == m - 1 || tile_ids[j + 1] != t) ranges[t].y = j + 1;
     }
 }
 
 }  // namespace
+
+cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n, unsigned long long* sum,
+                                    int32_t* status, cudaStream_t s) {
+    lookback_selftest_kernel<<<1, 32, 0, s>>>(slots, n, sum, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
@@ -361,7 +353,7 @@ cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* o
 
 cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* perm,
                              const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
-                             int64_t capacity, unsigned long long* keys, uint32_t* vals, int digit_bits,
+                             int64_t capacity, uint32_t* keys, uint32_t* vals, int digit_bits,
                              int passes, uint32_t* hist, cudaStream_t s) {
     cudaError_t e = launch_fill_u32(hist, 0u, (size_t)kHistEntries, s);
     if (e != cudaSuccess || R == 0) return e;
@@ -379,7 +371,7 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const unsigned long long* keys, const DeviceStatus* st, int64_t capacity,
+cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t capacity,
                           int64_t num_tiles, uint2* ranges, cudaStream_t s) {
     if (capacity == 0) return cudaSuccess;
     const int threads = 256;
@@ -392,7 +384,7 @@ cudaError_t launch_ranges(const unsigned long long* keys, const DeviceStatus* st
 }  // namespace sgs
 
 namespace sgs {
-cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, unsigned long long* keys,
+cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
                                uint32_t* vals, DeviceStatus* st, cudaStream_t s) {
     const int threads = 256;
     const int64_t blocks = (R + threads - 1) / threads;

@@ -1,6 +1,7 @@
 // Stage (e): front-to-back alpha blending per pixel, and its reverse-mode pass.
 //
-// One CTA per (view, tile), one pixel per thread.  The tile's depth-sorted instance list
+// One CTA per (view, tile); the forward uses one pixel per thread, the backward two.  The
+// tile's depth-sorted instance list
 // [start, end) is staged batch_depth Gaussians at a time in shared memory (three float4
 // records per Gaussian, gathered through the sorted record ids).  Per pixel centre p:
 //   power = -1/2 (A dx^2 + C dy^2) - B dx dy;  skip if power < -4.5 (outside 3 sigma)
@@ -47,6 +48,17 @@ __device__ __forceinline__ uint2 clamp_range(uint2 r, uint32_t m) {
     return r;
 }
 
+// Per-pixel state of the forward walk.
+struct FwdPixel {
+    float pxc, pyc;  // pixel centre
+    float T, C0, C1, C2;
+    uint32_t last, evaluated, contributed;
+    bool inside, done;
+};
+
+// PPT pixels per thread: pixel q of thread t is (t % tile_w, t / tile_w + q * tile_h / PPT)
+// inside the tile, so one shared-memory read of a Gaussian serves PPT pixels.
+template <int PPT>
 __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const uint2* __restrict__ ranges,
                                                      const uint32_t* __restrict__ vals, uint32_t R,
                                                      const float4* __restrict__ rec0,
@@ -66,16 +78,25 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
     const int lx = threadIdx.x % vt.tile_w, ly = threadIdx.x / vt.tile_w;
-    const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly;
-    const bool inside = x < cam.W && y < cam.H;
-    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const int rows = vt.tile_h / PPT;
+    FwdPixel P[PPT];
+    bool all_done = true;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly + q * rows;
+        P[q].inside = x < cam.W && y < cam.H;
+        P[q].pxc = (float)x + 0.5f;
+        P[q].pyc = (float)y + 0.5f;
+        P[q].T = 1.0f;
+        P[q].C0 = P[q].C1 = P[q].C2 = 0.0f;
+        P[q].last = P[q].evaluated = P[q].contributed = 0;
+        P[q].done = !P[q].inside;
+        all_done &= P[q].done;
+    }
     const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
     const int n = (int)(range.y - range.x);
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0, evaluated = 0, contributed = 0;
-    bool done = !inside;
     for (int base = 0; base < n; base += batch) {
-        if (__syncthreads_count(!done) == 0) break;
+        if (__syncthreads_count(!all_done) == 0) break;
         const int cnt = min(batch, n - base);
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
             const uint32_t id = min(vals[range.x + base + j], R - 1);  // ids are < R by construction
@@ -84,42 +105,53 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
             s2[j] = rec2[id];
         }
         __syncthreads();
-        const bool was_done = done;
-        int k = 0;
-        for (; !done && k < cnt; ++k) {
+        for (int k = 0; !all_done && k < cnt; ++k) {
             const float4 a = s0[k];
             const float4 b = s1[k];
-            const float power = support_power(a.z, a.w, b.x, a.x - pxc, a.y - pyc);
-            if (!(power >= kSupportPower)) continue;  // also skips a NaN exponent
-            const float alpha = fminf(kAlphaMax, b.y * __expf(power));
-            if (alpha < kAlphaMin) continue;
-            const float Tn = T * (1.0f - alpha);
-            if (Tn < kTransmittanceMin) {
-                done = true;
-                break;
+            all_done = true;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                FwdPixel& p = P[q];
+                if (!p.done) {
+                    ++p.evaluated;
+                    const float power = support_power(a.z, a.w, b.x, a.x - p.pxc, a.y - p.pyc);
+                    if (power >= kSupportPower) {  // also skips a NaN exponent
+                        const float alpha = fminf(kAlphaMax, b.y * __expf(power));
+                        if (alpha >= kAlphaMin) {
+                            const float Tn = p.T * (1.0f - alpha);
+                            if (Tn < kTransmittanceMin) {
+                                p.done = true;
+                            } else {
+                                const float4 c = s2[k];
+                                const float w = alpha * p.T;
+                                p.C0 += c.x * w;
+                                p.C1 += c.y * w;
+                                p.C2 += c.z * w;
+                                p.T = Tn;
+                                p.last = (uint32_t)(base + k + 1);
+                                ++p.contributed;
+                            }
+                        }
+                    }
+                }
+                all_done &= p.done;
             }
-            const float4 c = s2[k];
-            const float w = alpha * T;
-            C0 += c.x * w;
-            C1 += c.y * w;
-            C2 += c.z * w;
-            T = Tn;
-            last = (uint32_t)(base + k + 1);
-            ++contributed;
         }
-        if (!was_done) evaluated += (uint32_t)k + (done ? 1u : 0u);  // the stopping one counts
     }
-    if (inside) {
-        const int64_t hw = (int64_t)cam.W * cam.H;
-        const int64_t p = (int64_t)y * cam.W + x;
-        float* img = out_rgb + 3 * cam.pixel_base;
-        img[p] = C0 + T * bg0;
-        img[hw + p] = C1 + T * bg1;
-        img[2 * hw + p] = C2 + T * bg2;
-        if (out_T) out_T[cam.pixel_base + p] = T;
-        pix_T[cam.pixel_base + p] = T;
-        pix_last[cam.pixel_base + p] = last;
-        pix_count[cam.pixel_base + p] = make_uint2(evaluated, contributed);
+    const int64_t hw = (int64_t)cam.W * cam.H;
+    float* img = out_rgb + 3 * cam.pixel_base;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const FwdPixel& p = P[q];
+        if (!p.inside) continue;
+        const int64_t pi = (int64_t)(p.pyc - 0.5f) * cam.W + (int64_t)(p.pxc - 0.5f);
+        img[pi] = p.C0 + p.T * bg0;
+        img[hw + pi] = p.C1 + p.T * bg1;
+        img[2 * hw + pi] = p.C2 + p.T * bg2;
+        if (out_T) out_T[cam.pixel_base + pi] = p.T;
+        pix_T[cam.pixel_base + pi] = p.T;
+        pix_last[cam.pixel_base + pi] = p.last;
+        pix_count[cam.pixel_base + pi] = make_uint2(p.evaluated, p.contributed);
     }
 }
 
@@ -153,6 +185,14 @@ __device__ __forceinline__ float warp_sum8(const float v[8], int lane) {
     return x;
 }
 
+// Per-pixel state of the reverse walk.
+struct BwdPixel {
+    float pxc, pyc;
+    float T, g0, g1, g2, acc0, acc1, acc2;
+    uint32_t last;
+};
+
+template <int PPT>
 __global__ void __launch_bounds__(512) blend_backward_kernel(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, uint32_t R32,
     const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
@@ -168,31 +208,42 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
     const int lx = threadIdx.x % vt.tile_w, ly = threadIdx.x / vt.tile_w;
-    const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly;
-    const bool inside = x < cam.W && y < cam.H;
-    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const int rows = vt.tile_h / PPT;
     const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
-    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-    uint32_t last = 0;
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
-    if (inside) {
-        const int64_t hw = (int64_t)cam.W * cam.H;
-        const int64_t p = (int64_t)y * cam.W + x;
-        const float* gi = dL_drgb + 3 * cam.pixel_base;
-        g0 = gi[p];
-        g1 = gi[hw + p];
-        g2 = gi[2 * hw + p];
-        T = pix_T[cam.pixel_base + p];
-        last = min(pix_last[cam.pixel_base + p], range.y - range.x);
+    const int64_t hw = (int64_t)cam.W * cam.H;
+    const float* gi = dL_drgb + 3 * cam.pixel_base;
+    BwdPixel P[PPT];
+    uint32_t my_last = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly + q * rows;
+        BwdPixel& p = P[q];
+        p.pxc = (float)x + 0.5f;
+        p.pyc = (float)y + 0.5f;
+        p.acc0 = bg0;
+        p.acc1 = bg1;
+        p.acc2 = bg2;
+        p.T = 1.0f;
+        p.g0 = p.g1 = p.g2 = 0.0f;
+        p.last = 0;
+        if (x < cam.W && y < cam.H) {
+            const int64_t pi = (int64_t)y * cam.W + x;
+            p.g0 = gi[pi];
+            p.g1 = gi[hw + pi];
+            p.g2 = gi[2 * hw + pi];
+            p.T = pix_T[cam.pixel_base + pi];
+            p.last = min(pix_last[cam.pixel_base + pi], range.y - range.x);
+        }
+        my_last = max(my_last, p.last);
     }
-    const uint32_t wmax = __reduce_max_sync(kFullMask, last);
+    const uint32_t wmax = __reduce_max_sync(kFullMask, my_last);
     if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_max_last, wmax);
     __syncthreads();
     const int top = (int)s_max_last;
-    float acc0 = bg0, acc1 = bg1, acc2 = bg2;
     const int lane = threadIdx.x & 31;
-    const int warp_last = (int)wmax;  // no lane of this warp blends an entry at or past it
+    const int warp_last = (int)wmax;  // no pixel of this warp blends an entry at or past it
     for (int hi = top; hi > 0; hi -= batch) {
         const int lo = max(0, hi - batch);
         __syncthreads();
@@ -207,41 +258,44 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
         for (int k = min(hi, warp_last) - 1; k >= lo; --k) {
             const float4 a = s0[k - lo];
             const float4 b = s1[k - lo];
+            const float4 c = s2[k - lo];
             float d[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) d[q] = 0.0f;
-            bool contrib = (uint32_t)k < last;
-            if (contrib) {
-                const float dx = a.x - pxc, dy = a.y - pyc;
+            for (int i = 0; i < 9; ++i) d[i] = 0.0f;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                BwdPixel& p = P[q];
+                if ((uint32_t)k >= p.last) continue;
+                const float dx = a.x - p.pxc, dy = a.y - p.pyc;
                 const float power = support_power(a.z, a.w, b.x, dx, dy);
                 const float G = __expf(power);
                 const float oG = b.y * G;
                 const float alpha = fminf(kAlphaMax, oG);
-                contrib = power >= kSupportPower && alpha >= kAlphaMin;
-                if (contrib) {
-                    const float4 c = s2[k - lo];
-                    T = __fdividef(T, 1.0f - alpha);
-                    const float w = alpha * T;
-                    d[6] = g0 * w;
-                    d[7] = g1 * w;
-                    d[8] = g2 * w;
-                    const float dalpha = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
-                    acc0 = acc0 * (1.0f - alpha) + c.x * alpha;
-                    acc1 = acc1 * (1.0f - alpha) + c.y * alpha;
-                    acc2 = acc2 * (1.0f - alpha) + c.z * alpha;
-                    if (oG <= kAlphaMax) {
-                        const float gpow = dalpha * b.y * G;
-                        // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2)
-                        d[0] = gpow * (2.0f * a.z * dx + a.w * dy);
-                        d[1] = gpow * (a.w * dx + 2.0f * b.x * dy);
-                        d[2] = gpow * (-0.5f * dx * dx);
-                        d[3] = gpow * (-dx * dy);
-                        d[4] = gpow * (-0.5f * dy * dy);
-                        d[5] = dalpha * G;
-                    }
+                if (!(power >= kSupportPower && alpha >= kAlphaMin)) continue;
+                any = true;
+                p.T = __fdividef(p.T, 1.0f - alpha);
+                const float w = alpha * p.T;
+                d[6] += p.g0 * w;
+                d[7] += p.g1 * w;
+                d[8] += p.g2 * w;
+                const float dalpha =
+                    p.T * (p.g0 * (c.x - p.acc0) + p.g1 * (c.y - p.acc1) + p.g2 * (c.z - p.acc2));
+                p.acc0 = p.acc0 * (1.0f - alpha) + c.x * alpha;
+                p.acc1 = p.acc1 * (1.0f - alpha) + c.y * alpha;
+                p.acc2 = p.acc2 * (1.0f - alpha) + c.z * alpha;
+                if (oG <= kAlphaMax) {
+                    const float gpow = dalpha * b.y * G;
+                    // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2)
+                    d[0] += gpow * (2.0f * a.z * dx + a.w * dy);
+                    d[1] += gpow * (a.w * dx + 2.0f * b.x * dy);
+                    d[2] += gpow * (-0.5f * dx * dx);
+                    d[3] += gpow * (-dx * dy);
+                    d[4] += gpow * (-0.5f * dy * dy);
+                    d[5] += dalpha * G;
                 }
             }
-            if (__any_sync(kFullMask, contrib)) {
+            if (__any_sync(kFullMask, any)) {
                 const float s8 = warp_sum8(d, lane);
                 const float s9 = warp_sum(d[8]);
                 const uint32_t id = sid[k - lo];
@@ -292,19 +346,52 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 
 }  // namespace
 
+// Pixels per thread of the blend kernels: 2 when the tile splits into two halves of at
+// least one warp each, else 1.
+static int pixels_per_thread(const ViewTable& vt) {
+    return (vt.tile_h % 2 == 0 && vt.tile_w * vt.tile_h / 2 >= 32) ? 2 : 1;
+}
+
+template <int PPT>
+static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uint32_t* vals, int64_t R,
+                             const RecordPtrs& p, int batch, float bg0, float bg1, float bg2, float* out_rgb,
+                             float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
+                             const DeviceStatus* st, cudaStream_t s) {
+    const int threads = vt.tile_w * vt.tile_h / PPT;
+    const size_t smem = (size_t)batch * 3 * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(blend_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // with no records every range is empty and no id is read; the kernel still writes bg
+    blend_kernel<PPT><<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1,
+                                                                    p.rec2, batch, bg0, bg1, bg2, out_rgb, out_T,
+                                                                    pix_T, pix_last, pix_count, st);
+    return cudaGetLastError();
+}
+
+template <int PPT>
+static cudaError_t blend_backward_ppt(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
+                                      const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
+                                      const float* pix_T, const uint32_t* pix_last, const float* dL_drgb,
+                                      float4* grad2d, int64_t R, const DeviceStatus* st, cudaStream_t s) {
+    const int threads = vt.tile_w * vt.tile_h / PPT;
+    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t));
+    cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    blend_backward_kernel<PPT><<<(unsigned)vt.num_tiles, threads, smem, s>>>(
+        vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb,
+        grad2d, R, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
                          int64_t R, const RecordPtrs& p, int batch, float bg0, float bg1, float bg2,
                          float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
                          uint2* pix_count, const DeviceStatus* st, cudaStream_t s) {
     if (vt.num_tiles == 0) return cudaSuccess;
-    const int threads = vt.tile_w * vt.tile_h;
-    const size_t smem = (size_t)batch * 3 * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(blend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    // with no records every range is empty and no id is read; the kernel still writes bg
-    blend_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch,
-                                                              bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, pix_count, st);
-    return cudaGetLastError();
+    // one pixel per thread: the forward's early exit loses more than the shared reads save
+    return blend_ppt<1>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, pix_count,
+                        st, s);
 }
 
 cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,
@@ -313,15 +400,11 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                   const float* dL_drgb, float4* grad2d, int64_t R,
                                   const DeviceStatus* st, cudaStream_t s) {
     if (vt.num_tiles == 0 || R == 0) return cudaSuccess;
-    const int threads = vt.tile_w * vt.tile_h;
-    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t));
-    cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    blend_backward_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(
-        vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb,
-        grad2d, R, st);
-    return cudaGetLastError();
+    if (pixels_per_thread(vt) == 2)
+        return blend_backward_ppt<2>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d,
+                                     R, st, s);
+    return blend_backward_ppt<1>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d, R,
+                                 st, s);
 }
 
 cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s) {

@@ -52,6 +52,48 @@ __device__ __forceinline__ void set_status(DeviceStatus* st, int32_t bits) {
     atomicOr(&st->status, bits);
 }
 
+// ---- decoupled look-back slots: 64-bit words, a tag in the high bits and a count below ----
+__device__ __forceinline__ void slot_store(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long slot_load(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of a chained scan by decoupled look-back (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", 2016).  Walks the slots
+// slot[j * stride], j = first, first - 1, ..., 0: a slot tagged `agg` (the tile's own
+// count) is added and the walk goes on, a slot tagged `inc` (the tile's inclusive prefix)
+// is added and ends it, any other tag means the tile has not published yet and the slot is
+// polled again.  After `limit` such polls in all, SGS_ERR_TIMEOUT is set in the status
+// word and the partial sum is returned: the wait never hangs, the result is then invalid.
+__device__ __forceinline__ unsigned long long lookback_sum(const unsigned long long* slot, int64_t first,
+                                                           size_t stride, unsigned long long value_mask,
+                                                           unsigned long long tag_agg,
+                                                           unsigned long long tag_inc, DeviceStatus* st,
+                                                           uint32_t limit = kSpinLimit) {
+    unsigned long long acc = 0;
+    uint32_t spins = 0;
+    int64_t j = first;
+    while (j >= 0) {
+        const unsigned long long e = slot_load(slot + (size_t)j * stride);
+        const unsigned long long tag = e & ~value_mask;
+        if (tag == tag_inc) {
+            acc += e & value_mask;
+            break;
+        } else if (tag == tag_agg) {
+            acc += e & value_mask;
+            --j;
+        } else if (++spins > limit) {
+            set_status(st, SGS_ERR_TIMEOUT);
+            break;
+        }
+    }
+    return acc;
+}
+
 // Support exponent of a Gaussian at a pixel centre, in the fixed order
 //   power = fma(dx, fma(qa, dx, qb*dy), (qc*dy)*dy),  dx = px - cx_pix, dy = py - cy_pix,
 // with (qa, qb, qc) = (-A/2, -B, -C/2) the scaled conic.  Forward and backward kernels

@@ -6,6 +6,16 @@
 
 namespace sgs {
 
+// Records a timing probe on s.  While s is being captured into a CUDA graph the record
+// becomes an event-record node of the graph (a plain record would only mark a fork point).
+inline cudaError_t record_probe(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags(
+        ev, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 struct RecordPtrs {
     float4* rec0;  // px, py, -A/2, -B
     float4* rec1;  // -C/2, opacity, depth, radius
@@ -27,9 +37,12 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStream_t s);
+// The scan's bounded look-back over slots[0, n) from slot n-1 (sum and status word out).
+cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n, unsigned long long* sum,
+                                     int32_t* status, cudaStream_t s);
 // Keys (view depth bits; 0xffffffff without instances) and ids of the record sort; also
 // stores R in st->num_records.
-cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, unsigned long long* keys,
+cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
                                uint32_t* vals, DeviceStatus* st, cudaStream_t s);
 // Exclusive scan of tiles[perm[j]] (or tiles[j] when perm is null).
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
@@ -39,9 +52,9 @@ cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* o
 // passes (hist: kHistEntries u32, cleared here).
 cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uint32_t* perm,
                              const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
-                             int64_t capacity, unsigned long long* keys, uint32_t* vals, int digit_bits,
+                             int64_t capacity, uint32_t* keys, uint32_t* vals, int digit_bits,
                              int passes, uint32_t* hist, cudaStream_t s);
-cudaError_t launch_ranges(const unsigned long long* keys, const DeviceStatus* st, int64_t capacity,
+cudaError_t launch_ranges(const uint32_t* tile_ids, const DeviceStatus* st, int64_t capacity,
                           int64_t num_tiles, uint2* ranges, cudaStream_t s);
 
 // (c) onesweep radix sort
@@ -67,6 +80,11 @@ cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
                         unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
                         cudaEvent_t hist_end, bool histogram_ready = false);
+// The same sort for 32-bit keys (key_bits <= 32; 16 bytes moved per pair and pass).
+cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* m_ptr,
+                        int64_t capacity, int first_bit, int key_bits, int digit_bits, uint32_t* hist,
+                        uint32_t* goff, uint32_t* counters, unsigned long long* lookback, DeviceStatus* st,
+                        cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready = false);
 int sort_passes(int key_bits, int digit_bits);
 int sort_passes(int first_bit, int key_bits, int digit_bits);
 

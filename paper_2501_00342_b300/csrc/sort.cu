@@ -21,14 +21,6 @@
 namespace sgs {
 namespace {
 
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -44,8 +36,8 @@ __host__ __device__ __forceinline__ int pass_width(int p, int RB, int first_bit,
     return key_bits - lo < RB ? key_bits - lo : RB;
 }
 
-template <int RB>
-__global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long* __restrict__ keys,
+template <typename KeyT, int RB>
+__global__ void __launch_bounds__(256) histogram_kernel(const KeyT* __restrict__ keys,
                                                         const uint32_t* m_ptr, int passes, int first_bit,
                                                         int key_bits, uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
@@ -57,7 +49,7 @@ __global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long
     for (uint32_t base = blockIdx.x * blockDim.x; base < m; base += stride) {
         const uint32_t idx = base + threadIdx.x;
         const bool valid = idx < m;
-        const unsigned long long k = valid ? keys[idx] : 0ull;
+        const unsigned long long k = valid ? (unsigned long long)keys[idx] : 0ull;
         const uint32_t active = __ballot_sync(kFullMask, valid);
         for (int p = 0; p < passes; ++p) {
             const uint32_t mask = (1u << pass_width(p, RB, first_bit, key_bits)) - 1u;
@@ -92,15 +84,23 @@ __global__ void histogram_scan_kernel(const uint32_t* __restrict__ hist, uint32_
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x) goff[p * RADIX + d] = s[d];
 }
 
-template <int RB>
+// Items per thread: 15 for 64-bit keys, 24 for 32-bit keys (about the same registers).
+template <typename KeyT>
+struct SortShape {
+    static constexpr int ITEMS = sizeof(KeyT) == 8 ? 15 : 24;
+    static constexpr int TILE = kSortThreads * ITEMS;
+};
+
+template <typename KeyT, int RB>
 struct OnesweepSmem {
     static constexpr int RADIX = 1 << RB;
     static constexpr int WARPS = kSortThreads / 32;
+    static constexpr int TILE = SortShape<KeyT>::TILE;
     union {
         uint32_t warp_hist[WARPS][RADIX + 1];  // ranking; +1: sentinel bucket of the ragged tail
         struct {
-            unsigned long long keys[kSortTile];  // staging, after the positions are in registers
-            uint32_t vals[kSortTile];
+            KeyT keys[TILE];  // staging, after the positions are in registers
+            uint32_t vals[TILE];
         } stage;
     } u;
     uint32_t digit_start[RADIX];
@@ -109,17 +109,18 @@ struct OnesweepSmem {
     uint32_t tile;
 };
 
-template <int RB>
+template <typename KeyT, int RB>
 __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
-    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
-    unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* m_ptr,
-    const uint32_t* __restrict__ goff, unsigned long long* lookback, uint32_t* counter, int shift,
-    int width, int pass, DeviceStatus* st) {
+    const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* m_ptr, const uint32_t* __restrict__ goff,
+    unsigned long long* lookback, uint32_t* counter, int shift, int width, int pass, DeviceStatus* st) {
     constexpr int RADIX = 1 << RB;
     constexpr int WARPS = kSortThreads / 32;
     constexpr int DPT = (RADIX + kSortThreads - 1) / kSortThreads;  // digits per thread
+    constexpr int kSortItems = SortShape<KeyT>::ITEMS;
+    constexpr int kSortTile = SortShape<KeyT>::TILE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    OnesweepSmem<RB>& sm = *reinterpret_cast<OnesweepSmem<RB>*>(smem_raw);
+    OnesweepSmem<KeyT, RB>& sm = *reinterpret_cast<OnesweepSmem<KeyT, RB>*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t dmask = (1u << width) - 1u;
     if (threadIdx.x == 0) sm.tile = atomicAdd(counter, 1u);
@@ -132,13 +133,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const uint32_t count = (uint32_t)(m - tile_start < (uint64_t)kSortTile ? m - tile_start : kSortTile);
 
     // load keys warp-striped: item k of lane l of warp w is element w*32*ITEMS + k*32 + l
-    unsigned long long key[kSortItems];
+    KeyT key[kSortItems];
     uint32_t rank[kSortItems];
     const uint32_t wbase = warp * 32 * kSortItems;
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t e = wbase + k * 32 + lane;
-        key[k] = e < count ? kin[tile_start + e] : 0ull;
+        key[k] = e < count ? kin[tile_start + e] : (KeyT)0;
     }
     // stable warp-level ranking (items past the end go to the sentinel bucket RADIX)
     const uint32_t lt = lanemask_lt();
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
 #pragma unroll
     for (int i = 0; i < DPT; ++i) {
         const int d = threadIdx.x * DPT + i;
-        if (d < RADIX) st_relaxed(row + d, tile == 0 ? (tag_inc | (goff[d] + total[i])) : (tag_agg | total[i]));
+        if (d < RADIX) slot_store(row + d, tile == 0 ? (tag_inc | (goff[d] + total[i])) : (tag_agg | total[i]));
     }
 #pragma unroll
     for (int i = 0; i < DPT; ++i) {
@@ -220,25 +221,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
         if (d >= RADIX) continue;
         unsigned long long prefix = goff[d];
         if (tile != 0) {
-            int64_t j = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            unsigned long long acc = 0;
-            while (j >= 0) {
-                const unsigned long long e = ld_relaxed(lookback + (size_t)j * RADIX + d);
-                const unsigned long long tag = e & ~kCountMask;
-                if (tag == tag_inc) {
-                    acc += e & kCountMask;
-                    break;
-                } else if (tag == tag_agg) {
-                    acc += e & kCountMask;
-                    --j;
-                } else if (++spins > kSpinLimit) {
-                    set_status(st, SGS_ERR_TIMEOUT);
-                    break;
-                }
-            }
-            prefix = acc;  // the inclusive prefix of a tile includes goff[d]
-            st_relaxed(row + d, tag_inc | (prefix + total[i]));
+            // the inclusive prefix of a tile includes goff[d]
+            prefix = lookback_sum(lookback + d, (int64_t)tile - 1, RADIX, kCountMask, tag_agg, tag_inc, st);
+            slot_store(row + d, tag_inc | (prefix + total[i]));
         }
         sm.gbase[d] = (uint32_t)prefix;
     }
@@ -261,7 +246,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
-        const unsigned long long kk = sm.u.stage.keys[j];
+        const KeyT kk = sm.u.stage.keys[j];
         const uint32_t d = (uint32_t)(kk >> shift) & dmask;
         const uint32_t dest = sm.gbase[d] + (j - sm.digit_start[d]);
         if (dest < m) {
@@ -271,8 +256,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     }
 }
 
-__global__ void copy_pairs_kernel(const unsigned long long* __restrict__ ks, const uint32_t* __restrict__ vs,
-                                  unsigned long long* __restrict__ kd, uint32_t* __restrict__ vd, int64_t m) {
+template <typename KeyT>
+__global__ void copy_pairs_kernel(const KeyT* __restrict__ ks, const uint32_t* __restrict__ vs,
+                                  KeyT* __restrict__ kd, uint32_t* __restrict__ vd, int64_t m) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
          j += (int64_t)gridDim.x * blockDim.x) {
         kd[j] = ks[j];
@@ -287,8 +273,8 @@ __global__ void sort_init_kernel(DeviceStatus* st, uint32_t m) {
     for (int j = 0; j < 16; ++j) st->tile_counter[j] = 0;
 }
 
-template <int RB>
-cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
+template <typename KeyT, int RB>
+cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
                       const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, uint32_t* hist,
                       uint32_t* goff, uint32_t* counters, unsigned long long* lookback,
                       DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready) {
@@ -298,34 +284,35 @@ cudaError_t sort_impl(unsigned long long* k0, uint32_t* v0, unsigned long long* 
     if (!histogram_ready && (e = launch_fill_u32(hist, 0u, (size_t)passes * RADIX, s)) != cudaSuccess)
         return e;
     if ((e = launch_fill_u32(counters, 0u, kMaxSortPasses, s)) != cudaSuccess) return e;
+    constexpr int kSortTile = SortShape<KeyT>::TILE;
     const size_t tiles = (size_t)((capacity + kSortTile - 1) / kSortTile);
     if ((e = launch_fill_u32(reinterpret_cast<uint32_t*>(lookback), 0u, tiles * RADIX * 2, s)) != cudaSuccess)
         return e;
     if (capacity == 0 || tiles == 0 || passes <= 0) {
-        if (hist_end) return cudaEventRecord(hist_end, s);
+        if (hist_end) return record_probe(hist_end, s);
         return cudaSuccess;
     }
     if (!histogram_ready) {
         const int64_t want = (capacity + 255) / 256;
         const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
         const size_t hs = (size_t)passes * RADIX * sizeof(uint32_t);
-        if ((e = cudaFuncSetAttribute(histogram_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(histogram_kernel<KeyT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)hs)) != cudaSuccess)
             return e;
-        histogram_kernel<RB><<<blocks, 256, hs, s>>>(k0, m_ptr, passes, first_bit, key_bits, hist);
+        histogram_kernel<KeyT, RB><<<blocks, 256, hs, s>>>(k0, m_ptr, passes, first_bit, key_bits, hist);
     }
     histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : (RADIX > 1024 ? 1024 : RADIX), 0, s>>>(hist, goff);
-    if (hist_end && (e = cudaEventRecord(hist_end, s)) != cudaSuccess) return e;
-    const size_t smem = sizeof(OnesweepSmem<RB>);
-    if ((e = cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (hist_end && (e = record_probe(hist_end, s)) != cudaSuccess) return e;
+    const size_t smem = sizeof(OnesweepSmem<KeyT, RB>);
+    if ((e = cudaFuncSetAttribute(onesweep_kernel<KeyT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
     for (int p = 0; p < passes; ++p) {
-        const unsigned long long* kin = (p & 1) ? k1 : k0;
+        const KeyT* kin = (p & 1) ? k1 : k0;
         const uint32_t* vin = (p & 1) ? v1 : v0;
-        unsigned long long* kout = (p & 1) ? k0 : k1;
+        KeyT* kout = (p & 1) ? k0 : k1;
         uint32_t* vout = (p & 1) ? v0 : v1;
-        onesweep_kernel<RB><<<(unsigned)tiles, kSortThreads, smem, s>>>(
+        onesweep_kernel<KeyT, RB><<<(unsigned)tiles, kSortThreads, smem, s>>>(
             kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, first_bit + p * RB,
             pass_width(p, RB, first_bit, key_bits), p, st);
     }
@@ -352,33 +339,59 @@ int sort_passes(int first_bit, int key_bits, int digit_bits) {
 }
 
 size_t sort_lookback_entries(int64_t capacity, int digit_bits) {
+    // the 64-bit key tile is the smaller one, so this bounds both key widths
     return (size_t)((capacity + kSortTile - 1) / kSortTile) * ((size_t)1 << digit_bits);
 }
 
-cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
-                        const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, int digit_bits,
-                        uint32_t* hist, uint32_t* goff, uint32_t* counters,
-                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
-                        cudaEvent_t hist_end, bool histogram_ready) {
+namespace {
+template <typename KeyT>
+cudaError_t launch_sort_t(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* m_ptr, int64_t capacity,
+                          int first_bit, int key_bits, int digit_bits, uint32_t* hist, uint32_t* goff,
+                          uint32_t* counters, unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
+                          cudaEvent_t hist_end, bool histogram_ready) {
     int passes, rb;
     sort_digit_plan(first_bit, key_bits, digit_bits, &passes, &rb);
     switch (rb) {
-#define SGS_SORT(RB)                                                                                        \
-    case RB:                                                                                                \
-        return sort_impl<RB>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters,  \
-                             lookback, st, s, hist_end, histogram_ready);
+#define SGS_SORT(RB)                                                                                          \
+    case RB:                                                                                                  \
+        return sort_impl<KeyT, RB>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, \
+                                   lookback, st, s, hist_end, histogram_ready);
         SGS_SORT(4) SGS_SORT(5) SGS_SORT(6) SGS_SORT(7) SGS_SORT(8) SGS_SORT(9) SGS_SORT(10)
 #undef SGS_SORT
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
-                              uint32_t* vd, int64_t m, cudaStream_t s) {
+template <typename KeyT>
+cudaError_t copy_pairs_t(const KeyT* ks, const uint32_t* vs, KeyT* kd, uint32_t* vd, int64_t m, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     const int64_t want = (m + 255) / 256;
-    copy_pairs_kernel<<<(int)(want < 148 * 16 ? want : 148 * 16), 256, 0, s>>>(ks, vs, kd, vd, m);
+    copy_pairs_kernel<KeyT><<<(int)(want < 148 * 16 ? want : 148 * 16), 256, 0, s>>>(ks, vs, kd, vd, m);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long* k1, uint32_t* v1,
+                        const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, int digit_bits,
+                        uint32_t* hist, uint32_t* goff, uint32_t* counters,
+                        unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
+                        cudaEvent_t hist_end, bool histogram_ready) {
+    return launch_sort_t(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, digit_bits, hist, goff, counters,
+                         lookback, st, s, hist_end, histogram_ready);
+}
+
+cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* m_ptr,
+                        int64_t capacity, int first_bit, int key_bits, int digit_bits, uint32_t* hist,
+                        uint32_t* goff, uint32_t* counters, unsigned long long* lookback, DeviceStatus* st,
+                        cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready) {
+    if (key_bits > 32) return cudaErrorInvalidValue;
+    return launch_sort_t(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, digit_bits, hist, goff, counters,
+                         lookback, st, s, hist_end, histogram_ready);
+}
+
+cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
+                              uint32_t* vd, int64_t m, cudaStream_t s) {
+    return copy_pairs_t(ks, vs, kd, vd, m, s);
 }
 
 cudaError_t launch_sort_init(DeviceStatus* st, uint32_t m, cudaStream_t s) {

@@ -111,3 +111,13 @@ def test_sort_temp_bytes_validation():
 def test_status_strings():
     for code in (B.SGS_OK, B.SGS_ERR_INVALID, B.SGS_ERR_CAPACITY, B.SGS_ERR_TIMEOUT, B.SGS_ERR_CUDA):
         assert len(B.status_string(code)) > 1
+
+
+def test_selftest_lookback_rejects_bad_arguments_on_host():
+    with pytest.raises(B.SgsError) as e:
+        B.selftest_lookback(None, -1, 8, 8, None)
+    assert e.value.code == B.SGS_ERR_INVALID
+    with pytest.raises(B.SgsError):
+        B.selftest_lookback(None, 4, 8, 8, None)  # slots missing
+    with pytest.raises(B.SgsError):
+        B.selftest_lookback(8, 4, None, 8, None)  # sum missing

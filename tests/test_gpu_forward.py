@@ -62,10 +62,14 @@ def _check_bins(scene, cams, rast, tile_w=16, tile_h=16):
     b = O.mirror_bin(scene, cams, tile_w, tile_h)
     M = len(b["keys"])
     assert rast.num_instances == M
-    keys = rast.region("KEYS", torch.int64)[:M].cpu().numpy().view(np.uint64)
+    tile_ids = rast.region("KEYS", torch.int32)[:M].cpu().numpy().view(np.uint32)
     vals = rast.region("VALS", torch.int32)[:M].cpu().numpy().view(np.uint32)
     nt = O.num_tiles(cams, tile_w, tile_h)
     ranges = rast.region("RANGES", torch.int32)[:2 * nt].view(nt, 2).cpu().numpy().view(np.uint32)
+    # full 64-bit keys: tile id << 32 | depth bits of the record (REC1.z)
+    R = scene.n * len(cams)
+    depth_bits = rast.region("REC1", torch.float32)[:4 * R].view(R, 4)[:, 2].cpu().numpy().view(np.uint32)
+    keys = (tile_ids.astype(np.uint64) << np.uint64(32)) | depth_bits[vals].astype(np.uint64)
     assert (keys == b["keys"]).all()
     assert (vals == b["vals"]).all()
     assert (ranges == b["ranges"]).all()
