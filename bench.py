@@ -103,6 +103,22 @@ def _dist():
     return world, rank, local
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Max of a per-rank number over all ranks (the host-side timing collective)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, views_per_rank: int, ms_max: float) -> float:
+    """Whole-job views/s: every rank renders its own batch; the slowest rank sets the time."""
+    return world * views_per_rank / (ms_max / 1e3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -120,11 +136,7 @@ def run_gpu(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     stream = torch.cuda.current_stream()
     settings = RenderSettings(tile_w=args.tile[0], tile_h=args.tile[1], batch_depth=args.batch_depth,
@@ -205,7 +217,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     barrier()
     ms = max_over_ranks(t0.elapsed_time(t1) / args.steps)
-    value = world * nv / (ms / 1e3)
+    value = job_rate(world, nv, ms)
     try:  # the probe events of the last replay of the timed loop
         graph_evs[0].elapsed_time(graph_evs[1])
         ev_sets, stage_source = [graph_evs], "CUDA events inside the graph, last timed replay"
@@ -328,7 +340,7 @@ def run_gpu(args):
         b2.record(stream)
         torch.cuda.synchronize()
         pms = max_over_ranks(a.elapsed_time(b2) / args.steps)
-        out["plain"] = {"ms_per_16_views": round(pms, 4), "views_per_s": round(world * nv / (pms / 1e3), 3),
+        out["plain"] = {"ms_per_16_views": round(pms, 4), "views_per_s": round(job_rate(world, nv, pms), 3),
                         "batched_over_plain": round(pms / ms, 4)}
         del plain
 
@@ -387,7 +399,7 @@ def run_gpu(args):
     b2.record(stream)
     torch.cuda.synchronize()
     ems = max_over_ranks(a.elapsed_time(b2) / args.steps)
-    out["e2e"] = {"value": round(world * nv / (ems / 1e3), 3), "unit": UNIT, "ms_per_step": round(ems, 4),
+    out["e2e"] = {"value": round(job_rate(world, nv, ems), 3), "unit": UNIT, "ms_per_step": round(ems, 4),
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4}
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only); same sample checks parity
