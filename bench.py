@@ -374,6 +374,45 @@ def run_gpu(args):
         fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
         out["render_fps"] = fps
 
+        # ---- 8M Gaussians, 8 views at 3840x2160: one batched fwd+bwd step, peak device memory
+        sc4, cams4 = I.workload(4)
+        m4 = GaussianModel.from_scene(sc4)
+        r4 = Rasterizer(m4, cams4, settings)
+        i4 = torch.empty(3 * r4.num_pixels, device="cuda")
+        r4.forward(m4, out_rgb=i4, sync=True)  # sizes the instance capacity
+        M4 = r4.num_instances
+        del r4
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()  # parameters and image of this workload included below
+        base -= sum(t.numel() * 4 for t in m4.planes.values() if t is not None) + i4.numel() * 4
+        torch.cuda.reset_peak_memory_stats()
+        r4 = Rasterizer(m4, cams4, settings, capacity=int(M4 * 1.02) + 4096)
+        t4 = torch.from_numpy(np.concatenate([t.reshape(-1) for t in I.target_images(cams4, config=4)])).cuda()
+        g4 = m4.empty_grads()
+
+        def step4():
+            r4.forward(m4, out_rgb=i4, sync=False)
+            _, d4 = l1_loss(i4, t4)
+            r4.backward(m4, d4, grads=g4)
+
+        step4()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(max(2, args.steps // 2)):
+            step4()
+        b2.record(stream)
+        torch.cuda.synchronize()
+        ms4 = a.elapsed_time(b2) / max(2, args.steps // 2)
+        out["workload_8M_4k"] = {
+            "workload": "8M clustered Gaussians, SH-1 + 4 SG, 8 orbit views at 3840x2160, fwd+bwd batched",
+            "ms_per_step": round(ms4, 3), "views_per_s": round(8 / (ms4 / 1e3), 2), "instances": int(M4),
+            "status": r4.device_status(),
+            "peak_device_bytes": int(torch.cuda.max_memory_allocated() - base),
+            "workspace_bytes": int(r4.nbytes), "parameter_bytes": int(sum(
+                t.numel() * 4 for t in m4.planes.values() if t is not None))}
+        del r4, m4, i4, t4, g4, sc4
+        torch.cuda.empty_cache()
+
     # ---- end to end: host (pinned) parameters and targets in, loss out, every step, around
     # the same captured step
     host_planes = {p: (None if t is None else t.cpu().pin_memory()) for p, t in model.planes.items()}

@@ -312,15 +312,34 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
         if (h[j]) atomicAdd(&hist[j], h[j]);
 }
 
+// Per-tile [start, end) of the sorted instances: four tile ids per thread (one 16-byte
+// load) plus the two neighbours, which the adjacent threads load too (cache hits).
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ tile_ids,
                                                       const DeviceStatus* st, uint32_t num_tiles,
                                                       uint2* __restrict__ ranges) {
-    const uint32_t m = st->m_clamped;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        const uint32_t t = tile_ids[j];
-        if (t >= num_tiles) continue;  // only after a failed sort (status is set)
-        if (j == 0 || tile_ids[j - 1] != t) ranges[t].x = j;
-        if (j == m - 1 || tile_ids[j + 1] != t) ranges[t].y = j + 1;
+    const uint64_t m = st->m_clamped;  // 64-bit loop index: q + stride cannot wrap
+    const uint64_t nq = (m + 3) / 4;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j0 = 4 * q;
+        uint32_t t[6];  // t[0]: id at j0 - 1, t[1..4]: ids at j0..j0+3, t[5]: id at j0 + 4
+        if (j0 + 4 <= m) {
+            const uint4 v = reinterpret_cast<const uint4*>(tile_ids)[q];
+            t[1] = v.x, t[2] = v.y, t[3] = v.z, t[4] = v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[1 + k] = j0 + k < m ? tile_ids[j0 + k] : 0xffffffffu;
+        }
+        t[0] = j0 > 0 ? tile_ids[j0 - 1] : 0xffffffffu;
+        t[5] = j0 + 4 < m ? tile_ids[j0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t j = j0 + k;
+            const uint32_t c = t[1 + k];
+            if (j >= m || c >= num_tiles) continue;  // c >= num_tiles only after a failed sort
+            if (t[k] != c) ranges[c].x = (uint32_t)j;
+            if (t[k + 2] != c) ranges[c].y = (uint32_t)(j + 1);
+        }
     }
 }
 
@@ -375,8 +394,8 @@ cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t 
                           int64_t num_tiles, uint2* ranges, cudaStream_t s) {
     if (capacity == 0) return cudaSuccess;
     const int threads = 256;
-    const int64_t want = (capacity + threads - 1) / threads;
-    const int blocks = (int)(want < 148 * 64 ? want : 148 * 64);
+    const int64_t want = (capacity / 4 + threads) / threads;
+    const int blocks = (int)(want < 148 * 32 ? want : 148 * 32);
     ranges_kernel<<<blocks, threads, 0, s>>>(keys, st, (uint32_t)num_tiles, ranges);
     return cudaGetLastError();
 }

@@ -41,6 +41,76 @@ __device__ __forceinline__ TileCoord tile_of(const ViewTable& vt, uint32_t g) {
     return c;
 }
 
+// Thread-to-pixel map of a tile: each warp owns an 8-pixel-wide block of 4 * PPT rows
+// (blocks row-major over the tile), lane l takes column l % 8 and rows l / 8 + 4 q,
+// q < PPT.  Compact warp footprints let a whole warp skip a Gaussian whose ellipse misses
+// its block.  Needs tile_w % 8 == 0 and tile_h % (4 PPT) == 0.
+struct WarpBlock {
+    int x0, y0;                // block origin inside the tile
+    float fx0, fx1, fy0, fy1;  // first and last pixel-centre coordinates of the block (image)
+};
+
+template <int PPT>
+__device__ __forceinline__ WarpBlock warp_block(const ViewTable& vt, const TileCoord& tc) {
+    const int w = threadIdx.x >> 5, per_row = vt.tile_w >> 3;
+    WarpBlock b;
+    b.x0 = (w % per_row) * 8;
+    b.y0 = (w / per_row) * 4 * PPT;
+    b.fx0 = (float)(tc.tx * vt.tile_w + b.x0) + 0.5f;
+    b.fx1 = b.fx0 + 7.0f;
+    b.fy0 = (float)(tc.ty * vt.tile_h + b.y0) + 0.5f;
+    b.fy1 = b.fy0 + (float)(4 * PPT - 1);
+    return b;
+}
+
+// Half-extents of the box around the ellipse Q(d) <= 9.01 (Q = A dx^2 + 2B dx dy + C dy^2,
+// the conic), padded by 1/64 pixel: ex = sqrt(9.01 C / det), ey = sqrt(9.01 A / det).  A
+// pixel centre whose support exponent passes the -4.5 test (Q <= 9 up to single-precision
+// rounding, which the 0.1 % slack and the pad cover) lies inside the box, so a warp whose
+// block misses the box would skip the Gaussian at every pixel: skipping it whole changes no
+// result.  A degenerate conic gives an infinite box (never skipped).  Records store
+// (qa, qb, qc) = (-A/2, -B, -C/2).
+__device__ __forceinline__ float2 support_box(float qa, float qb, float qc) {
+    const float A = -2.0f * qa, B = -qb, C = -2.0f * qc;
+    const float det = A * C - B * B;
+    if (!(det > 0.0f)) return make_float2(INFINITY, INFINITY);
+    const float k = kSpanQ / det;
+    return make_float2(sqrtf(k * C) + kSpanPad, sqrtf(k * A) + kSpanPad);
+}
+
+// True when the box of the Gaussian centred at (gx, gy) misses the block (warp-uniform).
+__device__ __forceinline__ bool misses_block(const WarpBlock& wb, float gx, float gy, float ex, float ey) {
+    return gx + ex < wb.fx0 || gx - ex > wb.fx1 || gy + ey < wb.fy0 || gy - ey > wb.fy1;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// The staged batch entries [0, cnt) whose support box reaches the warp's block (and, in
+// the backward, lie below `limit`), in increasing order, written to list[0, count); the
+// lanes test 32 entries at a time.  Warp-collective; returns count.
+__device__ __forceinline__ int warp_hits(const WarpBlock& wb, const float4* s0, const float4* s1, int cnt,
+                                         int limit, uint16_t* list) {
+    const uint32_t lt = lanemask_lt();
+    int count = 0;
+    for (int j0 = 0; j0 < cnt; j0 += 32) {
+        const int j = j0 + (int)(threadIdx.x & 31);
+        bool hit = false;
+        if (j < cnt && j < limit) {
+            const float4 a = s0[j], b = s1[j];
+            hit = !misses_block(wb, a.x, a.y, b.z, b.w);
+        }
+        const uint32_t bal = __ballot_sync(kFullMask, hit);
+        if (hit) list[count + __popc(bal & lt)] = (uint16_t)j;
+        count += __popc(bal);
+    }
+    __syncwarp();
+    return count;
+}
+
 // Tile range clipped to the instances actually written (all of them unless overflowed).
 __device__ __forceinline__ uint2 clamp_range(uint2 r, uint32_t m) {
     r.y = min(r.y, m);
@@ -75,15 +145,16 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     float4* s0 = sbuf;
     float4* s1 = sbuf + batch;
     float4* s2 = sbuf + 2 * batch;
+    uint16_t* wlist = reinterpret_cast<uint16_t*>(sbuf + 3 * batch) + (threadIdx.x >> 5) * batch;
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
-    const int lx = threadIdx.x % vt.tile_w, ly = threadIdx.x / vt.tile_w;
-    const int rows = vt.tile_h / PPT;
+    const WarpBlock wb = warp_block<PPT>(vt, tc);
+    const int lx = wb.x0 + (threadIdx.x & 7), ly = wb.y0 + ((threadIdx.x >> 3) & 3);
     FwdPixel P[PPT];
     bool all_done = true;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly + q * rows;
+        const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly + 4 * q;
         P[q].inside = x < cam.W && y < cam.H;
         P[q].pxc = (float)x + 0.5f;
         P[q].pyc = (float)y + 0.5f;
@@ -100,12 +171,16 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         const int cnt = min(batch, n - base);
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
             const uint32_t id = min(vals[range.x + base + j], R - 1);  // ids are < R by construction
-            s0[j] = rec0[id];
-            s1[j] = rec1[id];
+            const float4 r0 = rec0[id], r1 = rec1[id];
+            const float2 box = support_box(r0.z, r0.w, r1.x);
+            s0[j] = r0;
+            s1[j] = make_float4(r1.x, r1.y, box.x, box.y);  // depth and radius are not needed here
             s2[j] = rec2[id];
         }
         __syncthreads();
-        for (int k = 0; !all_done && k < cnt; ++k) {
+        const int hits = warp_hits(wb, s0, s1, cnt, cnt, wlist);
+        for (int i = 0; !all_done && i < hits; ++i) {
+            const int k = wlist[i];
             const float4 a = s0[k];
             const float4 b = s1[k];
             all_done = true;
@@ -113,9 +188,9 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
             for (int q = 0; q < PPT; ++q) {
                 FwdPixel& p = P[q];
                 if (!p.done) {
-                    ++p.evaluated;
                     const float power = support_power(a.z, a.w, b.x, a.x - p.pxc, a.y - p.pyc);
                     if (power >= kSupportPower) {  // also skips a NaN exponent
+                        ++p.evaluated;
                         const float alpha = fminf(kAlphaMax, b.y * __expf(power));
                         if (alpha >= kAlphaMin) {
                             const float Tn = p.T * (1.0f - alpha);
@@ -204,11 +279,12 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     float4* s1 = sbuf + batch;
     float4* s2 = sbuf + 2 * batch;
     uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
+    uint16_t* wlist = reinterpret_cast<uint16_t*>(sid + batch) + (threadIdx.x >> 5) * batch;
     __shared__ uint32_t s_max_last;
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
-    const int lx = threadIdx.x % vt.tile_w, ly = threadIdx.x / vt.tile_w;
-    const int rows = vt.tile_h / PPT;
+    const WarpBlock wb = warp_block<PPT>(vt, tc);
+    const int lx = wb.x0 + (threadIdx.x & 7), ly = wb.y0 + ((threadIdx.x >> 3) & 3);
     const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
@@ -218,7 +294,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     uint32_t my_last = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly + q * rows;
+        const int x = tc.tx * vt.tile_w + lx, y = tc.ty * vt.tile_h + ly + 4 * q;
         BwdPixel& p = P[q];
         p.pxc = (float)x + 0.5f;
         p.pyc = (float)y + 0.5f;
@@ -249,16 +325,21 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
         __syncthreads();
         for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) {
             const uint32_t id = min(vals[range.x + lo + j], R32 - 1);  // ids are < R by construction
+            const float4 r0 = rec0[id], r1 = rec1[id];
+            const float2 box = support_box(r0.z, r0.w, r1.x);
             sid[j] = id;
-            s0[j] = rec0[id];
-            s1[j] = rec1[id];
+            s0[j] = r0;
+            s1[j] = make_float4(r1.x, r1.y, box.x, box.y);
             s2[j] = rec2[id];
         }
         __syncthreads();
-        for (int k = min(hi, warp_last) - 1; k >= lo; --k) {
-            const float4 a = s0[k - lo];
-            const float4 b = s1[k - lo];
-            const float4 c = s2[k - lo];
+        const int hits = warp_hits(wb, s0, s1, hi - lo, warp_last - lo, wlist);
+        for (int i = hits - 1; i >= 0; --i) {
+            const int j = wlist[i];
+            const int k = lo + j;
+            const float4 a = s0[j];
+            const float4 b = s1[j];
+            const float4 c = s2[j];
             float d[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) d[i] = 0.0f;
@@ -298,7 +379,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
             if (__any_sync(kFullMask, any)) {
                 const float s8 = warp_sum8(d, lane);
                 const float s9 = warp_sum(d[8]);
-                const uint32_t id = sid[k - lo];
+                const uint32_t id = sid[j];
                 if ((lane & 3) == 0) {  // lanes 0, 4, ..., 28 hold values 0..7
                     const int vi = (lane >> 2) & 7;
                     float* dst = reinterpret_cast<float*>(grad2d + (vi >> 2) * R + id) + (vi & 3);
@@ -346,10 +427,10 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 
 }  // namespace
 
-// Pixels per thread of the blend kernels: 2 when the tile splits into two halves of at
-// least one warp each, else 1.
+// Pixels per thread of the backward kernel: 2 when the tile splits into warp blocks of
+// 8 x 8 pixels (tile sides are multiples of 8), else 1.
 static int pixels_per_thread(const ViewTable& vt) {
-    return (vt.tile_h % 2 == 0 && vt.tile_w * vt.tile_h / 2 >= 32) ? 2 : 1;
+    return (vt.tile_h % 8 == 0 && vt.tile_w % 8 == 0) ? 2 : 1;
 }
 
 template <int PPT>
@@ -358,7 +439,7 @@ static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uin
                              float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
                              const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
-    const size_t smem = (size_t)batch * 3 * sizeof(float4);
+    const size_t smem = (size_t)batch * (3 * sizeof(float4) + (threads / 32) * sizeof(uint16_t));
     cudaError_t e = cudaFuncSetAttribute(blend_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // with no records every range is empty and no id is read; the kernel still writes bg
@@ -374,7 +455,7 @@ static cudaError_t blend_backward_ppt(const ViewTable& vt, const uint2* ranges, 
                                       const float* pix_T, const uint32_t* pix_last, const float* dL_drgb,
                                       float4* grad2d, int64_t R, const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
-    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t));
+    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t) + (threads / 32) * sizeof(uint16_t));
     cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

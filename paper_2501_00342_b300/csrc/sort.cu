@@ -44,10 +44,10 @@ __global__ void __launch_bounds__(256) histogram_kernel(const KeyT* __restrict__
     extern __shared__ uint32_t h[];  // [passes][RADIX]
     for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) h[j] = 0;
     __syncthreads();
-    const uint32_t m = *m_ptr;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < m; base += stride) {
-        const uint32_t idx = base + threadIdx.x;
+    const uint64_t m = *m_ptr;  // 64-bit loop index: base + stride cannot wrap
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const uint64_t idx = base + threadIdx.x;
         const bool valid = idx < m;
         const unsigned long long k = valid ? (unsigned long long)keys[idx] : 0ull;
         const uint32_t active = __ballot_sync(kFullMask, valid);
@@ -84,12 +84,22 @@ __global__ void histogram_scan_kernel(const uint32_t* __restrict__ hist, uint32_
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x) goff[p * RADIX + d] = s[d];
 }
 
-// Items per thread: 15 for 64-bit keys, 24 for 32-bit keys (about the same registers).
+// Items per thread: 15 for 64-bit keys, 22 for 32-bit keys (about the same registers; with
+// 9-bit digits three CTAs fit an SM's shared memory).
 template <typename KeyT>
 struct SortShape {
-    static constexpr int ITEMS = sizeof(KeyT) == 8 ? 15 : 24;
+    static constexpr int ITEMS = sizeof(KeyT) == 8 ? 15 : 22;
     static constexpr int TILE = kSortThreads * ITEMS;
 };
+
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 
 template <typename KeyT, int RB>
 struct OnesweepSmem {
@@ -103,6 +113,7 @@ struct OnesweepSmem {
             uint32_t vals[TILE];
         } stage;
     } u;
+    uint32_t vbuf[TILE];  // the tile's values, copied in while the keys are ranked
     uint32_t digit_start[RADIX];
     uint32_t gbase[RADIX];
     uint32_t wsum[WARPS];
@@ -124,9 +135,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t dmask = (1u << width) - 1u;
     if (threadIdx.x == 0) sm.tile = atomicAdd(counter, 1u);
+    const uint32_t m = *m_ptr;  // in flight together with the tile claim
     for (int j = threadIdx.x; j < WARPS * (RADIX + 1); j += kSortThreads) (&sm.u.warp_hist[0][0])[j] = 0;
     __syncthreads();
-    const uint32_t m = *m_ptr;
     const uint32_t tile = sm.tile;
     const uint64_t tile_start = (uint64_t)tile * kSortTile;
     if (tile_start >= m) return;  // whole CTA: nothing in this tile
@@ -140,6 +151,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t e = wbase + k * 32 + lane;
         key[k] = e < count ? kin[tile_start + e] : (KeyT)0;
+    }
+    // the values travel to shared memory meanwhile (each thread copies what it stages)
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const uint32_t e = wbase + k * 32 + lane;
+        if (e < count) cp_async4(&sm.vbuf[e], vin + tile_start + e);
     }
     // stable warp-level ranking (items past the end go to the sentinel bucket RADIX)
     const uint32_t lt = lanemask_lt();
@@ -236,12 +253,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
         const uint32_t d = (uint32_t)(key[k] >> shift) & dmask;
         rank[k] = e < count ? sm.digit_start[d] + sm.u.warp_hist[warp][d] + rank[k] : 0xffffffffu;
     }
+    cp_async_wait_all();
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         if (rank[k] != 0xffffffffu) {
             sm.u.stage.keys[rank[k]] = key[k];
-            sm.u.stage.vals[rank[k]] = vin[tile_start + wbase + k * 32 + lane];
+            sm.u.stage.vals[rank[k]] = sm.vbuf[wbase + k * 32 + lane];
         }
     }
     __syncthreads();

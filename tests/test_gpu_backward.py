@@ -11,11 +11,11 @@ import oracle as O
 from paper_2501_00342_b300 import inputs as I
 from paper_2501_00342_b300.render import (PLANES, GaussianModel, Rasterizer, RenderSettings, l1_loss,
                                           render)
-from tests.helpers import axis_camera, random_small_scene
+from tests.helpers import axis_camera, check_gradients, random_small_scene
 
 pytestmark = pytest.mark.gpu
 
-GRAD_REL = 1e-3     # max |g - g*| <= GRAD_REL * max |g*| per parameter plane
+GRAD_REL = 1e-3     # |g - g*| <= GRAD_REL * max(|g*|, GRAD_REL * max|g*|) per element (see check_gradients)
 AMBIGUOUS = 1e-5
 
 
@@ -48,27 +48,16 @@ def _oracle_grads(scene, cams, ws, bg=(0.0, 0.0, 0.0)):
     return O.adjoint_pixels(scene, cams, pix, gin, bg)
 
 
-def _compare(scene, g, ref, tol=GRAD_REL):
-    worst = {}
-    for p in PLANES:
-        if ref[p] is None or g[p] is None or ref[p].size == 0:
-            continue
-        a = g[p][..., :scene.n]
-        b = ref[p][..., :scene.n]
-        scale = np.abs(b).max()
-        if scale == 0:
-            assert np.abs(a).max() == 0, p
-            continue
-        rel = np.abs(a - b).max() / scale
-        worst[p] = rel
-        assert rel <= tol, (p, rel)
-    return worst
+def _compare(scene, cams, ws, g, ref, bg=(0.0, 0.0, 0.0)):
+    pix = np.concatenate([O.all_pixels(c, v) for v, c in enumerate(cams)])
+    dL = np.concatenate([w.reshape(3, -1).T for w in ws])
+    return check_gradients(scene, cams, pix, dL, g, ref, PLANES, bg, GRAD_REL)
 
 
 def test_gradients_config0_vs_adjoint():
     sc, cams = I.workload(0)
     ws = _weights(sc, cams, 1)
-    _compare(sc, _gpu_grads(sc, cams, ws), _oracle_grads(sc, cams, ws))
+    _compare(sc, cams, ws, _gpu_grads(sc, cams, ws), _oracle_grads(sc, cams, ws))
 
 
 @pytest.mark.parametrize("L,K,mode", [(1, 4, I.AXIS_FREE), (3, 0, I.AXIS_FREE), (0, 3, I.AXIS_ORTHO_FIXED),
@@ -78,7 +67,7 @@ def test_gradients_colour_variants_vs_adjoint(L, K, mode):
     cams = [axis_camera(48, 40, 60.0, 3.5), I.look_at((1.5, -1.0, 3.0), (0, 0, 0), 40, 48, 55.0)]
     bg = (0.3, 0.1, 0.6)
     ws = _weights(sc, cams, 2, bg)
-    _compare(sc, _gpu_grads(sc, cams, ws, RenderSettings(bg=bg)), _oracle_grads(sc, cams, ws, bg))
+    _compare(sc, cams, ws, _gpu_grads(sc, cams, ws, RenderSettings(bg=bg)), _oracle_grads(sc, cams, ws, bg), bg)
 
 
 def _slice_200():
@@ -93,7 +82,7 @@ def test_fd_slice_200_gaussians_32x32():
     ws = _weights(sc, cams, 3)
     g = _gpu_grads(sc, cams, ws)
     ref = _oracle_grads(sc, cams, ws)
-    _compare(sc, g, ref)
+    _compare(sc, cams, ws, g, ref)
     # central differences of the FP64 oracle on a sample of parameters
     w = ws[0].astype(np.float64)
 

@@ -86,7 +86,8 @@ def _check_image(scene, cams, img, view=0, bg=(0.0, 0.0, 0.0), rast=None, out_T=
     amb = ref["margin"][..., 0] < AMBIGUOUS
     err = np.abs(got - ref["rgb"]).max(0)
     assert err[~amb].max() <= IMG_TOL, (err[~amb].max(), np.unravel_index(np.argmax(np.where(amb, 0, err)), err.shape))
-    assert amb.mean() < 2e-3
+    # ambiguous decisions: fewer than 1e-4 of the pixels (one allowed in a smaller image)
+    assert amb.sum() <= max(1.0, 1e-4 * amb.size), int(amb.sum())
     if out_T is not None and rast is not None:
         b = rast.pixel_base[view]
         T = out_T[b:b + c.height * c.width].view(c.height, c.width).cpu().numpy()

@@ -12,7 +12,8 @@ sizes, so the checks are sampled:
   non-decreasing within a tile, the ranges partition [0, M);
 * image: 12x12 patches around projected Gaussians against the FP64 oracle, 1e-4 max abs;
 * gradients: dL/dpixel non-zero on the sampled patches only; every parameter plane against
-  the FP64 adjoint of those pixels, 1e-3 of the plane's max.
+  the FP64 adjoint of those pixels, |g - g*| <= 1e-3 max(|g*|, 1e-3 max|g*|) per element
+  (cancelling entries: see tests.helpers.check_gradients).
 """
 import numpy as np
 import pytest
@@ -21,6 +22,7 @@ import torch
 import oracle as O
 from paper_2501_00342_b300 import inputs as I
 from paper_2501_00342_b300.render import PLANES, GaussianModel, Rasterizer, RenderSettings
+from tests.helpers import check_gradients
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -174,7 +176,7 @@ def test_sampled_pixels_and_gradients(full):
     ref = O.render_pixels(sc, sub_cams, local)
     got = _gather(rast, cams, img.cpu().numpy(), pix)
     ok = ref["margin"][:, 0] >= AMBIGUOUS
-    assert ok.mean() > 0.99 and (ref["ncontrib"] > 0).mean() > 0.25
+    assert (~ok).sum() <= max(1.0, 1e-4 * len(ok)) and (ref["ncontrib"] > 0).mean() > 0.25
     assert np.abs(got - ref["rgb"]).max(1)[ok].max() <= IMG_TOL
     # gradients of a loss that weighs the sampled pixels only
     keep = ref["margin"][:, 1] >= AMBIGUOUS
@@ -190,14 +192,7 @@ def test_sampled_pixels_and_gradients(full):
     torch.cuda.synchronize()
     assert rast.device_status() == 0
     gref = O.adjoint_pixels(sc, sub_cams, local, w.astype(np.float32).astype(np.float64))
-    checked = 0
-    for p in PLANES:
-        if grads[p] is None or gref[p] is None or gref[p].size == 0:
-            continue
-        a = grads[p].cpu().numpy().astype(np.float64)[..., :sc.n]
-        b = gref[p][..., :sc.n]
-        scale = np.abs(b).max()
-        assert scale > 0, p
-        assert np.abs(a - b).max() <= GRAD_REL * scale, (p, np.abs(a - b).max() / scale)
-        checked += 1
-    assert checked >= 6
+    got = {p: (None if grads[p] is None else grads[p].cpu().numpy()) for p in PLANES}
+    checked = [p for p in PLANES if got[p] is not None and gref[p] is not None and gref[p].size]
+    assert len(checked) >= 6 and all(np.abs(gref[p]).max() > 0 for p in checked)
+    check_gradients(sc, sub_cams, local, w.astype(np.float32), got, gref, checked, rel=GRAD_REL)
