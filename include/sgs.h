@@ -234,6 +234,13 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
                           int32_t digit_bits, void* temp, size_t temp_bytes,
                           cudaStream_t stream);
 
+/* sgs_sort_pairs for 32-bit keys (key_bits <= 32), with the same scratch size
+ * (sgs_sort_temp_bytes).  This is the kernel the rasterizer runs on its 32-bit depth and
+ * tile-id keys: with 16-byte aligned keys and values it takes the persistent bulk-copy
+ * variant, otherwise the plain one.  Exposed for tests of the sort alone. */
+sgs_status sgs_sort_pairs32(uint32_t* keys, uint32_t* vals, int64_t m, int32_t key_bits,
+                            int32_t digit_bits, void* temp, size_t temp_bytes, cudaStream_t stream);
+
 /* Radix sort that allocates nothing and takes no scratch argument.  The paper has no
  * counterpart to this entry point; it exists for callers that may not obtain device
  * memory themselves -- e.g. a host that owns every device allocation through its own pool

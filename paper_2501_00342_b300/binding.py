@@ -27,7 +27,8 @@ REGION = dict(STATUS=0, REC0=1, REC1=2, REC2=3, RECT=4, TILES=5, OFFSETS=6, KEYS
 EXPORTS = ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
            "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
            "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss", "sgs_status_string",
-           "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc", "sgs_selftest_lookback")
+           "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc", "sgs_selftest_lookback",
+           "sgs_sort_pairs32")
 
 SORT_NOALLOC_MAX_PAIRS = 1 << 18
 
@@ -107,6 +108,8 @@ def lib():
         L.sgs_set_events.restype = st
         L.sgs_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, i32, vp]
         L.sgs_sort_pairs_noalloc.restype = st
+        L.sgs_sort_pairs32.argtypes = [vp, vp, i64, i32, i32, vp, C.c_size_t, vp]
+        L.sgs_sort_pairs32.restype = st
         L.sgs_selftest_lookback.argtypes = [vp, i64, vp, vp, vp]
         L.sgs_selftest_lookback.restype = st
         for f in ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
@@ -219,6 +222,11 @@ def sort_temp_bytes(m, key_bits, digit_bits) -> int:
 def sort_pairs(keys_ptr, vals_ptr, m, key_bits, digit_bits, temp_ptr, temp_bytes, stream):
     check("sgs_sort_pairs", lib().sgs_sort_pairs(keys_ptr, vals_ptr, int(m), int(key_bits), int(digit_bits),
                                                  temp_ptr, int(temp_bytes), stream))
+
+
+def sort_pairs32(keys_ptr, vals_ptr, m, key_bits, digit_bits, temp_ptr, temp_bytes, stream):
+    check("sgs_sort_pairs32", lib().sgs_sort_pairs32(keys_ptr, vals_ptr, int(m), int(key_bits), int(digit_bits),
+                                                     temp_ptr, int(temp_bytes), stream))
 
 
 def sort_pairs_noalloc(keys_ptr, vals_ptr, m, key_bits, digit_bits, stream):

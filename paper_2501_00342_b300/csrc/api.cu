@@ -431,6 +431,36 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
     return SGS_OK;
 }
 
+sgs_status sgs_sort_pairs32(uint32_t* keys, uint32_t* vals, int64_t m, int32_t key_bits,
+                            int32_t digit_bits, void* temp, size_t temp_bytes, cudaStream_t stream) {
+    size_t need = 0;
+    if (key_bits > 32 || sgs_sort_temp_bytes(m, key_bits, digit_bits, &need) != SGS_OK) return SGS_ERR_INVALID;
+    if (m == 0) return SGS_OK;
+    if (!keys || !vals || !temp || temp_bytes < need || ((uintptr_t)temp & 255u) != 0) return SGS_ERR_INVALID;
+    unsigned char* t = static_cast<unsigned char*>(temp);
+    DeviceStatus* st = reinterpret_cast<DeviceStatus*>(t);
+    size_t off = 256;
+    auto take = [&](size_t b) {
+        unsigned char* p = t + off;
+        off += align256(b);
+        return p;
+    };
+    // the same layout as sgs_sort_pairs (its 8-byte key slots hold 4-byte keys here)
+    uint32_t* k1 = reinterpret_cast<uint32_t*>(take(8 * (size_t)m));
+    uint32_t* v1 = reinterpret_cast<uint32_t*>(take(4 * (size_t)m));
+    int passes, rb;
+    sort_digit_plan(0, key_bits, digit_bits, &passes, &rb);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(take(4 * (size_t)kHistEntries));
+    uint32_t* goff = reinterpret_cast<uint32_t*>(take(4 * (size_t)kHistEntries));
+    uint32_t* counters = reinterpret_cast<uint32_t*>(take(4 * kMaxSortPasses));
+    unsigned long long* lb = reinterpret_cast<unsigned long long*>(take(8 * sort_lookback_entries(m, rb)));
+    SGS_TRY(launch_sort_init(st, (uint32_t)m, stream));
+    SGS_TRY(launch_sort(keys, vals, k1, v1, &st->m_clamped, m, 0, key_bits, digit_bits, hist, goff, counters, lb,
+                        st, stream, nullptr));
+    if (passes & 1) SGS_TRY(launch_copy_pairs(k1, v1, keys, vals, m, stream));
+    return SGS_OK;
+}
+
 sgs_status sgs_selftest_lookback(const uint64_t* slots, int64_t num_slots, uint64_t* sum,
                                  int32_t* status, cudaStream_t stream) {
     if (num_slots < 0 || !sum || !status || (num_slots > 0 && !slots)) return SGS_ERR_INVALID;

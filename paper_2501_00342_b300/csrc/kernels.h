@@ -104,6 +104,8 @@ cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count,
                            float* dL_dimg, cudaStream_t s);
 cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
                               uint32_t* vd, int64_t m, cudaStream_t s);
+cudaError_t launch_copy_pairs(const uint32_t* ks, const uint32_t* vs, uint32_t* kd, uint32_t* vd, int64_t m,
+                              cudaStream_t s);
 cudaError_t launch_sort_init(DeviceStatus* st, uint32_t m, cudaStream_t s);
 
 }  // namespace sgs

@@ -1,5 +1,6 @@
 """The onesweep radix sort on its own, against a stable sort: random, adversarial and
-ragged inputs, every digit width, key widths 1..64."""
+ragged inputs, every digit width, key widths 1..64; the 32-bit key path (persistent
+bulk-copy kernel when aligned, plain kernel otherwise) on tile-boundary sizes."""
 import numpy as np
 import pytest
 import torch
@@ -72,4 +73,60 @@ def test_sort_large():
     vals = np.arange(m, dtype=np.uint32)
     ks, vs = _sort_gpu(keys, vals, 46, 8)
     ek, ev = _expect(keys, vals, 46)
+    assert (ks == ek).all() and (vs == ev).all()
+
+
+def _sort32_gpu(keys, vals, key_bits, digit_bits, offset=0):
+    """Sorts on the device; offset > 0 shifts both arrays by `offset` elements inside
+    larger buffers (4-byte aligned only: the plain kernel)."""
+    m = len(keys)
+    kb = torch.zeros(m + offset, dtype=torch.int32, device="cuda")
+    vb = torch.zeros(m + offset, dtype=torch.int32, device="cuda")
+    kb[offset:] = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    vb[offset:] = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    nb = B.sort_temp_bytes(m, key_bits, digit_bits)
+    temp = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+    B.sort_pairs32(kb[offset:].data_ptr(), vb[offset:].data_ptr(), m, key_bits, digit_bits, temp.data_ptr(), nb,
+                   torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return kb[offset:].cpu().numpy().view(np.uint32), vb[offset:].cpu().numpy().view(np.uint32)
+
+
+def _expect32(keys, vals, key_bits):
+    masked = keys & np.uint32((1 << key_bits) - 1) if key_bits < 32 else keys
+    order = np.argsort(masked, kind="stable")
+    return keys[order], vals[order]
+
+
+@pytest.mark.parametrize("m", [1, 31, 4095, 4096, 4097, 8192, 12289, 100_003, (1 << 20) + 3])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_sort32_sizes(m, offset):
+    rng = np.random.default_rng(m + offset)
+    keys = rng.integers(0, 1 << 17, m).astype(np.uint32)
+    keys[::5] = keys[min(1, m - 1)]  # ties
+    vals = np.arange(m, dtype=np.uint32)
+    ks, vs = _sort32_gpu(keys, vals, 17, 9, offset)
+    ek, ev = _expect32(keys, vals, 17)
+    assert (ks == ek).all() and (vs == ev).all()
+
+
+@pytest.mark.parametrize("digit", [4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("key_bits", [1, 9, 17, 31, 32])
+def test_sort32_digit_widths(digit, key_bits):
+    rng = np.random.default_rng(1000 + digit * 100 + key_bits)
+    m = 70_001
+    keys = rng.integers(0, 1 << 32, m, dtype=np.uint64).astype(np.uint32)
+    vals = rng.integers(0, 1 << 32, m, dtype=np.uint64).astype(np.uint32)
+    ks, vs = _sort32_gpu(keys, vals, key_bits, digit)
+    ek, ev = _expect32(keys, vals, key_bits)
+    assert (ks == ek).all() and (vs == ev).all()
+
+
+def test_sort32_large_depth_keys():
+    rng = np.random.default_rng(3)
+    m = 30_000_000
+    keys = rng.uniform(0.2, 60.0, m).astype(np.float32).view(np.uint32)
+    vals = np.arange(m, dtype=np.uint32)
+    ks, vs = _sort32_gpu(keys, vals, 32, 8)
+    ek, ev = _expect32(keys, vals, 32)
     assert (ks == ek).all() and (vs == ev).all()
