@@ -235,9 +235,8 @@ sgs_status sgs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t m, int32_t key
                           cudaStream_t stream);
 
 /* sgs_sort_pairs for 32-bit keys (key_bits <= 32), with the same scratch size
- * (sgs_sort_temp_bytes).  This is the kernel the rasterizer runs on its 32-bit depth and
- * tile-id keys: with 16-byte aligned keys and values it takes the persistent bulk-copy
- * variant, otherwise the plain one.  Exposed for tests of the sort alone. */
+ * (sgs_sort_temp_bytes).  This is the kernel instantiation the rasterizer runs on its
+ * 32-bit depth and tile-id keys.  Exposed for tests of the sort alone. */
 sgs_status sgs_sort_pairs32(uint32_t* keys, uint32_t* vals, int64_t m, int32_t key_bits,
                             int32_t digit_bits, void* temp, size_t temp_bytes, cudaStream_t stream);
 

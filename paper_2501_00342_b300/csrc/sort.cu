@@ -291,299 +291,6 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     }
 }
 
-// ---- chunked LSD pass for 32-bit keys: count, scan, scatter (no look-back) ----
-//
-// The keys are cut into chunks of G tiles (G chosen on the host so that there are about
-// 1200-2400 chunks).  count: each CTA counts its chunk's digits.  scan: per digit, an
-// exclusive scan over the chunks, plus the digit's global start, gives every chunk its
-// first output position per digit.  scatter: each CTA walks its chunk tile by tile (keys
-// and values of the next tile copied into shared memory asynchronously meanwhile), ranks
-// each tile stably with warp match-any, stages it in place in sorted order and writes each
-// digit's run from a running per-digit position.  Nothing waits on another CTA, at the
-// cost of reading the keys twice per pass.
-constexpr int kChunkItems = 16;
-constexpr int kChunkTile = kSortThreads * kChunkItems;  // 4096 pairs
-constexpr int kChunkTarget = 1184;                      // about 4 waves of CTAs on 148 SMs x 2
-
-template <int RB>
-struct ChunkSmem {
-    static constexpr int RADIX = 1 << RB;
-    static constexpr int WARPS = kSortThreads / 32;
-    uint32_t kbuf[2][kChunkTile];
-    uint32_t vbuf[2][kChunkTile];
-    uint32_t warp_hist[WARPS][RADIX + 1];  // +1: sentinel bucket of the ragged tail
-    uint32_t digit_start[RADIX];
-    uint32_t running[RADIX];
-    uint32_t wsum[WARPS];
-};
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Per-warp stable ranking of ITEMS warp-striped keys of one tile into warp_hist (counts
-// per digit); rank[k] = position of the key among the warp's earlier keys of its digit.
-template <int RADIX, int ITEMS>
-__device__ __forceinline__ void warp_rank(const uint32_t (&key)[ITEMS], uint32_t (&rank)[ITEMS], uint32_t wbase,
-                                          uint32_t count, int shift, uint32_t dmask, uint32_t* hist) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        const uint32_t e = wbase + k * 32 + lane;
-        const uint32_t d = e < count ? (key[k] >> shift) & dmask : RADIX;
-        const uint32_t peers = digit_peers<ilog2(RADIX) + 1>(d);
-        const int leader = 31 - __clz(peers);
-        uint32_t prior = 0;
-        if (lane == leader) {
-            prior = hist[d];
-            hist[d] = prior + __popc(peers);
-        }
-        prior = __shfl_sync(kFullMask, prior, leader);
-        rank[k] = prior + __popc(peers & lt);
-        __syncwarp();
-    }
-}
-
-template <int RB>
-__global__ void __launch_bounds__(kSortThreads) chunk_count_kernel(const uint32_t* __restrict__ keys,
-                                                                   const uint32_t* m_ptr, uint32_t chunk,
-                                                                   int shift, int width, uint32_t nchunks,
-                                                                   uint32_t* __restrict__ counts) {
-    constexpr int RADIX = 1 << RB;
-    constexpr int WARPS = kSortThreads / 32;
-    __shared__ uint32_t h[WARPS][RADIX + 1];
-    for (int j = threadIdx.x; j < WARPS * (RADIX + 1); j += kSortThreads) (&h[0][0])[j] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t dmask = (1u << width) - 1u;
-    const uint64_t m = *m_ptr;
-    const uint64_t c0 = (uint64_t)blockIdx.x * chunk;
-    const uint64_t c1 = c0 + chunk < m ? c0 + chunk : m;
-    // four keys per thread per step (16-byte loads; chunk starts are multiples of 4096);
-    // the trip count is the same for all lanes of a warp, keys past the end count nowhere
-    const uint64_t nq = (c1 > c0 ? c1 - c0 + 3 : 0) / 4;
-    for (uint64_t qq = (uint64_t)(threadIdx.x & ~31u); qq < nq; qq += kSortThreads) {
-        const uint64_t q = c0 / 4 + qq + lane;
-        uint32_t kk[4] = {0u, 0u, 0u, 0u};
-        if (4 * q + 4 <= c1) {
-            const uint4 v = reinterpret_cast<const uint4*>(keys)[q];
-            kk[0] = v.x, kk[1] = v.y, kk[2] = v.z, kk[3] = v.w;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) kk[i] = 4 * q + i < c1 ? keys[4 * q + i] : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t d = 4 * q + i < c1 ? (kk[i] >> shift) & dmask : RADIX;
-            const uint32_t peers = digit_peers<RB + 1>(d);
-            if (lane == 31 - __clz(peers)) h[warp][d] += __popc(peers);
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < RADIX; d += kSortThreads) {
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) acc += h[w][d];
-        counts[(size_t)d * nchunks + blockIdx.x] = acc;
-    }
-}
-
-// One CTA per digit: exclusive scan over the chunks, offset by the digit's global start.
-template <int RB>
-__global__ void __launch_bounds__(1024) chunk_scan_kernel(uint32_t* __restrict__ counts, uint32_t nchunks,
-                                                          const uint32_t* __restrict__ goff) {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    uint32_t* row = counts + (size_t)blockIdx.x * nchunks;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = goff[blockIdx.x];
-    __syncthreads();
-    for (uint32_t base = 0; base < nchunks; base += 1024) {
-        const uint32_t j = base + threadIdx.x;
-        const uint32_t v = j < nchunks ? row[j] : 0u;
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFullMask, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = wsum[lane];
-            uint32_t inc = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFullMask, inc, o);
-                if (lane >= o) inc += y;
-            }
-            wsum[lane] = inc - w;
-        }
-        __syncthreads();
-        const uint32_t c = carry;
-        if (j < nchunks) row[j] = c + wsum[warp] + x - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = c + wsum[31] + x;
-        __syncthreads();
-    }
-}
-
-// Copies the pairs [t0, t0 + count) of the chunk into buffer b (16 bytes per copy where
-// possible, 4 at a ragged end).
-template <int RB>
-__device__ __forceinline__ void chunk_load(ChunkSmem<RB>& sm, int b, const uint32_t* kin, const uint32_t* vin,
-                                           uint64_t t0, uint32_t count) {
-    for (uint32_t q = threadIdx.x; 4 * q < count; q += kSortThreads) {
-        if (4 * q + 4 <= count) {
-            cp_async16(&sm.kbuf[b][4 * q], kin + t0 + 4 * q);
-            cp_async16(&sm.vbuf[b][4 * q], vin + t0 + 4 * q);
-        } else {
-            for (uint32_t e = 4 * q; e < count; ++e) {
-                cp_async4(&sm.kbuf[b][e], kin + t0 + e);
-                cp_async4(&sm.vbuf[b][e], vin + t0 + e);
-            }
-        }
-    }
-    cp_async_commit();
-}
-
-template <int RB>
-__global__ void __launch_bounds__(kSortThreads, 2) chunk_scatter_kernel(
-    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* m_ptr, uint32_t chunk, int shift, int width, uint32_t nchunks,
-    const uint32_t* __restrict__ offsets) {
-    using Smem = ChunkSmem<RB>;
-    constexpr int RADIX = Smem::RADIX;
-    constexpr int WARPS = Smem::WARPS;
-    constexpr int DPT = (RADIX + kSortThreads - 1) / kSortThreads;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t dmask = (1u << width) - 1u;
-    const uint64_t m = *m_ptr;
-    const uint64_t c0 = (uint64_t)blockIdx.x * chunk;
-    if (c0 >= m) return;
-    const uint64_t c1 = c0 + chunk < m ? c0 + chunk : m;
-    const int ntile = (int)((c1 - c0 + kChunkTile - 1) / kChunkTile);
-#pragma unroll
-    for (int i = 0; i < DPT; ++i) {
-        const int d = threadIdx.x * DPT + i;
-        if (d < RADIX) sm.running[d] = offsets[(size_t)d * nchunks + blockIdx.x];
-    }
-    auto tile_count = [&](int i) {
-        const uint64_t t0 = c0 + (uint64_t)i * kChunkTile;
-        return (uint32_t)(c1 - t0 < (uint64_t)kChunkTile ? c1 - t0 : kChunkTile);
-    };
-    chunk_load<RB>(sm, 0, kin, vin, c0, tile_count(0));
-    for (int i = 0; i < ntile; ++i) {
-        const int b = i & 1;
-        const uint32_t count = tile_count(i);
-        if (i + 1 < ntile) {  // the other buffer was released at the end of the last tile
-            chunk_load<RB>(sm, b ^ 1, kin, vin, c0 + (uint64_t)(i + 1) * kChunkTile, tile_count(i + 1));
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        for (int j = threadIdx.x; j < WARPS * (RADIX + 1); j += kSortThreads) (&sm.warp_hist[0][0])[j] = 0;
-        __syncthreads();  // every thread's copies of tile i have landed; histograms clear
-        uint32_t key[kChunkItems], rank[kChunkItems];
-        const uint32_t wbase = warp * 32 * kChunkItems;
-#pragma unroll
-        for (int k = 0; k < kChunkItems; ++k) {
-            const uint32_t e = wbase + k * 32 + lane;
-            key[k] = e < count ? sm.kbuf[b][e] : 0u;
-        }
-        warp_rank<RADIX, kChunkItems>(key, rank, wbase, count, shift, dmask, sm.warp_hist[warp]);
-        __syncthreads();
-        uint32_t total[DPT];
-        uint32_t tsum = 0;
-#pragma unroll
-        for (int i2 = 0; i2 < DPT; ++i2) {
-            const int d = threadIdx.x * DPT + i2;
-            uint32_t acc = 0;
-            if (d < RADIX) {
-#pragma unroll
-                for (int w = 0; w < WARPS; ++w) {
-                    const uint32_t c = sm.warp_hist[w][d];
-                    sm.warp_hist[w][d] = acc;
-                    acc += c;
-                }
-            }
-            total[i2] = acc;
-            tsum += acc;
-        }
-        uint32_t x = tsum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFullMask, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) sm.wsum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = lane < WARPS ? sm.wsum[lane] : 0u;
-            uint32_t inc = w;
-#pragma unroll
-            for (int o = 1; o < WARPS; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFullMask, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane < WARPS) sm.wsum[lane] = inc - w;
-        }
-        __syncthreads();
-        {
-            uint32_t run = x - tsum + sm.wsum[warp];
-#pragma unroll
-            for (int i2 = 0; i2 < DPT; ++i2) {
-                const int d = threadIdx.x * DPT + i2;
-                if (d < RADIX) sm.digit_start[d] = run;
-                run += total[i2];
-            }
-        }
-        __syncthreads();
-        uint32_t val[kChunkItems];
-#pragma unroll
-        for (int k = 0; k < kChunkItems; ++k) {
-            const uint32_t e = wbase + k * 32 + lane;
-            const uint32_t d = (key[k] >> shift) & dmask;
-            rank[k] = e < count ? sm.digit_start[d] + sm.warp_hist[warp][d] + rank[k] : 0xffffffffu;
-            val[k] = e < count ? sm.vbuf[b][e] : 0u;
-        }
-        __syncthreads();  // every read of the tile's buffers is done: stage in place
-#pragma unroll
-        for (int k = 0; k < kChunkItems; ++k) {
-            if (rank[k] != 0xffffffffu) {
-                sm.kbuf[b][rank[k]] = key[k];
-                sm.vbuf[b][rank[k]] = val[k];
-            }
-        }
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
-            const uint32_t kk = sm.kbuf[b][j];
-            const uint32_t d = (kk >> shift) & dmask;
-            const uint32_t dest = sm.running[d] + (j - sm.digit_start[d]);
-            if (dest < m) {
-                kout[dest] = kk;
-                vout[dest] = sm.vbuf[b][j];
-            }
-        }
-        __syncthreads();  // the write-out read running, digit_start and the buffer
-#pragma unroll
-        for (int i2 = 0; i2 < DPT; ++i2) {
-            const int d = threadIdx.x * DPT + i2;
-            if (d < RADIX) sm.running[d] += total[i2];
-        }
-    }
-}
-
 template <typename KeyT>
 __global__ void copy_pairs_kernel(const KeyT* __restrict__ ks, const uint32_t* __restrict__ vs,
                                   KeyT* __restrict__ kd, uint32_t* __restrict__ vd, int64_t m) {
@@ -601,43 +308,6 @@ __global__ void sort_init_kernel(DeviceStatus* st, uint32_t m) {
     for (int j = 0; j < 16; ++j) st->tile_counter[j] = 0;
 }
 
-inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-constexpr bool kUseChunked = false;
-
-// Chunk length (a multiple of the tile) that gives at most about kChunkTarget chunks.
-inline uint32_t chunk_len(int64_t capacity) {
-    const int64_t tiles = (capacity + kChunkTile - 1) / kChunkTile;
-    const int64_t g = (tiles + kChunkTarget - 1) / kChunkTarget;
-    return (uint32_t)((g < 1 ? 1 : g) * kChunkTile);
-}
-
-// The passes of a 32-bit key sort on the chunked kernels.  counts holds RADIX x nchunks.
-template <int RB>
-cudaError_t chunk_passes(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* m_ptr,
-                         int64_t capacity, int first_bit, int key_bits, uint32_t* goff, uint32_t* counts,
-                         cudaStream_t s, int passes) {
-    constexpr int RADIX = 1 << RB;
-    const size_t smem = sizeof(ChunkSmem<RB>);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(chunk_scatter_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    const uint32_t chunk = chunk_len(capacity);
-    const uint32_t nchunks = (uint32_t)((capacity + chunk - 1) / chunk);
-    for (int p = 0; p < passes; ++p) {
-        const uint32_t* kin = (p & 1) ? k1 : k0;
-        const uint32_t* vin = (p & 1) ? v1 : v0;
-        uint32_t* kout = (p & 1) ? k0 : k1;
-        uint32_t* vout = (p & 1) ? v0 : v1;
-        const int shift = first_bit + p * RB, width = pass_width(p, RB, first_bit, key_bits);
-        chunk_count_kernel<RB><<<nchunks, kSortThreads, 0, s>>>(kin, m_ptr, chunk, shift, width, nchunks, counts);
-        chunk_scan_kernel<RB><<<RADIX, 1024, 0, s>>>(counts, nchunks, goff + p * RADIX);
-        chunk_scatter_kernel<RB><<<nchunks, kSortThreads, smem, s>>>(kin, vin, kout, vout, m_ptr, chunk, shift,
-                                                                      width, nchunks, counts);
-    }
-    return cudaGetLastError();
-}
-
 template <typename KeyT, int RB>
 cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
                       const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, uint32_t* hist,
@@ -649,14 +319,9 @@ cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
     if (!histogram_ready && (e = launch_fill_u32(hist, 0u, (size_t)passes * RADIX, s)) != cudaSuccess)
         return e;
     if ((e = launch_fill_u32(counters, 0u, kMaxSortPasses, s)) != cudaSuccess) return e;
-    // 32-bit keys in 16-byte aligned buffers take the chunked kernels (no look-back; the
-    // look-back table holds their per-chunk counts instead)
-    const bool chunked = kUseChunked && sizeof(KeyT) == 4 && aligned16(k0) && aligned16(v0) && aligned16(k1) &&
-                         aligned16(v1);
     constexpr int kSortTile = SortShape<KeyT>::TILE;
     const size_t tiles = (size_t)((capacity + kSortTile - 1) / kSortTile);
-    if (!chunked &&
-        (e = launch_fill_u32(reinterpret_cast<uint32_t*>(lookback), 0u, tiles * RADIX * 2, s)) != cudaSuccess)
+    if ((e = launch_fill_u32(reinterpret_cast<uint32_t*>(lookback), 0u, tiles * RADIX * 2, s)) != cudaSuccess)
         return e;
     if (capacity == 0 || tiles == 0 || passes <= 0) {
         if (hist_end) return record_probe(hist_end, s);
@@ -673,11 +338,6 @@ cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
     }
     histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : (RADIX > 1024 ? 1024 : RADIX), 0, s>>>(hist, goff);
     if (hist_end && (e = record_probe(hist_end, s)) != cudaSuccess) return e;
-    if constexpr (sizeof(KeyT) == 4) {
-        if (chunked)
-            return chunk_passes<RB>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, goff,
-                                    reinterpret_cast<uint32_t*>(lookback), s, passes);
-    }
     const size_t smem = sizeof(OnesweepSmem<KeyT, RB>);
     if ((e = cudaFuncSetAttribute(onesweep_kernel<KeyT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)

@@ -1,6 +1,6 @@
 """The onesweep radix sort on its own, against a stable sort: random, adversarial and
-ragged inputs, every digit width, key widths 1..64; the 32-bit key path (persistent
-bulk-copy kernel when aligned, plain kernel otherwise) on tile-boundary sizes."""
+ragged inputs, every digit width, key widths 1..64; the 32-bit key instantiation (the
+one the rasterizer runs) on tile-boundary sizes and unaligned buffers."""
 import numpy as np
 import pytest
 import torch
@@ -78,7 +78,7 @@ def test_sort_large():
 
 def _sort32_gpu(keys, vals, key_bits, digit_bits, offset=0):
     """Sorts on the device; offset > 0 shifts both arrays by `offset` elements inside
-    larger buffers (4-byte aligned only: the plain kernel)."""
+    larger buffers (4-byte aligned only)."""
     m = len(keys)
     kb = torch.zeros(m + offset, dtype=torch.int32, device="cuda")
     vb = torch.zeros(m + offset, dtype=torch.int32, device="cuda")
