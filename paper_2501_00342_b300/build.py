@@ -22,8 +22,10 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                   "--expt-relaxed-constexpr"]
+    # host code computes per-view single-precision constants the kernels must reproduce:
+    # no contraction of a multiply and an add into one rounding there
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                   "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
 def _obj(src):

@@ -29,10 +29,13 @@ int ceil_log2(int64_t x) {
     return b;
 }
 
+// Tile sides are powers of two of at least 8 (the blend's warps own 8-wide blocks of 4 or
+// 8 rows), with 64-512 pixels per tile (one CTA of at most 512 threads).
 bool valid_tile(int32_t w, int32_t h) {
-    if (w < 1 || h < 1) return false;
+    auto pow2 = [](int32_t x) { return x >= 8 && x <= 64 && (x & (x - 1)) == 0; };
+    if (!pow2(w) || !pow2(h)) return false;
     const int32_t t = w * h;
-    return t == 64 || t == 128 || t == 256 || t == 512;
+    return t >= 64 && t <= 512;
 }
 
 sgs_status check_gaussians(const sgs_gaussians* g) {
@@ -73,6 +76,8 @@ ViewTable view_table(const sgs_plan* p) {
     vt.B = p->B;
     vt.tile_w = p->settings.tile_w;
     vt.tile_h = p->settings.tile_h;
+    vt.inv_tile_w = 1.0f / (float)vt.tile_w;  // exact: powers of two
+    vt.inv_tile_h = 1.0f / (float)vt.tile_h;
     vt.num_tiles = p->num_tiles;
     for (int v = 0; v < p->B; ++v) {
         const sgs_camera& c = p->cams[v];
@@ -86,6 +91,11 @@ ViewTable view_table(const sgs_plan* p) {
         w.W = c.width;
         w.H = c.height;
         w.near_plane = c.near_plane;
+        // single-precision steps, each correctly rounded, as the FP32 projection orders them
+        const float half_w = 0.5f * (float)c.width, half_h = 0.5f * (float)c.height;
+        const float qx = half_w / c.fx, qy = half_h / c.fy;
+        w.limx = 1.3f * qx;
+        w.limy = 1.3f * qy;
         w.tiles_x = p->tiles_x[v];
         w.tiles_y = p->tiles_y[v];
         w.tile_base = (uint32_t)p->tile_base[v];

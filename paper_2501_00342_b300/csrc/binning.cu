@@ -266,11 +266,11 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
             const int TWj = __shfl_sync(kFullMask, TW, jj);
             const int v = (int)(rj / n32);
             uint32_t oj = obase + __shfl_sync(kFullMask, incl - cnt, jj);
-            const RowSpans rs = row_setup(px, py, A, B, C, vt.tile_h, vt.v[v].tiles_y);
+            const RowSpans rs = row_setup(px, py, A, B, C, vt.inv_tile_h, vt.v[v].tiles_y);
             for (int row0 = rs.ty0; row0 <= rs.ty1; row0 += 32) {
                 const int ty = row0 + lane;
                 int c0 = 0, c1 = -1;
-                if (ty <= rs.ty1 && !row_span(rs, px, py, B, ty, vt.tile_w, vt.tile_h, TWj, c0, c1)) c1 = -1;
+                if (ty <= rs.ty1 && !row_span(rs, px, py, B, ty, vt.inv_tile_w, vt.tile_h, TWj, c0, c1)) c1 = -1;
                 const uint32_t len = (uint32_t)(c1 - c0 + 1);
                 uint32_t rincl = len;
 #pragma unroll

@@ -20,12 +20,16 @@ struct View {
     float near_plane;
     int32_t tiles_x, tiles_y;
     uint32_t tile_base;
+    // 1.3 x the half field of view on x/z and y/z: 1.3 * ((0.5 * W) / fx), correctly
+    // rounded single precision in that order (computed on the host)
+    float limx, limy;
     int64_t pixel_base;
 };
 
 struct ViewTable {
     int32_t B;
-    int32_t tile_w, tile_h;
+    int32_t tile_w, tile_h;    // powers of two
+    float inv_tile_w, inv_tile_h;  // exact reciprocals: x * inv == x / tile, bit for bit
     int32_t pad;
     int64_t num_tiles;
     View v[SGS_MAX_VIEWS];
@@ -125,7 +129,7 @@ struct RowSpans {
     bool ok;
 };
 
-__device__ __forceinline__ RowSpans row_setup(float px, float py, float A, float B, float C, int th,
+__device__ __forceinline__ RowSpans row_setup(float px, float py, float A, float B, float C, float inv_th,
                                               int TH) {
     RowSpans r;
     r.ok = false;
@@ -142,8 +146,8 @@ __device__ __forceinline__ RowSpans row_setup(float px, float py, float A, float
     const float t1 = sub_rn(add_rn(add_rn(py, r.ey), kSpanPad), 0.5f);
     const float y0 = ceilf(t0), y1 = floorf(t1);  // pixel rows with centres in the extent
     if (!(y0 <= y1)) return r;
-    const float f0 = fmaxf(floorf(div_rn(y0, (float)th)), 0.0f);
-    const float f1 = fminf(floorf(div_rn(y1, (float)th)), (float)(TH - 1));
+    const float f0 = fmaxf(floorf(mul_rn(y0, inv_th)), 0.0f);
+    const float f1 = fminf(floorf(mul_rn(y1, inv_th)), (float)(TH - 1));
     if (!(f0 <= f1)) return r;
     r.ty0 = (int)f0;
     r.ty1 = (int)f1;
@@ -152,7 +156,7 @@ __device__ __forceinline__ RowSpans row_setup(float px, float py, float A, float
 }
 
 // Tile columns [tx0, tx1] of row ty (false: none).
-__device__ __forceinline__ bool row_span(const RowSpans& r, float px, float py, float B, int ty, int tw,
+__device__ __forceinline__ bool row_span(const RowSpans& r, float px, float py, float B, int ty, float inv_tw,
                                          int th, int TW, int& tx0, int& tx1) {
     const float ly = add_rn((float)(ty * th), 0.5f), hy = sub_rn((float)(ty * th + th), 0.5f);
     const float eyp = add_rn(r.ey, kSpanPad);
@@ -170,8 +174,8 @@ __device__ __forceinline__ bool row_span(const RowSpans& r, float px, float py, 
     const float xs1 = add_rn(add_rn(px, xmax), kSpanPad);
     const float x0 = ceilf(sub_rn(xs0, 0.5f)), x1 = floorf(sub_rn(xs1, 0.5f));
     if (!(x0 <= x1)) return false;
-    const float f0 = fmaxf(floorf(div_rn(x0, (float)tw)), 0.0f);
-    const float f1 = fminf(floorf(div_rn(x1, (float)tw)), (float)(TW - 1));
+    const float f0 = fmaxf(floorf(mul_rn(x0, inv_tw)), 0.0f);
+    const float f1 = fminf(floorf(mul_rn(x1, inv_tw)), (float)(TW - 1));
     if (!(f0 <= f1)) return false;
     tx0 = (int)f0;
     tx1 = (int)f1;

@@ -90,7 +90,7 @@ struct Projected {
 
 // Exact-order projection of one Gaussian into one view.
 __device__ __forceinline__ void project_exact(const View& cam, const float X[3], const Geometry& G,
-                                              int tile_w, int tile_h, Projected& P) {
+                                              float inv_tw, float inv_th, Projected& P) {
     P.visible = false;
     const float* V = cam.V;
 #pragma unroll
@@ -102,8 +102,7 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
     }
     const float tz = P.t[2];
     if (!(tz > cam.near_plane)) return;
-    const float limx = mul_rn(1.3f, div_rn(mul_rn(0.5f, (float)cam.W), cam.fx));
-    const float limy = mul_rn(1.3f, div_rn(mul_rn(0.5f, (float)cam.H), cam.fy));
+    const float limx = cam.limx, limy = cam.limy;
     const float u0 = div_rn(P.t[0], tz), v0 = div_rn(P.t[1], tz);
     P.u = fminf(limx, fmaxf(-limx, u0));
     P.v = fminf(limy, fmaxf(-limy, v0));
@@ -154,10 +153,10 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
     const float px = add_rn(mul_rn(cam.fx, div_rn(P.t[0], tz)), cam.cx);
     const float py = add_rn(mul_rn(cam.fy, div_rn(P.t[1], tz)), cam.cy);
     if (rad != rad || px != px || py != py) return;
-    const float fx0 = floorf(div_rn(sub_rn(px, rad), (float)tile_w));
-    const float fx1 = floorf(div_rn(add_rn(px, rad), (float)tile_w));
-    const float fy0 = floorf(div_rn(sub_rn(py, rad), (float)tile_h));
-    const float fy1 = floorf(div_rn(add_rn(py, rad), (float)tile_h));
+    const float fx0 = floorf(mul_rn(sub_rn(px, rad), inv_tw));  // == division by the tile side
+    const float fx1 = floorf(mul_rn(add_rn(px, rad), inv_tw));
+    const float fy0 = floorf(mul_rn(sub_rn(py, rad), inv_th));
+    const float fy1 = floorf(mul_rn(add_rn(py, rad), inv_th));
     const float x0 = fmaxf(fx0, 0.0f), x1 = fminf(fx1, (float)(cam.tiles_x - 1));
     const float y0 = fmaxf(fy0, 0.0f), y1 = fminf(fy1, (float)(cam.tiles_y - 1));
     P.px = px;
@@ -174,24 +173,21 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
 // Tiles the ellipse reaches (0: the Gaussian is culled), and the packed row table the
 // duplicate kernel reads (16 words): word 0 = first row | rows << 16; words 1..15 = first
 // column | (tiles in the earlier rows) << 16 per row.  More than kSpanRows rows or more
-// than 65535 tiles mark a table the kernel recomputes instead.
-__device__ __forceinline__ uint32_t count_tiles(const Projected& P, const View& cam, int tw, int th,
-                                                uint32_t table[16]) {
-    const RowSpans rs = row_setup(P.px, P.py, P.A, P.B, P.C, th, cam.tiles_y);
+// than 65535 tiles mark a table the kernel recomputes instead.  The table is written to
+// table[k * stride] (a thread's column of a shared-memory array).
+__device__ __forceinline__ uint32_t count_tiles(const Projected& P, const View& cam, const ViewTable& vt,
+                                                uint32_t* table, int stride) {
+    const RowSpans rs = row_setup(P.px, P.py, P.A, P.B, P.C, vt.inv_tile_h, cam.tiles_y);
     uint32_t hits = 0;
-#pragma unroll
-    for (int k = 1; k < 16; ++k) table[k] = 0xffff0000u;
     for (int ty = rs.ty0; ty <= rs.ty1; ++ty) {
         int a0 = 0, a1 = -1;
-        row_span(rs, P.px, P.py, P.B, ty, tw, th, cam.tiles_x, a0, a1);
+        row_span(rs, P.px, P.py, P.B, ty, vt.inv_tile_w, vt.tile_h, cam.tiles_x, a0, a1);
         const int k = ty - rs.ty0;
-        const uint32_t word = (uint32_t)(a1 >= a0 ? a0 : 0) | (min(hits, 0xffffu) << 16);
-#pragma unroll
-        for (int j = 0; j < kSpanRows; ++j)
-            if (j == k) table[1 + j] = word;
+        if (k < kSpanRows) table[(1 + k) * stride] = (uint32_t)(a1 >= a0 ? a0 : 0) | (min(hits, 0xffffu) << 16);
         if (a1 >= a0) hits += (uint32_t)(a1 - a0 + 1);
     }
     const int rows = rs.ty1 - rs.ty0 + 1;
+    for (int k = rows < 0 ? 0 : rows; k < kSpanRows; ++k) table[(1 + k) * stride] = 0xffff0000u;
     const bool fits = rows <= kSpanRows && hits <= 0xffffu;
     table[0] = (uint32_t)rs.ty0 | ((fits ? (uint32_t)rows : kSpanRowsOverflow) << 16);
     return hits;
@@ -207,14 +203,72 @@ __device__ __forceinline__ void view_direction(const View& cam, const float X[3]
     d[2] = dz * inv;
 }
 
+constexpr int kPreThreads = 128;
+
+// A Gaussian's colour parameters held in a column of shared memory (stride kPreThreads):
+// the view loop reads them per view instead of keeping ~40 registers live.
 template <int L, int K, bool FIXED>
-__global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, const ViewTable vt,
-                                                         float4* __restrict__ rec0,
-                                                         float4* __restrict__ rec1,
-                                                         float4* __restrict__ rec2,
-                                                         uint2* __restrict__ rect,
-                                                         uint32_t* __restrict__ tiles,
-                                                         uint4* __restrict__ spans) {
+struct ColourShared {
+    static constexpr int NSH = (L + 1) * (L + 1);
+    static constexpr int NAX = (K > 0 && !FIXED) ? 3 * K : 0;
+    static constexpr int COUNT = 3 * NSH + 3 * K + NAX + K;  // sh, amp, unit axes, sharpness
+    float* p;
+
+    __device__ __forceinline__ float& at(int j) const { return p[j * kPreThreads]; }
+
+    __device__ __forceinline__ void load(const sgs_gaussians& g, int64_t i) const {
+        const int64_t S = g.stride;
+#pragma unroll
+        for (int k = 0; k < 3 * NSH; ++k) at(k) = __ldg(g.sh + k * S + i);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) at(3 * NSH + 3 * k + c) = __ldg(g.sg_amp + (k * 3 + c) * S + i);
+            at(3 * NSH + 3 * K + NAX + k) = __ldg(g.sg_sharp + k * S + i);
+            if (!FIXED) {
+                float m[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
+                const float inv = 1.0f / sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) at(3 * NSH + 3 * K + 3 * k + c) = m[c] * inv;
+            }
+        }
+    }
+
+    // pre-clamp colour at unit direction d (the same arithmetic as ColourParams::eval)
+    __device__ __forceinline__ void eval(const float* d, float* pre) const {
+        float Y[NSH];
+        sh_basis<L>(d[0], d[1], d[2], Y);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pre[c] = 0.5f;
+#pragma unroll
+        for (int k = 0; k < NSH; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pre[c] = fmaf(at(3 * k + c), Y[k], pre[c]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float cosv = FIXED ? d[k]
+                                     : at(3 * NSH + 3 * K + 3 * k) * d[0] + at(3 * NSH + 3 * K + 3 * k + 1) * d[1] +
+                                           at(3 * NSH + 3 * K + 3 * k + 2) * d[2];
+            const float e = expf(at(3 * NSH + 3 * K + NAX + k) * (cosv - 1.0f));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pre[c] = fmaf(at(3 * NSH + 3 * k + c), e, pre[c]);
+        }
+    }
+};
+
+template <int L, int K, bool FIXED>
+__global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_gaussians g, const ViewTable vt,
+                                                                 float4* __restrict__ rec0,
+                                                                 float4* __restrict__ rec1,
+                                                                 float4* __restrict__ rec2,
+                                                                 uint2* __restrict__ rect,
+                                                                 uint32_t* __restrict__ tiles,
+                                                                 uint4* __restrict__ spans) {
+    using CS = ColourShared<L, K, FIXED>;
+    __shared__ float s_colour[CS::COUNT * kPreThreads];
+    __shared__ uint32_t s_table[16 * kPreThreads];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int64_t S = g.stride;
@@ -222,15 +276,15 @@ __global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, 
     const float opacity = __ldg(g.opacity + i);
     Geometry G;
     geometry_exact(g, i, G);
-    ColourParams<L, K, FIXED> cp;
+    const CS cp{s_colour + threadIdx.x};
     cp.load(g, i);
+    uint32_t* table = s_table + threadIdx.x;
     for (int v = 0; v < vt.B; ++v) {
         const View& cam = vt.v[v];
         const int64_t r = (int64_t)v * g.n + i;
         Projected P;
-        project_exact(cam, X, G, vt.tile_w, vt.tile_h, P);
-        uint32_t table[16];
-        const uint32_t hits = P.visible ? count_tiles(P, cam, vt.tile_w, vt.tile_h, table) : 0u;
+        project_exact(cam, X, G, vt.inv_tile_w, vt.inv_tile_h, P);
+        const uint32_t hits = P.visible ? count_tiles(P, cam, vt, table, kPreThreads) : 0u;
         if (hits == 0u) {
             rect[r] = make_uint2(0u, 0u);
             tiles[r] = 0u;
@@ -255,7 +309,8 @@ __global__ void __launch_bounds__(128) preprocess_kernel(const sgs_gaussians g, 
         tiles[r] = hits;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            spans[4 * r + k] = make_uint4(table[4 * k], table[4 * k + 1], table[4 * k + 2], table[4 * k + 3]);
+            spans[4 * r + k] = make_uint4(table[(4 * k) * kPreThreads], table[(4 * k + 1) * kPreThreads],
+                                          table[(4 * k + 2) * kPreThreads], table[(4 * k + 3) * kPreThreads]);
     }
 }
 
@@ -288,7 +343,7 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(
         const float4 g0 = grad2d[r], g1 = grad2d[R + r], g2 = grad2d[2 * R + r];
         const View& cam = vt.v[v];
         Projected P;
-        project_exact(cam, X, G, vt.tile_w, vt.tile_h, P);
+        project_exact(cam, X, G, vt.inv_tile_w, vt.inv_tile_h, P);
         gop += g1.y;
         // colour
         {

@@ -67,8 +67,8 @@ def test_plan_sizes_and_key_bits():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(tw=16, th=12), dict(tw=0, th=16), dict(batch=16), dict(batch=4096), dict(digit=3),
-    dict(digit=11),
+    dict(tw=16, th=12), dict(tw=0, th=16), dict(tw=4, th=32), dict(tw=2, th=32), dict(tw=64, th=4),
+    dict(tw=32, th=32), dict(batch=16), dict(batch=4096), dict(digit=3), dict(digit=11),
 ])
 def test_invalid_settings_rejected(bad):
     cams = [I.look_at((0, 0, 4), (0, 0, 0), 64, 64, 60)]
