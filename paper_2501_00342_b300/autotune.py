@@ -19,7 +19,7 @@ import torch
 
 from .render import GaussianModel, Rasterizer, RenderSettings
 
-TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (16, 8), (32, 8), (8, 8))
+TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 16), (16, 32), (32, 8), (16, 8), (64, 8), (8, 8))
 BATCHES: Tuple[int, ...] = (128, 256, 512)
 DIGITS: Tuple[int, ...] = (8, 9, 10)
 
