@@ -346,10 +346,21 @@ def run_gpu(args):
 
         # ---- render FPS, 1 M Gaussians at 1280x720: SG colour vs SH degree 3
         fps = {}
-        for label, L, K in (("sh1_sg3", 1, 3), ("sh3", 3, 0)):
+        for label, L, K, adaptive in (("sh1_sg3", 1, 3, None), ("sh3", 3, 0, None),
+                                      ("adaptive_sh012_sg3", 2, 3, (0.5, 0.9))):
             sc1, cams1 = I.workload(1, sh_degree=L, num_lobes=K)
-            m1 = GaussianModel.from_scene(sc1)
             cams1 = cams1[:8]
+            if adaptive:
+                # degree 0 for the smaller half of the records, 1 up to the 90th percentile
+                # of the pixel radius, 2 above (the paper: most Gaussians are small)
+                probe = Rasterizer(GaussianModel.from_scene(sc1), cams1[:1], settings)
+                probe.forward(GaussianModel.from_scene(sc1), sync=True)
+                rad = probe.region("REC1", torch.float32)[:4 * sc1.n].view(-1, 4)[:, 3]
+                rad = rad[probe.region("TILES", torch.int32)[:sc1.n] != 0]
+                adaptive = tuple(float(torch.quantile(rad, q).ceil()) for q in adaptive)
+                sc1.sh_adaptive, sc1.sh_radius = 1, adaptive
+                del probe
+            m1 = GaussianModel.from_scene(sc1)
             rs = []
             for c in cams1:
                 r1 = Rasterizer(m1, [c], settings)
@@ -369,8 +380,15 @@ def run_gpu(args):
             fms = max_over_ranks(a.elapsed_time(b2) / (reps * len(rs)))
             fps[label] = {"ms_per_frame": round(fms, 4), "fps": round(1e3 / fms, 1),
                           "floats_per_gaussian": sc1.floats_per_gaussian()}
+            if adaptive:  # share of the visible records that summed bands up to 0, 1, 2
+                rad = torch.cat([r1.region("REC1", torch.float32)[:4 * sc1.n].view(-1, 4)[:, 3][
+                    r1.region("TILES", torch.int32)[:sc1.n] != 0] for r1, _ in rs])
+                deg = torch.where(rad < adaptive[0], 0, torch.where(rad < adaptive[1], 1, 2))
+                fps[label]["thresholds_px"] = list(adaptive)
+                fps[label]["records_per_degree"] = [round(float((deg == d).float().mean()), 4) for d in range(3)]
             del rs, m1
         fps["sg_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["sh1_sg3"]["ms_per_frame"], 4)
+        fps["adaptive_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["adaptive_sh012_sg3"]["ms_per_frame"], 4)
         fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
         out["render_fps"] = fps
 
@@ -553,8 +571,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--tile", type=int, nargs=2, default=(16, 16))
-    ap.add_argument("--batch-depth", type=int, default=256)
+    ap.add_argument("--tile", type=int, nargs=2, default=(16, 32))
+    ap.add_argument("--batch-depth", type=int, default=512)
     ap.add_argument("--digit-bits", type=int, default=9)
     ap.add_argument("--workload", default="batched", choices=("batched", "single", "medium"),
                     help="single: 1M Gaussians, one 1280x720 view; medium: the 3M scene, two "

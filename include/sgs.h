@@ -88,13 +88,22 @@ typedef struct {
  *   sg_amp   [K][3][stride]           lobe amplitudes alpha_k per channel (Eq. 5, 7)
  *   sg_axis  [K][3][stride]           lobe axes mu_k (free-axis mode; NULL otherwise)
  *   sg_sharp [K][stride]              lobe sharpness lambda_k
- * colour = max(0, sum_lm c_lm Y_lm(d) + 0.5 + sum_k alpha_k exp(lambda_k (mu_k.d - 1))). */
+ * colour = max(0, sum_lm c_lm Y_lm(d) + 0.5 + sum_k alpha_k exp(lambda_k (mu_k.d - 1))).
+ *
+ * Adaptive SH degree (Sec. "Mixing Spherical Harmonics and Spherical Gaussians": the SH
+ * degree follows the Gaussian's projected size): with sh_adaptive != 0 the record of
+ * Gaussian i in view v sums the SH bands l <= D only, D = 0 if its 3-sigma radius r (the
+ * integer pixel radius of the projection) < sh_radius[0], D = 1 if r < sh_radius[1],
+ * else D = 2, and never above sh_degree.  Bands above D contribute nothing to that
+ * record's colour and receive no gradient from it.  sh_adaptive = 0: D = sh_degree. */
 typedef struct {
     int64_t n, stride;
     int32_t sh_degree; /* L in 0..3 */
     int32_t num_lobes; /* K in 0..4 (0..3 in SGS_AXIS_ORTHO_FIXED) */
     int32_t axis_mode; /* sgs_axis_mode */
     const float *mean, *scale, *rot, *opacity, *sh, *sg_amp, *sg_axis, *sg_sharp;
+    int32_t sh_adaptive;  /* 0 or 1 */
+    float sh_radius[2];   /* pixel thresholds, 0 <= sh_radius[0] <= sh_radius[1] */
 } sgs_gaussians;
 
 /* Parameter gradients, same layouts as sgs_gaussians (device pointers, overwritten). */

@@ -30,7 +30,8 @@ class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("stride", C.c_int64), ("sh_degree", C.c_int32),
                 ("num_lobes", C.c_int32), ("axis_mode", C.c_int32)] + \
                [(f, C.c_void_p) for f in ("mean", "scale", "rot", "opacity", "sh", "sg_amp",
-                                          "sg_axis", "sg_sharp")]
+                                          "sg_axis", "sg_sharp")] + \
+               [("sh_adaptive", C.c_int32), ("sh_radius", C.c_float * 2)]
 
 
 class _Grads(C.Structure):
@@ -72,6 +73,9 @@ def _scene_struct(sc):
     keep = [_f32(getattr(sc, f)) for f in ("mean", "scale", "rot", "opacity", "sh", "sg_amp",
                                            "sg_axis", "sg_sharp")]
     st = _Scene(sc.n, sc.stride, sc.sh_degree, sc.num_lobes, sc.axis_mode, *[_ptr(a) for a in keep])
+    st.sh_adaptive = int(getattr(sc, "sh_adaptive", 0))
+    r = getattr(sc, "sh_radius", (0.0, 0.0))
+    st.sh_radius[0], st.sh_radius[1] = float(r[0]), float(r[1])
     return st, keep
 
 

@@ -40,7 +40,7 @@ void chain_to_params(const orc_scene* s, const Cam64& k, const Pre64& p, const d
     double gpre[3];
     for (int ch = 0; ch < 3; ++ch) gpre[ch] = p.pre[ch] < 0.0 ? 0.0 : g2[6 + ch];
     double gdir[3] = {0.0, 0.0, 0.0};
-    for (int l = 0; l <= s->sh_degree; ++l)
+    for (int l = 0; l <= p.sh_top; ++l)  // bands above the record's degree get nothing
         for (int m = -l; m <= l; ++m) {
             const int kk = l * l + l + m;
             const double Y = sh_basis(l, m, p.dir);

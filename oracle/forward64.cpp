@@ -194,8 +194,16 @@ Pre64 preprocess(const orc_scene* s, int64_t i, const float* cam) {
     for (int j = 0; j < 3; ++j) p.dvec[j] = p.X[j] - k.campos[j];
     p.dlen = std::sqrt(p.dvec[0] * p.dvec[0] + p.dvec[1] * p.dvec[1] + p.dvec[2] * p.dvec[2]);
     for (int j = 0; j < 3; ++j) p.dir[j] = p.dvec[j] / p.dlen;
+    // SH bands summed: all stored ones, or with adaptive degrees the ones the record's
+    // projected size calls for (its FP32 pixel radius against the two thresholds)
+    p.sh_top = s->sh_degree;
+    if (s->sh_adaptive) {
+        const float r = p.sup.radius;
+        const int D = r < s->sh_radius[0] ? 0 : (r < s->sh_radius[1] ? 1 : 2);
+        p.sh_top = D < s->sh_degree ? D : s->sh_degree;
+    }
     double col[3] = {0.5, 0.5, 0.5};
-    for (int l = 0; l <= s->sh_degree; ++l)
+    for (int l = 0; l <= p.sh_top; ++l)
         for (int m = -l; m <= l; ++m) {
             const int kk = l * l + l + m;
             const double Y = sh_basis(l, m, p.dir);
@@ -324,6 +332,7 @@ void orc_render_pixels(const orc_scene* s, const float* cams, int32_t B, const d
                 for (int ch = 0; ch < 3; ++ch)
                     sig = (sig ^ (uint64_t)(g.pre[ch] < 0.0)) * 1099511628211ull;
                 sig = (sig ^ (uint64_t)(g.clampx * 2 + g.clampy)) * 1099511628211ull;
+                sig = (sig ^ (uint64_t)g.sh_top) * 1099511628211ull;  // adaptive SH degree
             }
             for (int ch = 0; ch < 3; ++ch) out_rgb[3 * p + ch] = C[ch] + T * bg[ch];
             out_T[p] = T;

@@ -286,6 +286,7 @@ Support support_of(const orc_scene* s, int64_t i, const float* cam) {
     o.qa = -0.5f * r.A;
     o.qb = -r.B;
     o.qc = -0.5f * r.C;
+    o.radius = r.r;
     return o;
 }
 

@@ -32,6 +32,12 @@ typedef struct {
     int64_t n, stride;
     int32_t sh_degree, num_lobes, axis_mode; /* axis_mode: 0 free axes, 1 world axes */
     const float *mean, *scale, *rot, *opacity, *sh, *sg_amp, *sg_axis, *sg_sharp;
+    /* Adaptive SH degree (Sec. "Mixing Spherical Harmonics and Spherical Gaussians"): when
+     * sh_adaptive is 1, a record sums the SH bands l <= D, D = 0 below radius threshold
+     * sh_radius[0], 1 below sh_radius[1], else 2, capped at sh_degree; the radius is the
+     * mirror's integer pixel radius ceil(3 sqrt(lambda_max)). */
+    int32_t sh_adaptive;
+    float sh_radius[2];
 } orc_scene;
 
 typedef struct { /* double planes with the same [..][stride] layout as the scene */

@@ -12,6 +12,7 @@ struct Support {
     bool visible;
     uint32_t depth_bits;
     float px, py, qa, qb, qc;
+    float radius;  // ceil(3 sqrt(lambda_max)), pixels
 };
 Support support_of(const orc_scene* s, int64_t i, const float* cam);
 bool in_support(const Support& g, int x, int y);
@@ -44,6 +45,7 @@ struct Pre64 {
     double dvec[3], dlen, dir[3];
     double pre[3], rgb[3];
     double opacity;
+    int sh_top;  // highest SH band the record sums (adaptive degree, else sh_degree)
 };
 Pre64 preprocess(const orc_scene* s, int64_t i, const float* cam);
 

@@ -48,7 +48,8 @@ class Gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("stride", C.c_int64), ("sh_degree", C.c_int32),
                 ("num_lobes", C.c_int32), ("axis_mode", C.c_int32)] + \
                [(f, C.c_void_p) for f in ("mean", "scale", "rot", "opacity", "sh", "sg_amp",
-                                          "sg_axis", "sg_sharp")]
+                                          "sg_axis", "sg_sharp")] + \
+               [("sh_adaptive", C.c_int32), ("sh_radius", C.c_float * 2)]
 
 
 class Grads(C.Structure):

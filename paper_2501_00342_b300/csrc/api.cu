@@ -44,6 +44,9 @@ sgs_status check_gaussians(const sgs_gaussians* g) {
     if (g->num_lobes < 0 || g->num_lobes > 4) return SGS_ERR_INVALID;
     if (g->axis_mode != SGS_AXIS_FREE && g->axis_mode != SGS_AXIS_ORTHO_FIXED) return SGS_ERR_INVALID;
     if (g->axis_mode == SGS_AXIS_ORTHO_FIXED && g->num_lobes > 3) return SGS_ERR_INVALID;
+    if (g->sh_adaptive != 0 && g->sh_adaptive != 1) return SGS_ERR_INVALID;
+    if (g->sh_adaptive && !(g->sh_radius[0] >= 0.0f && g->sh_radius[0] <= g->sh_radius[1]))
+        return SGS_ERR_INVALID;  // also rejects NaN thresholds
     return SGS_OK;
 }
 

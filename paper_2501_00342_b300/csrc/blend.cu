@@ -260,6 +260,12 @@ __device__ __forceinline__ float warp_sum8(const float v[8], int lane) {
     return x;
 }
 
+// grad += (a, b, c, d) as one 16-byte vector reduction in L2 (no return value).
+__device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
 // Per-pixel state of the reverse walk.
 struct BwdPixel {
     float pxc, pyc;
@@ -377,14 +383,15 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                 }
             }
             if (__any_sync(kFullMask, any)) {
+                // lanes 0, 4, ..., 28 hold the sums of values 0..7; lanes 0 and 16 gather
+                // values 0-3 and 4-7 and add them with one 16-byte vector reduction each
                 const float s8 = warp_sum8(d, lane);
                 const float s9 = warp_sum(d[8]);
+                const float u1 = __shfl_down_sync(kFullMask, s8, 4);
+                const float u2 = __shfl_down_sync(kFullMask, s8, 8);
+                const float u3 = __shfl_down_sync(kFullMask, s8, 12);
                 const uint32_t id = sid[j];
-                if ((lane & 3) == 0) {  // lanes 0, 4, ..., 28 hold values 0..7
-                    const int vi = (lane >> 2) & 7;
-                    float* dst = reinterpret_cast<float*>(grad2d + (vi >> 2) * R + id) + (vi & 3);
-                    atomicAdd(dst, s8);
-                }
+                if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
                 if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
             }
         }

@@ -83,6 +83,40 @@ __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const fl
     }
 }
 
+// |m| of a lobe axis, in one written-out operation order (the forward and the backward
+// pass must normalise an axis to the same bits).
+__device__ __forceinline__ float axis_length(const float m[3]) {
+    return sqrtf(fmaf(m[0], m[0], fmaf(m[1], m[1], m[2] * m[2])));
+}
+
+// Pre-clamp colour at unit direction d from the first nsh SH coefficients and the K lobes
+// (Eq. 4, 5, 7, 9).  P provides csh(k, c), camp(k, c), caxis(k, c) (unit axes) and
+// csharp(k).  Every operation is written out (fmaf, no contraction left to the compiler),
+// so that the forward pass, which reads the parameters from shared memory, and the
+// backward pass, which holds them in registers, compute the same bits and take the same
+// colour-clamp decisions.
+template <int L, int K, bool FIXED, class P>
+__device__ __forceinline__ void colour_eval(const P& p, const float* d, float* pre, int nsh) {
+    constexpr int NSH = (L + 1) * (L + 1);
+    float Y[NSH];
+    sh_basis<L>(d[0], d[1], d[2], Y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pre[c] = 0.5f;
+#pragma unroll
+    for (int k = 0; k < NSH; ++k)
+        if (k < nsh) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pre[c] = fmaf(p.csh(k, c), Y[k], pre[c]);
+        }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float cosv = FIXED ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
+        const float e = expf(p.csharp(k) * (cosv - 1.0f));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pre[c] = fmaf(p.camp(k, c), e, pre[c]);
+    }
+}
+
 // Colour parameters of one Gaussian held in registers.
 template <int L, int K, bool FIXED>
 struct ColourParams {
@@ -108,7 +142,7 @@ struct ColourParams {
                 float m[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
-                const float n = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                const float n = axis_length(m);
                 axis_norm[k] = n;
                 const float inv = 1.0f / n;
 #pragma unroll
@@ -117,29 +151,26 @@ struct ColourParams {
         }
     }
 
-    __device__ __forceinline__ float lobe_cos(int k, const float* d) const {
-        if (FIXED) return d[k];
-        return axis[k][0] * d[0] + axis[k][1] * d[1] + axis[k][2] * d[2];
-    }
+    __device__ __forceinline__ float csh(int k, int c) const { return sh[k][c]; }
+    __device__ __forceinline__ float camp(int k, int c) const { return amp[k][c]; }
+    __device__ __forceinline__ float caxis(int k, int c) const { return axis[k][c]; }
+    __device__ __forceinline__ float csharp(int k) const { return sharp[k]; }
+    __device__ __forceinline__ float caxis_norm(int k) const { return axis_norm[k]; }
 
-    // pre-clamp colour at unit direction d
-    __device__ __forceinline__ void eval(const float* d, float* pre) const {
-        float Y[NSH];
-        sh_basis<L>(d[0], d[1], d[2], Y);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) pre[c] = 0.5f;
-#pragma unroll
-        for (int k = 0; k < NSH; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) pre[c] = fmaf(sh[k][c], Y[k], pre[c]);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float e = expf(sharp[k] * (lobe_cos(k, d) - 1.0f));
-#pragma unroll
-            for (int c = 0; c < 3; ++c) pre[c] = fmaf(amp[k][c], e, pre[c]);
-        }
-    }
 };
+
+// Number of SH coefficients a record sums: (D+1)^2 with D = sh_degree, or with adaptive
+// degrees D = 0 / 1 / 2 as the record's integer pixel radius is below sh_radius[0] /
+// below sh_radius[1] / not (capped at the stored degree L).
+template <int L>
+__device__ __forceinline__ int record_sh_coeffs(const sgs_gaussians& g, float radius) {
+    int D = L;
+    if (g.sh_adaptive) {
+        D = radius < g.sh_radius[0] ? 0 : (radius < g.sh_radius[1] ? 1 : 2);
+        D = D < L ? D : L;
+    }
+    return (D + 1) * (D + 1);
+}
 
 // Gradient accumulators of the colour parameters (summed over views).
 template <int L, int K, bool FIXED>
@@ -166,47 +197,49 @@ struct ColourGrads {
         }
     }
 
-    // g_pre: dL/d(pre-clamp colour) at direction d; accumulates into this and returns
-    // dL/dd (ambient) in gd.
-    __device__ __forceinline__ void accumulate(const ColourParams<L, K, FIXED>& p, const float* d,
-                                               const float* g_pre, float* gd) {
+    // g_pre: dL/d(pre-clamp colour) at direction d for a record that sums the first
+    // `nsh` SH coefficients; accumulates into this and returns dL/dd (ambient) in gd.
+    template <class P>
+    __device__ __forceinline__ void accumulate(const P& p, const float* d, const float* g_pre, float* gd,
+                                               int nsh) {
         float Y[NSH];
         sh_basis<L>(d[0], d[1], d[2], Y);
         float gY[NSH];
 #pragma unroll
         for (int k = 0; k < NSH; ++k) {
+            const float on = k < nsh ? 1.0f : 0.0f;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sh[k][c] = fmaf(g_pre[c], Y[k], sh[k][c]);
-            gY[k] = g_pre[0] * p.sh[k][0] + g_pre[1] * p.sh[k][1] + g_pre[2] * p.sh[k][2];
+            for (int c = 0; c < 3; ++c) sh[k][c] = fmaf(g_pre[c] * on, Y[k], sh[k][c]);
+            gY[k] = on * (g_pre[0] * p.csh(k, 0) + g_pre[1] * p.csh(k, 1) + g_pre[2] * p.csh(k, 2));
         }
         gd[0] = gd[1] = gd[2] = 0.0f;
         sh_basis_vjp<L>(d[0], d[1], d[2], gY, gd[0], gd[1], gd[2]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float cs = p.lobe_cos(k, d);
-            const float e = expf(p.sharp[k] * (cs - 1.0f));
+            const float cs = FIXED ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
+            const float e = expf(p.csharp(k) * (cs - 1.0f));
             float s = 0.0f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 amp[k][c] = fmaf(g_pre[c], e, amp[k][c]);
-                s = fmaf(g_pre[c] * p.amp[k][c], e, s);
+                s = fmaf(g_pre[c] * p.camp(k, c), e, s);
             }
             sharp[k] = fmaf(s, cs - 1.0f, sharp[k]);
-            const float gcos = s * p.sharp[k];
+            const float gcos = s * p.csharp(k);
             if (FIXED) {
                 gd[k] += gcos;
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    gd[c] = fmaf(gcos, p.axis[k][c], gd[c]);
+                    gd[c] = fmaf(gcos, p.caxis(k, c), gd[c]);
                     axis[k][c] = fmaf(gcos, d[c], axis[k][c]);
                 }
             }
         }
     }
 
-    __device__ __forceinline__ void store(const ColourParams<L, K, FIXED>& p, const sgs_grads& out,
-                                          int64_t S, int64_t i) const {
+    template <class P>
+    __device__ __forceinline__ void store(const P& p, const sgs_grads& out, int64_t S, int64_t i) const {
 #pragma unroll
         for (int k = 0; k < NSH; ++k)
 #pragma unroll
@@ -218,12 +251,12 @@ struct ColourGrads {
             out.sg_sharp[k * S + i] = sharp[k];
             if (!FIXED) {
                 // mu = m/|m|:  dL/dm = (g - mu (mu . g)) / |m|
-                const float dot = axis[k][0] * p.axis[k][0] + axis[k][1] * p.axis[k][1] +
-                                  axis[k][2] * p.axis[k][2];
-                const float inv = 1.0f / p.axis_norm[k];
+                const float dot = axis[k][0] * p.caxis(k, 0) + axis[k][1] * p.caxis(k, 1) +
+                                  axis[k][2] * p.caxis(k, 2);
+                const float inv = 1.0f / p.caxis_norm(k);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.axis[k][c] * dot) * inv;
+                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.caxis(k, c) * dot) * inv;
             }
         }
     }

@@ -211,7 +211,7 @@ template <int L, int K, bool FIXED>
 struct ColourShared {
     static constexpr int NSH = (L + 1) * (L + 1);
     static constexpr int NAX = (K > 0 && !FIXED) ? 3 * K : 0;
-    static constexpr int COUNT = 3 * NSH + 3 * K + NAX + K;  // sh, amp, unit axes, sharpness
+    static constexpr int COUNT = 3 * NSH + 3 * K + NAX + K + NAX / 3;  // sh, amp, unit axes, sharpness, |axis|
     float* p;
 
     __device__ __forceinline__ float& at(int j) const { return p[j * kPreThreads]; }
@@ -229,33 +229,20 @@ struct ColourShared {
                 float m[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
-                const float inv = 1.0f / sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                const float n = axis_length(m);
+                at(3 * NSH + 3 * K + NAX + K + k) = n;
+                const float inv = 1.0f / n;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) at(3 * NSH + 3 * K + 3 * k + c) = m[c] * inv;
             }
         }
     }
 
-    // pre-clamp colour at unit direction d (the same arithmetic as ColourParams::eval)
-    __device__ __forceinline__ void eval(const float* d, float* pre) const {
-        float Y[NSH];
-        sh_basis<L>(d[0], d[1], d[2], Y);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) pre[c] = 0.5f;
-#pragma unroll
-        for (int k = 0; k < NSH; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) pre[c] = fmaf(at(3 * k + c), Y[k], pre[c]);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float cosv = FIXED ? d[k]
-                                     : at(3 * NSH + 3 * K + 3 * k) * d[0] + at(3 * NSH + 3 * K + 3 * k + 1) * d[1] +
-                                           at(3 * NSH + 3 * K + 3 * k + 2) * d[2];
-            const float e = expf(at(3 * NSH + 3 * K + NAX + k) * (cosv - 1.0f));
-#pragma unroll
-            for (int c = 0; c < 3; ++c) pre[c] = fmaf(at(3 * NSH + 3 * k + c), e, pre[c]);
-        }
-    }
+    __device__ __forceinline__ float csh(int k, int c) const { return at(3 * k + c); }
+    __device__ __forceinline__ float camp(int k, int c) const { return at(3 * NSH + 3 * k + c); }
+    __device__ __forceinline__ float caxis(int k, int c) const { return at(3 * NSH + 3 * K + 3 * k + c); }
+    __device__ __forceinline__ float csharp(int k) const { return at(3 * NSH + 3 * K + NAX + k); }
+    __device__ __forceinline__ float caxis_norm(int k) const { return at(3 * NSH + 3 * K + NAX + K + k); }
 };
 
 template <int L, int K, bool FIXED>
@@ -293,7 +280,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         float d[3], len;
         view_direction(cam, X, d, len);
         float pre[3];
-        cp.eval(d, pre);
+        colour_eval<L, K, FIXED>(cp, d, pre, record_sh_coeffs<L>(g, P.radius));
         uint32_t mask = 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -316,7 +303,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
 
 // ------------------------------------------------------------------------------ backward
 template <int L, int K, bool FIXED>
-__global__ void __launch_bounds__(128) preprocess_backward_kernel(
+__global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     const sgs_gaussians g, const ViewTable vt, const float4* __restrict__ rec0,
     const float4* __restrict__ rec1, const uint32_t* __restrict__ tiles,
     const float4* __restrict__ grad2d, int64_t R, sgs_grads out) {
@@ -349,13 +336,15 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(
         {
             float d[3], len;
             view_direction(cam, X, d, len);
+            // the forward's colour, bit for bit (same arithmetic), for its clamp decisions
+            const int nsh = record_sh_coeffs<L>(g, P.radius);
             float pre[3];
-            cp.eval(d, pre);
+            colour_eval<L, K, FIXED>(cp, d, pre, nsh);
             const float grgb[3] = {g1.z, g1.w, g2.x};
             float gpre[3], gd[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) gpre[c] = pre[c] < 0.0f ? 0.0f : grgb[c];
-            cg.accumulate(cp, d, gpre, gd);
+            cg.accumulate(cp, d, gpre, gd, nsh);
             const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
             const float inv = 1.0f / len;
 #pragma unroll

@@ -24,7 +24,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -121,6 +121,10 @@ class Scene:
     sg_amp: np.ndarray
     sg_axis: Optional[np.ndarray]
     sg_sharp: np.ndarray
+    # adaptive SH degree: 0 off; 1: bands up to 0 / 1 / 2 as a record's pixel radius is
+    # below sh_radius[0] / below sh_radius[1] / not
+    sh_adaptive: int = 0
+    sh_radius: Tuple[float, float] = (0.0, 0.0)
 
     PLANES = ("mean", "scale", "rot", "opacity", "sh", "sg_amp", "sg_axis", "sg_sharp")
 
@@ -148,7 +152,8 @@ class Scene:
             return out
 
         return Scene(n, s, self.sh_degree, self.num_lobes, self.axis_mode,
-                     *(take(getattr(self, p)) for p in self.PLANES))
+                     *(take(getattr(self, p)) for p in self.PLANES),
+                     sh_adaptive=self.sh_adaptive, sh_radius=self.sh_radius)
 
 
 def _unit_rows(g: np.ndarray) -> np.ndarray:

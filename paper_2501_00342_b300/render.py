@@ -35,8 +35,11 @@ class RenderSettings:
 class GaussianModel:
     """Gaussian parameter planes on the device, in the layout of ``sgs_gaussians``."""
 
-    def __init__(self, n, sh_degree, num_lobes, axis_mode, **planes):
+    def __init__(self, n, sh_degree, num_lobes, axis_mode, sh_adaptive=0, sh_radius=(0.0, 0.0), **planes):
         self.n, self.sh_degree, self.num_lobes, self.axis_mode = n, sh_degree, num_lobes, axis_mode
+        # adaptive SH degree: bands up to 0 / 1 / 2 for records of pixel radius below
+        # sh_radius[0] / below sh_radius[1] / above (see sgs_gaussians)
+        self.sh_adaptive, self.sh_radius = int(sh_adaptive), (float(sh_radius[0]), float(sh_radius[1]))
         self.planes: Dict[str, Optional[torch.Tensor]] = {p: planes.get(p) for p in PLANES}
         self.stride = self.planes["mean"].shape[-1]
         for p, t in self.planes.items():
@@ -47,12 +50,14 @@ class GaussianModel:
     def from_scene(cls, scene, device="cuda"):
         planes = {p: (None if getattr(scene, p) is None else
                       torch.from_numpy(getattr(scene, p)).to(device).contiguous()) for p in PLANES}
-        return cls(scene.n, scene.sh_degree, scene.num_lobes, scene.axis_mode, **planes)
+        return cls(scene.n, scene.sh_degree, scene.num_lobes, scene.axis_mode,
+                   getattr(scene, "sh_adaptive", 0), getattr(scene, "sh_radius", (0.0, 0.0)), **planes)
 
     def with_planes(self, **planes) -> "GaussianModel":
         d = dict(self.planes)
         d.update(planes)
-        return GaussianModel(self.n, self.sh_degree, self.num_lobes, self.axis_mode, **d)
+        return GaussianModel(self.n, self.sh_degree, self.num_lobes, self.axis_mode, self.sh_adaptive,
+                             self.sh_radius, **d)
 
     def struct(self) -> B.Gaussians:
         g = B.Gaussians()
@@ -60,6 +65,8 @@ class GaussianModel:
         g.sh_degree, g.num_lobes, g.axis_mode = self.sh_degree, self.num_lobes, self.axis_mode
         for p in PLANES:
             setattr(g, p, B.ptr(self.planes[p]))
+        g.sh_adaptive = self.sh_adaptive
+        g.sh_radius[0], g.sh_radius[1] = self.sh_radius
         return g
 
     def empty_grads(self) -> Dict[str, Optional[torch.Tensor]]:

@@ -70,6 +70,22 @@ def test_gradients_colour_variants_vs_adjoint(L, K, mode):
     _compare(sc, cams, ws, _gpu_grads(sc, cams, ws, RenderSettings(bg=bg)), _oracle_grads(sc, cams, ws, bg), bg)
 
 
+def test_gradients_adaptive_sh_vs_adjoint():
+    sc = random_small_scene(60, seed=42, sh_degree=2, K=2, log_scale=(-2.0, 0.5))
+    cams = [axis_camera(48, 40, 60.0, 3.2), I.look_at((1.0, 0.8, 3.0), (0, 0, 0), 40, 48, 55.0)]
+    m = O.mirror_preprocess(sc, cams)
+    u = np.unique(m["radius"][m["visible"]])
+    sc.sh_adaptive, sc.sh_radius = 1, (float(u[len(u) // 3]), float(u[2 * len(u) // 3]))
+    ws = _weights(sc, cams, 6)
+    g = _gpu_grads(sc, cams, ws)
+    _compare(sc, cams, ws, g, _oracle_grads(sc, cams, ws))
+    # bands above every record's degree get no gradient at all
+    top = np.where(m["radius"] < sc.sh_radius[0], 0, np.where(m["radius"] < sc.sh_radius[1], 1, 2))
+    top = np.where(m["visible"], top, -1).reshape(len(cams), sc.n).max(0)
+    for i in range(sc.n):
+        assert np.all(g["sh"][(top[i] + 1) ** 2:, :, i] == 0.0)
+
+
 def _slice_200():
     """200 clustered Gaussians (the training-step distribution), one 32x32 view."""
     sc = I.cluster_scene(200, 1, 4, config=2, num_clusters=8)

@@ -225,3 +225,18 @@ def test_graph_capture_replay_matches_eager():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, eager)
+
+
+def test_adaptive_sh_degree_records_and_image():
+    """Adaptive SH degree (bands 0 / 0-1 / 0-2 by the record's pixel radius): records and
+    image against the oracle, thresholds at radii that occur (ties take the upper band)."""
+    from tests.helpers import random_small_scene
+    sc = random_small_scene(80, seed=41, sh_degree=2, K=2, log_scale=(-2.2, 0.6))
+    cams = [axis_camera(64, 48, 60.0, 3.0), I.look_at((1.2, -0.8, 2.6), (0, 0, 0), 48, 64, 55.0)]
+    m = O.mirror_preprocess(sc, cams)
+    u = np.unique(m["radius"][m["visible"]])
+    sc.sh_adaptive, sc.sh_radius = 1, (float(u[len(u) // 3]), float(u[2 * len(u) // 3]))
+    rast, _, img, out_T = _run(sc, cams)
+    _check_records(sc, cams, rast)
+    for v in range(len(cams)):
+        _check_image(sc, cams, img, view=v, rast=rast, out_T=out_T)

@@ -11,6 +11,7 @@ sizes, so the checks are sampled:
 * invariants over all instances: M = sum of tiles touched, tile ids non-decreasing, depth
   non-decreasing within a tile, the ranges partition [0, M);
 * image: 12x12 patches around projected Gaussians against the FP64 oracle, 1e-4 max abs;
+* the 2.5 M workload once more with degree-2 SH storage and adaptive degrees;
 * gradients: dL/dpixel non-zero on the sampled patches only; every parameter plane against
   the FP64 adjoint of those pixels, |g - g*| <= 1e-3 max(|g*|, 1e-3 max|g*|) per element
   (cancelling entries: see tests.helpers.check_gradients).
@@ -32,10 +33,15 @@ AMBIGUOUS = 1e-5
 SUBSET = 20_000
 
 
-@pytest.fixture(scope="module", params=[1, 2, 3, 4])
+@pytest.fixture(scope="module", params=[1, 2, 3, 4, "2-adaptive"])
 def full(request):
     config = request.param
-    sc, cams = I.workload(config)
+    if config == "2-adaptive":  # degree-2 storage, bands 0 / 0-1 / 0-2 below 4 / 16 pixels
+        config = 2
+        sc, cams = I.workload(2, sh_degree=2)
+        sc.sh_adaptive, sc.sh_radius = 1, (4.0, 16.0)
+    else:
+        sc, cams = I.workload(config)
     model = GaussianModel.from_scene(sc)
     rast = Rasterizer(model, cams, RenderSettings())
     img = rast.forward(model, sync=True)
