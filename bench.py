@@ -346,9 +346,10 @@ def run_gpu(args):
 
         # ---- render FPS, 1 M Gaussians at 1280x720: SG colour vs SH degree 3
         fps = {}
-        for label, L, K, adaptive in (("sh1_sg3", 1, 3, None), ("sh3", 3, 0, None),
-                                      ("adaptive_sh012_sg3", 2, 3, (0.5, 0.9))):
-            sc1, cams1 = I.workload(1, sh_degree=L, num_lobes=K)
+        for label, L, K, adaptive, mode in (("sh1_sg3", 1, 3, None, I.AXIS_FREE), ("sh3", 3, 0, None, I.AXIS_FREE),
+                                            ("adaptive_sh012_sg3", 2, 3, (0.5, 0.9), I.AXIS_FREE),
+                                            ("dc_sg3_frame", 0, 3, None, I.AXIS_ORTHO_FRAME)):
+            sc1, cams1 = I.workload(1, sh_degree=L, num_lobes=K, axis_mode=mode)
             cams1 = cams1[:8]
             if adaptive:
                 # degree 0 for the smaller half of the records, 1 up to the 90th percentile
@@ -379,7 +380,8 @@ def run_gpu(args):
             torch.cuda.synchronize()
             fms = max_over_ranks(a.elapsed_time(b2) / (reps * len(rs)))
             fps[label] = {"ms_per_frame": round(fms, 4), "fps": round(1e3 / fms, 1),
-                          "floats_per_gaussian": sc1.floats_per_gaussian()}
+                          "floats_per_gaussian": sc1.floats_per_gaussian(),
+                          "model_mb": round(sc1.n * 4 * sc1.floats_per_gaussian() / 1e6, 1)}
             if adaptive:  # share of the visible records that summed bands up to 0, 1, 2
                 rad = torch.cat([r1.region("REC1", torch.float32)[:4 * sc1.n].view(-1, 4)[:, 3][
                     r1.region("TILES", torch.int32)[:sc1.n] != 0] for r1, _ in rs])
@@ -389,6 +391,7 @@ def run_gpu(args):
             del rs, m1
         fps["sg_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["sh1_sg3"]["ms_per_frame"], 4)
         fps["adaptive_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["adaptive_sh012_sg3"]["ms_per_frame"], 4)
+        fps["frame_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["dc_sg3_frame"]["ms_per_frame"], 4)
         fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
         out["render_fps"] = fps
 

@@ -58,9 +58,14 @@ typedef enum {
 } sgs_status;
 
 typedef enum {
-    SGS_AXIS_FREE = 0,       /* each lobe has its own axis mu_k, normalised in the kernel */
-    SGS_AXIS_ORTHO_FIXED = 1 /* lobes k = 0,1,2 use the world axes (Eq. 7-8 and
-                                Sec. "Implementation"); no axis is stored, K <= 3 */
+    SGS_AXIS_FREE = 0,        /* each lobe has its own axis mu_k, normalised in the kernel */
+    SGS_AXIS_ORTHO_FIXED = 1, /* lobes k = 0,1,2 use the world axes (Eq. 7-8 and
+                                 Sec. "Implementation"); no axis is stored, K <= 3 */
+    SGS_AXIS_ORTHO_FRAME = 2  /* lobes k = 0,1,2 use the columns of a per-Gaussian rotation
+                                 of 3 parameters f (Sec. "Multi-Axis Orthogonal Gaussians":
+                                 15 parameters for 3 orthogonal lobes): the unit quaternion
+                                 (1, f0, f1, f2) / |(1, f0, f1, f2)|; sg_axis holds f as
+                                 [3][stride]; K <= 3 */
 } sgs_axis_mode;
 
 /* Pinhole camera, OpenCV axes (+x right, +y down, +z forward).
@@ -86,7 +91,8 @@ typedef struct {
  *   sh       [(L+1)^2][3][stride]     SH coefficients c_lm per RGB channel (Eq. 4),
  *                                     basis index l*l + l + m, Condon-Shortley phase
  *   sg_amp   [K][3][stride]           lobe amplitudes alpha_k per channel (Eq. 5, 7)
- *   sg_axis  [K][3][stride]           lobe axes mu_k (free-axis mode; NULL otherwise)
+ *   sg_axis  [K][3][stride]           lobe axes mu_k (free-axis mode), or [3][stride] frame
+ *                                     parameters (SGS_AXIS_ORTHO_FRAME); NULL otherwise
  *   sg_sharp [K][stride]              lobe sharpness lambda_k
  * colour = max(0, sum_lm c_lm Y_lm(d) + 0.5 + sum_k alpha_k exp(lambda_k (mu_k.d - 1))).
  *
@@ -99,7 +105,7 @@ typedef struct {
 typedef struct {
     int64_t n, stride;
     int32_t sh_degree; /* L in 0..3 */
-    int32_t num_lobes; /* K in 0..4 (0..3 in SGS_AXIS_ORTHO_FIXED) */
+    int32_t num_lobes; /* K in 0..4 (0..3 in SGS_AXIS_ORTHO_FIXED / _FRAME) */
     int32_t axis_mode; /* sgs_axis_mode */
     const float *mean, *scale, *rot, *opacity, *sh, *sg_amp, *sg_axis, *sg_sharp;
     int32_t sh_adaptive;  /* 0 or 1 */

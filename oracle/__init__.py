@@ -184,7 +184,7 @@ def grad_buffers(sc):
     g = dict(mean=np.zeros((3, S)), scale=np.zeros((3, S)), rot=np.zeros((4, S)),
              opacity=np.zeros(S), sh=np.zeros((sc.num_sh, 3, S)),
              sg_amp=np.zeros((max(sc.num_lobes, 0), 3, S)),
-             sg_axis=np.zeros((sc.num_lobes, 3, S)) if sc.sg_axis is not None else None,
+             sg_axis=(None if sc.sg_axis is None else np.zeros(sc.sg_axis.shape[:-1] + (S,))),
              sg_sharp=np.zeros((sc.num_lobes, S)))
     return g
 

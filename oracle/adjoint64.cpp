@@ -53,14 +53,14 @@ void chain_to_params(const orc_scene* s, const Cam64& k, const Pre64& p, const d
             }
             for (int j = 0; j < 3; ++j) gdir[j] += wsum * gY[j];
         }
+    double gF[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};  // frame mode: dL/dR
     for (int lobe = 0; lobe < s->num_lobes; ++lobe) {
-        double mu[3], mun = 1.0, muraw[3] = {0.0, 0.0, 0.0};
+        double mu[3], mun = 1.0;
+        lobe_axis(s, i, lobe, mu);
         if (s->axis_mode == 0) {
+            double muraw[3];
             for (int j = 0; j < 3; ++j) muraw[j] = s->sg_axis[(lobe * 3 + j) * S + i];
             mun = std::sqrt(muraw[0] * muraw[0] + muraw[1] * muraw[1] + muraw[2] * muraw[2]);
-            for (int j = 0; j < 3; ++j) mu[j] = muraw[j] / mun;
-        } else {
-            for (int j = 0; j < 3; ++j) mu[j] = (j == lobe) ? 1.0 : 0.0;
         }
         const double lam = s->sg_sharp[lobe * S + i];
         const double cosang = mu[0] * p.dir[0] + mu[1] * p.dir[1] + mu[2] * p.dir[2];
@@ -82,7 +82,26 @@ void chain_to_params(const orc_scene* s, const Cam64& k, const Pre64& p, const d
             }
             for (int j = 0; j < 3; ++j)
                 out->sg_axis[(lobe * 3 + j) * S + i] += (gmu[j] - mu[j] * dotp) / mun;
+        } else if (s->axis_mode == 2) {
+            for (int j = 0; j < 3; ++j) gF[j][lobe] += gcos * p.dir[j];  // mu = column `lobe` of R
         }
+    }
+    if (s->axis_mode == 2 && s->num_lobes > 0) {
+        // R(q) entry by entry, differentiated w.r.t. (w, x, y, z); then q = v / |v|, v = (1, f)
+        const double f[3] = {s->sg_axis[i], s->sg_axis[S + i], s->sg_axis[2 * S + i]};
+        double q[4], R[3][3];
+        const double n = lobe_frame(f, q, R);
+        const double w = q[0], x = q[1], y = q[2], z = q[3];
+        const double dR[3][3][4] = {
+            {{0, 0, -4 * y, -4 * z}, {-2 * z, 2 * y, 2 * x, -2 * w}, {2 * y, 2 * z, 2 * w, 2 * x}},
+            {{2 * z, 2 * y, 2 * x, 2 * w}, {0, -4 * x, 0, -4 * z}, {-2 * x, -2 * w, 2 * z, 2 * y}},
+            {{-2 * y, 2 * z, -2 * w, 2 * x}, {2 * x, 2 * w, 2 * z, 2 * y}, {0, -4 * x, -4 * y, 0}}};
+        double gq[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 4; ++k) gq[k] += gF[r][c] * dR[r][c][k];
+        const double dotq = gq[0] * q[0] + gq[1] * q[1] + gq[2] * q[2] + gq[3] * q[3];
+        for (int j = 0; j < 3; ++j) out->sg_axis[j * S + i] += (gq[1 + j] - q[1 + j] * dotq) / n;
     }
     {  // d = dvec / |dvec|, dvec = X - campos
         double dotp = 0.0;
@@ -195,6 +214,7 @@ void orc_adjoint_pixels(const orc_scene* s, const float* cams, int32_t B, const 
         std::fill(out->sg_amp, out->sg_amp + s->num_lobes * 3 * S, 0.0);
         std::fill(out->sg_sharp, out->sg_sharp + s->num_lobes * S, 0.0);
         if (s->axis_mode == 0) std::fill(out->sg_axis, out->sg_axis + s->num_lobes * 3 * S, 0.0);
+        if (s->axis_mode == 2) std::fill(out->sg_axis, out->sg_axis + 3 * S, 0.0);
     }
     for (int v = 0; v < B; ++v) {
         std::vector<int64_t> mine;

@@ -85,6 +85,39 @@ static double sh_norm(int l, int m) {
 // Y_lm(d) = N_lm Q_l|m|(z) P_m(x, y), with P_m = Re (x+iy)^m for m > 0, Im (x+iy)^|m| for
 // m < 0 and 1 for m = 0.  On the unit sphere (x+iy)^m = sin^m(theta) e^{i m phi}, so this
 // is sqrt(2) N P_l^m(cos theta) cos(m phi) (resp. sin) as in the textbook definition.
+double lobe_frame(const double f[3], double q[4], double R[3][3]) {
+    const double n = std::sqrt(1.0 + f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    q[0] = 1.0 / n;
+    for (int j = 0; j < 3; ++j) q[1 + j] = f[j] / n;
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+    return n;
+}
+
+void lobe_axis(const orc_scene* s, int64_t i, int lobe, double mu[3]) {
+    const int64_t S = s->stride;
+    if (s->axis_mode == 0) {  // free: mu_k / |mu_k|
+        for (int j = 0; j < 3; ++j) mu[j] = s->sg_axis[(lobe * 3 + j) * S + i];
+        const double n = std::sqrt(mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]);
+        for (int j = 0; j < 3; ++j) mu[j] /= n;
+    } else if (s->axis_mode == 1) {  // world axes
+        for (int j = 0; j < 3; ++j) mu[j] = (j == lobe) ? 1.0 : 0.0;
+    } else {  // column `lobe` of the Gaussian's frame
+        const double f[3] = {s->sg_axis[i], s->sg_axis[S + i], s->sg_axis[2 * S + i]};
+        double q[4], R[3][3];
+        lobe_frame(f, q, R);
+        for (int j = 0; j < 3; ++j) mu[j] = R[j][lobe];
+    }
+}
+
 double sh_basis(int l, int m, const double d[3]) {
     const int am = std::abs(m);
     const std::complex<double> w(d[0], d[1]);
@@ -211,13 +244,7 @@ Pre64 preprocess(const orc_scene* s, int64_t i, const float* cam) {
         }
     for (int lobe = 0; lobe < s->num_lobes; ++lobe) {
         double mu[3];
-        if (s->axis_mode == 0) {
-            for (int j = 0; j < 3; ++j) mu[j] = s->sg_axis[(lobe * 3 + j) * S + i];
-            const double n = std::sqrt(mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]);
-            for (int j = 0; j < 3; ++j) mu[j] /= n;
-        } else {
-            for (int j = 0; j < 3; ++j) mu[j] = (j == lobe) ? 1.0 : 0.0;
-        }
+        lobe_axis(s, i, lobe, mu);
         const double lam = s->sg_sharp[lobe * S + i];
         const double e = std::exp(lam * (mu[0] * p.dir[0] + mu[1] * p.dir[1] + mu[2] * p.dir[2] - 1.0));
         for (int ch = 0; ch < 3; ++ch) col[ch] += s->sg_amp[(lobe * 3 + ch) * S + i] * e;

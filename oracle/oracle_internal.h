@@ -49,6 +49,13 @@ struct Pre64 {
 };
 Pre64 preprocess(const orc_scene* s, int64_t i, const float* cam);
 
+// Lobe frame of the orthogonal-frame mode from its 3 parameters f: the unit quaternion
+// q = (1, f) / |(1, f)| and its rotation matrix R (lobe k's axis is column k).  Returns
+// |(1, f)|.
+double lobe_frame(const double f[3], double q[4], double R[3][3]);
+// Lobe k's unit axis for any axis mode (0 free, 1 world, 2 frame) of Gaussian i.
+void lobe_axis(const orc_scene* s, int64_t i, int lobe, double mu[3]);
+
 // Real SH basis (Condon-Shortley phase), and its gradient w.r.t. the ambient direction.
 double sh_basis(int l, int m, const double d[3]);
 void sh_basis_grad(int l, int m, const double d[3], double g[3]);

@@ -42,8 +42,10 @@ sgs_status check_gaussians(const sgs_gaussians* g) {
     if (!g || g->n < 0 || g->stride < g->n || (g->stride & 3) != 0) return SGS_ERR_INVALID;
     if (g->sh_degree < 0 || g->sh_degree > SGS_MAX_SH_DEGREE) return SGS_ERR_INVALID;
     if (g->num_lobes < 0 || g->num_lobes > 4) return SGS_ERR_INVALID;
-    if (g->axis_mode != SGS_AXIS_FREE && g->axis_mode != SGS_AXIS_ORTHO_FIXED) return SGS_ERR_INVALID;
-    if (g->axis_mode == SGS_AXIS_ORTHO_FIXED && g->num_lobes > 3) return SGS_ERR_INVALID;
+    if (g->axis_mode != SGS_AXIS_FREE && g->axis_mode != SGS_AXIS_ORTHO_FIXED &&
+        g->axis_mode != SGS_AXIS_ORTHO_FRAME)
+        return SGS_ERR_INVALID;
+    if (g->axis_mode != SGS_AXIS_FREE && g->num_lobes > 3) return SGS_ERR_INVALID;
     if (g->sh_adaptive != 0 && g->sh_adaptive != 1) return SGS_ERR_INVALID;
     if (g->sh_adaptive && !(g->sh_radius[0] >= 0.0f && g->sh_radius[0] <= g->sh_radius[1]))
         return SGS_ERR_INVALID;  // also rejects NaN thresholds
@@ -58,7 +60,7 @@ sgs_status check_pointers(const sgs_gaussians* g) {
     if (g->num_lobes > 0) {
         if (!g->sg_amp || !g->sg_sharp || !aligned16(g->sg_amp) || !aligned16(g->sg_sharp))
             return SGS_ERR_INVALID;
-        if (g->axis_mode == SGS_AXIS_FREE && (!g->sg_axis || !aligned16(g->sg_axis))) return SGS_ERR_INVALID;
+        if (g->axis_mode != SGS_AXIS_ORTHO_FIXED && (!g->sg_axis || !aligned16(g->sg_axis))) return SGS_ERR_INVALID;
     }
     return SGS_OK;
 }
@@ -339,7 +341,7 @@ sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const flo
     if (plan->n > 0) {
         if (!out->mean || !out->scale || !out->rot || !out->opacity || !out->sh) return SGS_ERR_INVALID;
         if (plan->num_lobes > 0 && (!out->sg_amp || !out->sg_sharp)) return SGS_ERR_INVALID;
-        if (plan->num_lobes > 0 && plan->axis_mode == SGS_AXIS_FREE && !out->sg_axis) return SGS_ERR_INVALID;
+        if (plan->num_lobes > 0 && plan->axis_mode != SGS_AXIS_ORTHO_FIXED && !out->sg_axis) return SGS_ERR_INVALID;
     }
     const ViewTable vt = view_table(plan);
     const RecordPtrs rp = records(plan);

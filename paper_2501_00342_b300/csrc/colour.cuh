@@ -89,13 +89,58 @@ __device__ __forceinline__ float axis_length(const float m[3]) {
     return sqrtf(fmaf(m[0], m[0], fmaf(m[1], m[1], m[2] * m[2])));
 }
 
+// Lobe-axis layouts (sgs_axis_mode): 0 free unit axes, 1 the world axes, 2 the columns of
+// a per-Gaussian rotation given by 3 parameters.
+constexpr int kAxFree = 0, kAxWorld = 1, kAxFrame = 2;
+
+// Rotation matrix of the unit quaternion q = (w, x, y, z) (the covariance rotation of Eq. 3
+// and the lobe frame use the same map).
+__device__ __forceinline__ void quat_to_matrix(const float q[4], float R[3][3]) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0f - 2.0f * (y * y + z * z);
+    R[0][1] = 2.0f * (x * y - w * z);
+    R[0][2] = 2.0f * (x * z + w * y);
+    R[1][0] = 2.0f * (x * y + w * z);
+    R[1][1] = 1.0f - 2.0f * (x * x + z * z);
+    R[1][2] = 2.0f * (y * z - w * x);
+    R[2][0] = 2.0f * (x * z - w * y);
+    R[2][1] = 2.0f * (y * z + w * x);
+    R[2][2] = 1.0f - 2.0f * (x * x + y * y);
+}
+
+// dL/dq of R(q) for a unit q, given dL/dR (the unnormalised-quaternion chain is separate).
+__device__ __forceinline__ void quat_to_matrix_vjp(const float q[4], const float gR[3][3], float gq[4]) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    gq[0] = 2.0f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+    gq[1] = 2.0f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.0f * x * gR[1][1] - w * gR[1][2] +
+                    z * gR[2][0] + w * gR[2][1] - 2.0f * x * gR[2][2]);
+    gq[2] = 2.0f * (-2.0f * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] -
+                    w * gR[2][0] + z * gR[2][1] - 2.0f * y * gR[2][2]);
+    gq[3] = 2.0f * (-2.0f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2.0f * z * gR[1][1] +
+                    y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+}
+
+// The orthonormal lobe frame of 3 parameters f (Sec. "Multi-Axis Orthogonal Gaussians": 3
+// parameters fix the orthogonal directions): q = (1, f0, f1, f2) / |(1, f0, f1, f2)|, the
+// lobe axes are the columns of R(q).  f = 0 is the world frame.  Returns |(1, f)|.
+__device__ __forceinline__ float frame_axes(const float f[3], float q[4], float R[3][3]) {
+    const float n = sqrtf(fmaf(f[0], f[0], fmaf(f[1], f[1], fmaf(f[2], f[2], 1.0f))));
+    const float inv = 1.0f / n;
+    q[0] = inv;
+    q[1] = f[0] * inv;
+    q[2] = f[1] * inv;
+    q[3] = f[2] * inv;
+    quat_to_matrix(q, R);
+    return n;
+}
+
 // Pre-clamp colour at unit direction d from the first nsh SH coefficients and the K lobes
 // (Eq. 4, 5, 7, 9).  P provides csh(k, c), camp(k, c), caxis(k, c) (unit axes) and
 // csharp(k).  Every operation is written out (fmaf, no contraction left to the compiler),
 // so that the forward pass, which reads the parameters from shared memory, and the
 // backward pass, which holds them in registers, compute the same bits and take the same
 // colour-clamp decisions.
-template <int L, int K, bool FIXED, class P>
+template <int L, int K, int AX, class P>
 __device__ __forceinline__ void colour_eval(const P& p, const float* d, float* pre, int nsh) {
     constexpr int NSH = (L + 1) * (L + 1);
     float Y[NSH];
@@ -110,7 +155,8 @@ __device__ __forceinline__ void colour_eval(const P& p, const float* d, float* p
         }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float cosv = FIXED ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
+        const float cosv =
+            AX == kAxWorld ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
         const float e = expf(p.csharp(k) * (cosv - 1.0f));
 #pragma unroll
         for (int c = 0; c < 3; ++c) pre[c] = fmaf(p.camp(k, c), e, pre[c]);
@@ -118,13 +164,16 @@ __device__ __forceinline__ void colour_eval(const P& p, const float* d, float* p
 }
 
 // Colour parameters of one Gaussian held in registers.
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 struct ColourParams {
     static constexpr int NSH = (L + 1) * (L + 1);
+    static constexpr bool AXES = K > 0 && AX != kAxWorld;  // unit axes held
     float sh[NSH][3];
     float amp[K > 0 ? K : 1][3];
-    float axis[(K > 0 && !FIXED) ? K : 1][3];  // normalised in load()
-    float axis_norm[(K > 0 && !FIXED) ? K : 1];
+    float axis[AXES ? K : 1][3];                      // unit lobe axes
+    float axis_norm[(K > 0 && AX == kAxFree) ? K : 1];  // |mu_k| (free axes)
+    float fq[AX == kAxFrame ? 4 : 1];                 // frame quaternion and |(1, f)|
+    float fnorm;
     float sharp[K > 0 ? K : 1];
 
     __device__ __forceinline__ void load(const sgs_gaussians& g, int64_t i) {
@@ -133,12 +182,21 @@ struct ColourParams {
         for (int k = 0; k < NSH; ++k)
 #pragma unroll
             for (int c = 0; c < 3; ++c) sh[k][c] = __ldg(g.sh + (k * 3 + c) * S + i);
+        if constexpr (AX == kAxFrame && K > 0) {
+            const float f[3] = {__ldg(g.sg_axis + i), __ldg(g.sg_axis + S + i), __ldg(g.sg_axis + 2 * S + i)};
+            float R[3][3];
+            fnorm = frame_axes(f, fq, R);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) axis[k][c] = R[c][k];
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) amp[k][c] = __ldg(g.sg_amp + (k * 3 + c) * S + i);
             sharp[k] = __ldg(g.sg_sharp + k * S + i);
-            if (!FIXED) {
+            if constexpr (AX == kAxFree) {
                 float m[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
@@ -155,8 +213,6 @@ struct ColourParams {
     __device__ __forceinline__ float camp(int k, int c) const { return amp[k][c]; }
     __device__ __forceinline__ float caxis(int k, int c) const { return axis[k][c]; }
     __device__ __forceinline__ float csharp(int k) const { return sharp[k]; }
-    __device__ __forceinline__ float caxis_norm(int k) const { return axis_norm[k]; }
-
 };
 
 // Number of SH coefficients a record sums: (D+1)^2 with D = sh_degree, or with adaptive
@@ -173,12 +229,12 @@ __device__ __forceinline__ int record_sh_coeffs(const sgs_gaussians& g, float ra
 }
 
 // Gradient accumulators of the colour parameters (summed over views).
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 struct ColourGrads {
     static constexpr int NSH = (L + 1) * (L + 1);
     float sh[NSH][3];
     float amp[K > 0 ? K : 1][3];
-    float axis[(K > 0 && !FIXED) ? K : 1][3];  // w.r.t. the normalised axis
+    float axis[(K > 0 && AX != kAxWorld) ? K : 1][3];  // w.r.t. the unit axis
     float sharp[K > 0 ? K : 1];
 
     __device__ __forceinline__ void zero() {
@@ -191,7 +247,7 @@ struct ColourGrads {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 amp[k][c] = 0.0f;
-                if (!FIXED) axis[k][c] = 0.0f;
+                if (AX != kAxWorld) axis[k][c] = 0.0f;
             }
             sharp[k] = 0.0f;
         }
@@ -216,7 +272,8 @@ struct ColourGrads {
         sh_basis_vjp<L>(d[0], d[1], d[2], gY, gd[0], gd[1], gd[2]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float cs = FIXED ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
+            const float cs =
+                AX == kAxWorld ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
             const float e = expf(p.csharp(k) * (cs - 1.0f));
             float s = 0.0f;
 #pragma unroll
@@ -226,7 +283,7 @@ struct ColourGrads {
             }
             sharp[k] = fmaf(s, cs - 1.0f, sharp[k]);
             const float gcos = s * p.csharp(k);
-            if (FIXED) {
+            if (AX == kAxWorld) {
                 gd[k] += gcos;
             } else {
 #pragma unroll
@@ -238,8 +295,8 @@ struct ColourGrads {
         }
     }
 
-    template <class P>
-    __device__ __forceinline__ void store(const P& p, const sgs_grads& out, int64_t S, int64_t i) const {
+    __device__ __forceinline__ void store(const ColourParams<L, K, AX>& p, const sgs_grads& out, int64_t S,
+                                          int64_t i) const {
 #pragma unroll
         for (int k = 0; k < NSH; ++k)
 #pragma unroll
@@ -249,15 +306,28 @@ struct ColourGrads {
 #pragma unroll
             for (int c = 0; c < 3; ++c) out.sg_amp[(k * 3 + c) * S + i] = amp[k][c];
             out.sg_sharp[k * S + i] = sharp[k];
-            if (!FIXED) {
+            if constexpr (AX == kAxFree) {
                 // mu = m/|m|:  dL/dm = (g - mu (mu . g)) / |m|
-                const float dot = axis[k][0] * p.caxis(k, 0) + axis[k][1] * p.caxis(k, 1) +
-                                  axis[k][2] * p.caxis(k, 2);
-                const float inv = 1.0f / p.caxis_norm(k);
+                const float dot = axis[k][0] * p.axis[k][0] + axis[k][1] * p.axis[k][1] + axis[k][2] * p.axis[k][2];
+                const float inv = 1.0f / p.axis_norm[k];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.caxis(k, c) * dot) * inv;
+                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.axis[k][c] * dot) * inv;
             }
+        }
+        if constexpr (AX == kAxFrame && K > 0) {
+            // mu_k = column k of R(q): dL/dR[c][k] = dL/dmu_k[c]; then q = v/|v|, v = (1, f)
+            float gR[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gR[c][k] = k < K ? axis[k < K ? k : 0][c] : 0.0f;
+            float gq[4];
+            quat_to_matrix_vjp(p.fq, gR, gq);
+            const float dot = gq[0] * p.fq[0] + gq[1] * p.fq[1] + gq[2] * p.fq[2] + gq[3] * p.fq[3];
+            const float inv = 1.0f / p.fnorm;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) out.sg_axis[j * S + i] = (gq[1 + j] - p.fq[1 + j] * dot) * inv;
         }
     }
 };

@@ -207,10 +207,10 @@ constexpr int kPreThreads = 128;
 
 // A Gaussian's colour parameters held in a column of shared memory (stride kPreThreads):
 // the view loop reads them per view instead of keeping ~40 registers live.
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 struct ColourShared {
     static constexpr int NSH = (L + 1) * (L + 1);
-    static constexpr int NAX = (K > 0 && !FIXED) ? 3 * K : 0;
+    static constexpr int NAX = (K > 0 && AX != kAxWorld) ? 3 * K : 0;
     static constexpr int COUNT = 3 * NSH + 3 * K + NAX + K + NAX / 3;  // sh, amp, unit axes, sharpness, |axis|
     float* p;
 
@@ -220,12 +220,21 @@ struct ColourShared {
         const int64_t S = g.stride;
 #pragma unroll
         for (int k = 0; k < 3 * NSH; ++k) at(k) = __ldg(g.sh + k * S + i);
+        if constexpr (AX == kAxFrame && K > 0) {
+            const float f[3] = {__ldg(g.sg_axis + i), __ldg(g.sg_axis + S + i), __ldg(g.sg_axis + 2 * S + i)};
+            float q[4], R[3][3];
+            frame_axes(f, q, R);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) at(3 * NSH + 3 * K + 3 * k + c) = R[c][k];
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) at(3 * NSH + 3 * k + c) = __ldg(g.sg_amp + (k * 3 + c) * S + i);
             at(3 * NSH + 3 * K + NAX + k) = __ldg(g.sg_sharp + k * S + i);
-            if (!FIXED) {
+            if constexpr (AX == kAxFree) {
                 float m[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
@@ -245,7 +254,7 @@ struct ColourShared {
     __device__ __forceinline__ float caxis_norm(int k) const { return at(3 * NSH + 3 * K + NAX + K + k); }
 };
 
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_gaussians g, const ViewTable vt,
                                                                  float4* __restrict__ rec0,
                                                                  float4* __restrict__ rec1,
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
                                                                  uint2* __restrict__ rect,
                                                                  uint32_t* __restrict__ tiles,
                                                                  uint4* __restrict__ spans) {
-    using CS = ColourShared<L, K, FIXED>;
+    using CS = ColourShared<L, K, AX>;
     __shared__ float s_colour[CS::COUNT * kPreThreads];
     __shared__ uint32_t s_table[16 * kPreThreads];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         float d[3], len;
         view_direction(cam, X, d, len);
         float pre[3];
-        colour_eval<L, K, FIXED>(cp, d, pre, record_sh_coeffs<L>(g, P.radius));
+        colour_eval<L, K, AX>(cp, d, pre, record_sh_coeffs<L>(g, P.radius));
         uint32_t mask = 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
 }
 
 // ------------------------------------------------------------------------------ backward
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     const sgs_gaussians g, const ViewTable vt, const float4* __restrict__ rec0,
     const float4* __restrict__ rec1, const uint32_t* __restrict__ tiles,
@@ -313,9 +322,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     const float X[3] = {__ldg(g.mean + i), __ldg(g.mean + S + i), __ldg(g.mean + 2 * S + i)};
     Geometry G;
     geometry_exact(g, i, G);
-    ColourParams<L, K, FIXED> cp;
+    ColourParams<L, K, AX> cp;
     cp.load(g, i);
-    ColourGrads<L, K, FIXED> cg;
+    ColourGrads<L, K, AX> cg;
     cg.zero();
     float gX[3] = {0.0f, 0.0f, 0.0f};
     float gSig[3][3];
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
             // the forward's colour, bit for bit (same arithmetic), for its clamp decisions
             const int nsh = record_sh_coeffs<L>(g, P.radius);
             float pre[3];
-            colour_eval<L, K, FIXED>(cp, d, pre, nsh);
+            colour_eval<L, K, AX>(cp, d, pre, nsh);
             const float grgb[3] = {g1.z, g1.w, g2.x};
             float gpre[3], gd[3];
 #pragma unroll
@@ -435,24 +444,24 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     cg.store(cp, out, S, i);
 }
 
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 cudaError_t launch_pre(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
                        cudaStream_t s) {
     const int threads = 128;
     const int blocks = (int)((g.n + threads - 1) / threads);
     if (blocks > 0)
-        preprocess_kernel<L, K, FIXED><<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.rec2, p.rect,
+        preprocess_kernel<L, K, AX><<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.rec2, p.rect,
                                                                  p.tiles, p.spans);
     return cudaGetLastError();
 }
 
-template <int L, int K, bool FIXED>
+template <int L, int K, int AX>
 cudaError_t launch_pre_bwd(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
                            const float4* grad2d, int64_t R, const sgs_grads& out, cudaStream_t s) {
     const int threads = 128;
     const int blocks = (int)((g.n + threads - 1) / threads);
     if (blocks > 0)
-        preprocess_backward_kernel<L, K, FIXED>
+        preprocess_backward_kernel<L, K, AX>
             <<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.tiles, grad2d, R, out);
     return cudaGetLastError();
 }
@@ -460,15 +469,18 @@ cudaError_t launch_pre_bwd(const sgs_gaussians& g, const ViewTable& vt, const Re
 template <int L, int K>
 cudaError_t dispatch_axis(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
                           const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
-    if (g.axis_mode == SGS_AXIS_ORTHO_FIXED) {
+    if (g.axis_mode == SGS_AXIS_ORTHO_FIXED || g.axis_mode == SGS_AXIS_ORTHO_FRAME) {
         if constexpr (K <= 3) {
-            return fwd ? launch_pre<L, K, true>(g, vt, p, s)
-                       : launch_pre_bwd<L, K, true>(g, vt, p, grad2d, R, *out, s);
+            if (g.axis_mode == SGS_AXIS_ORTHO_FIXED)
+                return fwd ? launch_pre<L, K, kAxWorld>(g, vt, p, s)
+                           : launch_pre_bwd<L, K, kAxWorld>(g, vt, p, grad2d, R, *out, s);
+            return fwd ? launch_pre<L, K, kAxFrame>(g, vt, p, s)
+                       : launch_pre_bwd<L, K, kAxFrame>(g, vt, p, grad2d, R, *out, s);
         }
         return cudaErrorInvalidValue;
     }
-    return fwd ? launch_pre<L, K, false>(g, vt, p, s)
-               : launch_pre_bwd<L, K, false>(g, vt, p, grad2d, R, *out, s);
+    return fwd ? launch_pre<L, K, kAxFree>(g, vt, p, s)
+               : launch_pre_bwd<L, K, kAxFree>(g, vt, p, grad2d, R, *out, s);
 }
 
 template <int L>

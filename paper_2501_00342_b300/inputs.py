@@ -30,6 +30,7 @@ import numpy as np
 
 AXIS_FREE = 0
 AXIS_ORTHO_FIXED = 1
+AXIS_ORTHO_FRAME = 2  # lobe axes = columns of the rotation of 3 per-Gaussian parameters
 
 CAM_FLOATS = 22  # viewmat[12], campos[3], fx, fy, cx, cy, width, height, near
 
@@ -134,8 +135,10 @@ class Scene:
 
     def floats_per_gaussian(self) -> int:
         """Parameter floats read per Gaussian: geometry 11, SH 3(L+1)^2,
-        SG 7K (free axes) or 4K (world axes, no axis stored)."""
+        SG 7K (free axes), 4K (world axes, no axis stored) or 4K + 3 (a frame)."""
         sg = (7 if self.axis_mode == AXIS_FREE else 4) * self.num_lobes
+        if self.axis_mode == AXIS_ORTHO_FRAME and self.num_lobes:
+            sg += 3  # the frame's 3 parameters
         return 11 + 3 * self.num_sh + sg
 
     def subset(self, idx) -> "Scene":
@@ -176,6 +179,12 @@ def _colour_planes(rng, n, s, sh_degree, num_lobes, axis_mode, dc=(0.5, 0.2), re
             axis = np.zeros((num_lobes, 3, s), np.float32)
             ax = _unit_rows(rng.normal(size=(num_lobes, n, 3)))
             axis[:, :, :n] = np.transpose(ax, (0, 2, 1))
+        elif axis_mode == AXIS_ORTHO_FRAME:
+            # frame parameters f: uniform random unit quaternions q, f = q_xyz / q_w
+            axis = np.zeros((3, s), np.float32)
+            q = _unit_rows(rng.normal(size=(n, 4)))
+            q *= np.sign(q[:, :1] + 1e-30)
+            axis[:, :n] = (q[:, 1:] / np.maximum(q[:, :1], 0.05)).T
     return sh, amp, axis, sharp
 
 

@@ -31,6 +31,9 @@ def make_scene(means, scales, quats, opacity, sh, sg_amp=None, sg_axis=None, sg_
         if axis_mode == I.AXIS_FREE:
             axis = plane((K, 3))
             axis[:, :, :n] = np.transpose(np.asarray(sg_axis, np.float64).reshape(n, K, 3), (1, 2, 0))
+        elif axis_mode == I.AXIS_ORTHO_FRAME:  # sg_axis: [n][3] frame parameters
+            axis = plane((3,))
+            axis[:, :n] = np.asarray(sg_axis, np.float64).reshape(n, 3).T
     return I.Scene(n, s, L, K, axis_mode, mean, scale, rot, opa, shp, amp, axis, sharp)
 
 
@@ -60,6 +63,8 @@ def random_small_scene(n, seed, sh_degree=1, K=2, axis_mode=I.AXIS_FREE, log_sca
     sh[:, 0, :] = rng.normal(0.5, 0.3, (n, 3))
     amp = rng.normal(0.0, 0.3, (n, K, 3))
     axis = rng.normal(size=(n, K, 3)) * rng.uniform(0.5, 2.0, (n, K, 1))
+    if axis_mode == I.AXIS_ORTHO_FRAME:
+        axis = rng.normal(0.0, 0.8, (n, 3))  # frame parameters
     sharp = np.exp(rng.uniform(0.0, np.log(20.0), (n, K)))
     return make_scene(means, scales, q, opacity, sh, amp if K else None,
                       axis if K else None, sharp if K else None, axis_mode)

@@ -79,7 +79,15 @@ def test_invalid_settings_rejected(bad):
     assert e.value.code == B.SGS_ERR_INVALID
 
 
-@pytest.mark.parametrize("g", [_g(L=4), _g(K=5), _g(K=4, mode=1), _g(mode=2)])
+def _adaptive(flag, r0, r1):
+    g = _g(L=2)
+    g.sh_adaptive, g.sh_radius[0], g.sh_radius[1] = flag, r0, r1
+    return g
+
+
+@pytest.mark.parametrize("g", [_g(L=4), _g(K=5), _g(K=4, mode=1), _g(K=4, mode=2), _g(mode=3),
+                               _adaptive(2, 1.0, 2.0), _adaptive(1, 3.0, 2.0), _adaptive(1, -1.0, 2.0),
+                               _adaptive(1, float("nan"), 2.0)])
 def test_invalid_gaussians_rejected(g):
     cams = [I.look_at((0, 0, 4), (0, 0, 0), 64, 64, 60)]
     with pytest.raises(B.SgsError):
@@ -121,3 +129,9 @@ def test_selftest_lookback_rejects_bad_arguments_on_host():
         B.selftest_lookback(None, 4, 8, 8, None)  # slots missing
     with pytest.raises(B.SgsError):
         B.selftest_lookback(8, 4, None, 8, None)  # sum missing
+
+
+def test_valid_colour_layouts_accepted():
+    cams = [I.look_at((0, 0, 4), (0, 0, 0), 64, 64, 60)]
+    for g in (_g(K=3, mode=2), _g(K=0, mode=2), _adaptive(1, 0.0, 0.0), _adaptive(1, 4.0, 16.0)):
+        B.workspace_size(g, cams, _s(), 1000)

@@ -61,7 +61,7 @@ def test_gradients_config0_vs_adjoint():
 
 
 @pytest.mark.parametrize("L,K,mode", [(1, 4, I.AXIS_FREE), (3, 0, I.AXIS_FREE), (0, 3, I.AXIS_ORTHO_FIXED),
-                                      (2, 2, I.AXIS_FREE)])
+                                      (2, 2, I.AXIS_FREE), (1, 3, I.AXIS_ORTHO_FRAME), (0, 2, I.AXIS_ORTHO_FRAME)])
 def test_gradients_colour_variants_vs_adjoint(L, K, mode):
     sc = random_small_scene(60, seed=40 + L * 5 + K, sh_degree=L, K=K, axis_mode=mode)
     cams = [axis_camera(48, 40, 60.0, 3.5), I.look_at((1.5, -1.0, 3.0), (0, 0, 0), 40, 48, 55.0)]

@@ -150,7 +150,8 @@ def test_multi_view_images_against_oracle():
 
 
 def test_background_and_world_axes_and_sh3():
-    for L, K, mode in [(3, 0, I.AXIS_FREE), (0, 3, I.AXIS_ORTHO_FIXED), (2, 4, I.AXIS_FREE), (1, 1, I.AXIS_ORTHO_FIXED)]:
+    for L, K, mode in [(3, 0, I.AXIS_FREE), (0, 3, I.AXIS_ORTHO_FIXED), (2, 4, I.AXIS_FREE), (1, 1, I.AXIS_ORTHO_FIXED),
+                       (1, 3, I.AXIS_ORTHO_FRAME), (0, 2, I.AXIS_ORTHO_FRAME)]:
         sc = I.uniform_cube_scene(1500, L, K, mode, config=0, stream=L * 10 + K)
         cams = [I.look_at((0.3, 0.5, 3.8), (0, 0, 0), 72, 56, 60.0)]
         bg = (0.2, 0.5, 0.9)
