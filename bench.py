@@ -395,6 +395,44 @@ def run_gpu(args):
         fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
         out["render_fps"] = fps
 
+        # ---- training iterations (render, L1, backward, fused Adam) on 2.5M Gaussians, one
+        # 1264x832 view, U(0,1) target; the lobes train from iteration 0 here (past sg_start)
+        from paper_2501_00342_b300.train import TrainConfig, Trainer
+        sc2, cams2 = I.workload(2)
+        m2 = GaussianModel.from_scene(sc2)
+        t2 = torch.from_numpy(I.target_images(cams2, config=2)[0].reshape(-1)).cuda()
+        trainer = Trainer(m2, cams2, t2, settings, TrainConfig(sg_start=0, extent=4.0))
+        trainer.step(sync=True)
+        for _ in range(args.warmup):
+            trainer.step()
+        iters = max(5, args.steps)
+        ad0, ad1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(iters):
+            trainer.rast.forward(m2, out_rgb=trainer.img, sync=False)
+            _, d2 = l1_loss(trainer.img, t2)
+            trainer.rast.backward(m2, d2, grads=trainer.grads)
+            if k == iters - 1:
+                ad0.record(stream)
+            B.adam_step(m2.struct(), *trainer._structs, trainer.adam_config(trainer.iteration), stream.cuda_stream)
+            if k == iters - 1:
+                ad1.record(stream)
+            trainer.iteration += 1
+        b2.record(stream)
+        torch.cuda.synchronize()
+        tms = a.elapsed_time(b2) / iters
+        adam_ms = ad0.elapsed_time(ad1)
+        entries = sc2.n * sc2.floats_per_gaussian()
+        adam_bytes = entries * 28 + sc2.n * 4 * 4  # raw, grad, m, v in; raw, m, v out; act of scale and opacity
+        out["train_2.5M_1264x832"] = {
+            "workload": "2.5M clustered Gaussians, SH-1 + 4 SG, one 1264x832 view, L1 vs U(0,1) target",
+            "ms_per_iteration": round(tms, 4), "iterations_per_s": round(1e3 / tms, 1),
+            "adam_ms": round(adam_ms, 4), "adam_entries": int(entries),
+            "adam_roofline": {"bound": "hbm", "achieved": round(adam_bytes / (adam_ms / 1e3) / 1e9, 1), "peak": hbm,
+                              "unit": "GB/s", "frac": round(adam_bytes / (adam_ms / 1e3) / 1e9 / hbm, 4),
+                              "algorithmic_bytes": int(adam_bytes)}}
+        del trainer, m2, t2, sc2
+
         # ---- 8M Gaussians, 8 views at 3840x2160: one batched fwd+bwd step, peak device memory
         sc4, cams4 = I.workload(4)
         m4 = GaussianModel.from_scene(sc4)

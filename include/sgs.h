@@ -283,6 +283,35 @@ sgs_status sgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t m, int
 sgs_status sgs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
                        float* dL_dimg, cudaStream_t stream);
 
+/* ---- Training: fused Adam step over the parameter planes ----
+ * The optimiser works on raw planes (same layouts as sgs_gaussians): scale holds log s and
+ * opacity holds logit o (the 3D-GS activations), every other plane is the parameter
+ * itself.  One call updates every entry of every plane with Adam (Kingma & Ba 2015):
+ *   g  = dL/d(raw) = dL/d(act) * act'(raw)   (exp for scale, sigmoid for opacity)
+ *   m  = b1 m + (1 - b1) g,   v = b2 v + (1 - b2) g^2
+ *   raw -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ *   act = exp(raw) | sigmoid(raw) | raw
+ * with the learning rate lr and step t of the entry's group.  A group whose lr is 0 is
+ * left untouched (raw, act, m and v): the paper trains the SG lobes only after the first
+ * 2,000 iterations, with lr 0.0025 (Sec. "Implementation"), and gives them their own step
+ * count from then on.  grad is sgs_render_backward's output (w.r.t. the activated
+ * parameters, the ones the renderer reads from `act`).  act planes of identity groups may
+ * alias the raw planes.  m and v start at zero (caller-owned).  Asynchronous. */
+typedef enum {
+    SGS_GROUP_MEAN = 0, SGS_GROUP_SCALE, SGS_GROUP_ROT, SGS_GROUP_OPACITY, SGS_GROUP_SH_DC,
+    SGS_GROUP_SH_REST, SGS_GROUP_SG, SGS_GROUP_COUNT
+} sgs_param_group;
+
+typedef struct {
+    float lr[SGS_GROUP_COUNT];
+    int32_t step[SGS_GROUP_COUNT]; /* t >= 1 of each group with lr > 0 */
+    float beta1, beta2, eps;
+} sgs_adam_config;
+
+sgs_status sgs_adam_step(const sgs_gaussians* layout, const sgs_grads* raw, const sgs_grads* act,
+                         const sgs_grads* grad, const sgs_grads* m, const sgs_grads* v,
+                         const sgs_adam_config* cfg, cudaStream_t stream);
+
 /* Failure-detection self-test of the bounded device-side waits; the paper has no
  * counterpart.  The scan and the radix sort find each tile's prefix by decoupled look-back,
  * polling a predecessor's 8-byte slot until it is published; every such wait gives up
@@ -300,8 +329,9 @@ sgs_status sgs_selftest_lookback(const uint64_t* slots, int64_t num_slots, uint6
 
 const char* sgs_status_string(sgs_status s);
 
-/* sizeof(sgs_plan), sizeof(sgs_camera), sizeof(sgs_gaussians), sizeof(sgs_settings) in
- * that order into sizes[4]: lets a foreign-language binding check its struct layouts. */
+/* sizeof(sgs_plan), sizeof(sgs_camera), sizeof(sgs_gaussians), sizeof(sgs_settings),
+ * sizeof(sgs_adam_config), sizeof(sgs_grads) in that order into sizes[6]: lets a
+ * foreign-language binding check its struct layouts. */
 void sgs_abi_sizes(size_t* sizes);
 
 #ifdef __cplusplus

@@ -28,7 +28,7 @@ EXPORTS = ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
            "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
            "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss", "sgs_status_string",
            "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc", "sgs_selftest_lookback",
-           "sgs_sort_pairs32")
+           "sgs_sort_pairs32", "sgs_adam_step")
 
 SORT_NOALLOC_MAX_PAIRS = 1 << 18
 
@@ -55,6 +55,14 @@ class Gaussians(C.Structure):
 class Grads(C.Structure):
     _fields_ = [(f, C.c_void_p) for f in ("mean", "scale", "rot", "opacity", "sh", "sg_amp",
                                           "sg_axis", "sg_sharp")]
+
+
+GROUPS = ("MEAN", "SCALE", "ROT", "OPACITY", "SH_DC", "SH_REST", "SG")  # sgs_param_group
+
+
+class AdamConfig(C.Structure):
+    _fields_ = [("lr", C.c_float * len(GROUPS)), ("step", C.c_int32 * len(GROUPS)), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
 
 
 class Settings(C.Structure):
@@ -111,15 +119,18 @@ def lib():
         L.sgs_sort_pairs_noalloc.restype = st
         L.sgs_sort_pairs32.argtypes = [vp, vp, i64, i32, i32, vp, C.c_size_t, vp]
         L.sgs_sort_pairs32.restype = st
+        L.sgs_adam_step.argtypes = [P(Gaussians), P(Grads), P(Grads), P(Grads), P(Grads), P(Grads), P(AdamConfig), vp]
+        L.sgs_adam_step.restype = st
         L.sgs_selftest_lookback.argtypes = [vp, i64, vp, vp, vp]
         L.sgs_selftest_lookback.restype = st
         for f in ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
                   "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
                   "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss"):
             getattr(L, f).restype = st
-        sizes = (C.c_size_t * 4)()
+        sizes = (C.c_size_t * 6)()
         L.sgs_abi_sizes(sizes)
-        want = (C.sizeof(Plan), C.sizeof(Camera), C.sizeof(Gaussians), C.sizeof(Settings))
+        want = (C.sizeof(Plan), C.sizeof(Camera), C.sizeof(Gaussians), C.sizeof(Settings), C.sizeof(AdamConfig),
+                C.sizeof(Grads))
         if tuple(sizes) != want:
             raise RuntimeError(f"sgs ABI mismatch: library {tuple(sizes)} vs binding {want}")
         _lib = L
@@ -234,6 +245,11 @@ def sort_pairs_noalloc(keys_ptr, vals_ptr, m, key_bits, digit_bits, stream):
     """In-place sort with the library's own fixed scratch (no allocation anywhere)."""
     check("sgs_sort_pairs_noalloc",
           lib().sgs_sort_pairs_noalloc(keys_ptr, vals_ptr, int(m), int(key_bits), int(digit_bits), stream))
+
+
+def adam_step(layout, raw, act, grad, m, v, cfg, stream):
+    check("sgs_adam_step", lib().sgs_adam_step(C.byref(layout), C.byref(raw), C.byref(act), C.byref(grad),
+                                               C.byref(m), C.byref(v), C.byref(cfg), stream))
 
 
 # slot flags of sgs_selftest_lookback

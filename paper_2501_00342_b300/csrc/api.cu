@@ -153,6 +153,8 @@ void sgs_abi_sizes(size_t* sizes) {
     sizes[1] = sizeof(sgs_camera);
     sizes[2] = sizeof(sgs_gaussians);
     sizes[3] = sizeof(sgs_settings);
+    sizes[4] = sizeof(sgs_adam_config);
+    sizes[5] = sizeof(sgs_grads);
 }
 
 sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, int32_t B,
@@ -481,6 +483,33 @@ sgs_status sgs_selftest_lookback(const uint64_t* slots, int64_t num_slots, uint6
     if (num_slots < 0 || !sum || !status || (num_slots > 0 && !slots)) return SGS_ERR_INVALID;
     SGS_TRY(launch_lookback_selftest(reinterpret_cast<const unsigned long long*>(slots), num_slots,
                                      reinterpret_cast<unsigned long long*>(sum), status, stream));
+    return SGS_OK;
+}
+
+sgs_status sgs_adam_step(const sgs_gaussians* layout, const sgs_grads* raw, const sgs_grads* act,
+                         const sgs_grads* grad, const sgs_grads* m, const sgs_grads* v,
+                         const sgs_adam_config* cfg, cudaStream_t stream) {
+    if (!layout || !raw || !act || !grad || !m || !v || !cfg || check_gaussians(layout) != SGS_OK)
+        return SGS_ERR_INVALID;
+    if (!(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f && cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f && cfg->eps >= 0.0f))
+        return SGS_ERR_INVALID;
+    for (int gi = 0; gi < SGS_GROUP_COUNT; ++gi)
+        if (!(cfg->lr[gi] >= 0.0f) || (cfg->lr[gi] > 0.0f && cfg->step[gi] < 1)) return SGS_ERR_INVALID;
+    if (layout->n > 0) {
+        const sgs_grads* sets[] = {raw, act, grad, m, v};
+        for (const sgs_grads* q : sets) {
+            const float* need[] = {q->mean, q->scale, q->rot, q->opacity, q->sh};
+            for (const float* ptr : need)
+                if (!ptr || !aligned16(ptr)) return SGS_ERR_INVALID;
+            if (layout->num_lobes > 0 && (!q->sg_amp || !q->sg_sharp || !aligned16(q->sg_amp) || !aligned16(q->sg_sharp)))
+                return SGS_ERR_INVALID;
+            if (layout->num_lobes > 0 && layout->axis_mode != SGS_AXIS_ORTHO_FIXED &&
+                (!q->sg_axis || !aligned16(q->sg_axis)))
+                return SGS_ERR_INVALID;
+        }
+        if (act->scale == raw->scale || act->opacity == raw->opacity) return SGS_ERR_INVALID;
+    }
+    SGS_TRY(launch_adam(*layout, *raw, *act, *grad, *m, *v, *cfg, stream));
     return SGS_OK;
 }
 

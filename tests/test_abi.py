@@ -29,9 +29,10 @@ def test_library_exports_every_declared_function():
 
 
 def test_struct_layouts_match():
-    sizes = (C.c_size_t * 4)()
+    sizes = (C.c_size_t * 6)()
     B.lib().sgs_abi_sizes(sizes)
-    assert tuple(sizes) == (C.sizeof(B.Plan), C.sizeof(B.Camera), C.sizeof(B.Gaussians), C.sizeof(B.Settings))
+    assert tuple(sizes) == (C.sizeof(B.Plan), C.sizeof(B.Camera), C.sizeof(B.Gaussians), C.sizeof(B.Settings),
+                            C.sizeof(B.AdamConfig), C.sizeof(B.Grads))
     assert C.sizeof(B.Camera) == 88
 
 

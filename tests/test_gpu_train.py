@@ -1,0 +1,90 @@
+"""The fused Adam step against the FP64 oracle Adam, and the training loop (render, L1,
+backward, Adam) on a small fitting problem with the staged introduction of the lobes."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adam as A
+from paper_2501_00342_b300 import binding as B
+from paper_2501_00342_b300 import inputs as I
+from paper_2501_00342_b300.render import PLANES, GaussianModel, Rasterizer, RenderSettings
+from paper_2501_00342_b300.train import TrainConfig, Trainer
+from tests.helpers import axis_camera, random_small_scene
+
+pytestmark = pytest.mark.gpu
+
+LR = dict(MEAN=1e-3, SCALE=5e-3, ROT=1e-3, OPACITY=5e-2, SH_DC=2.5e-3, SH_REST=1.25e-4, SG=2.5e-3)
+
+
+@pytest.mark.parametrize("mode", [I.AXIS_FREE, I.AXIS_ORTHO_FRAME, I.AXIS_ORTHO_FIXED])
+def test_adam_step_matches_oracle(mode):
+    sc = random_small_scene(1001, seed=60 + mode, sh_degree=2, K=3, axis_mode=mode)
+    model = GaussianModel.from_scene(sc)
+    act = model.planes
+    rng = np.random.default_rng(7)
+    raw = {p: (None if t is None else torch.from_numpy(rng.normal(0, 0.5, t.shape).astype(np.float32)).cuda())
+           for p, t in act.items()}
+    act = {p: (None if t is None else (torch.empty_like(t) if p in ("scale", "opacity") else raw[p]))
+           for p, t in act.items()}
+    m = {p: (None if t is None else torch.zeros_like(t)) for p, t in raw.items()}
+    v = {p: (None if t is None else torch.zeros_like(t)) for p, t in raw.items()}
+    x64 = {p: (None if t is None else t.cpu().numpy().astype(np.float64)) for p, t in raw.items()}
+    m64 = {p: (None if t is None else np.zeros(t.shape)) for p, t in raw.items()}
+    v64 = {p: (None if t is None else np.zeros(t.shape)) for p, t in raw.items()}
+    structs = [B.Grads(*[B.ptr(d[p]) for p in PLANES]) for d in (raw, act)]
+    steps = {k: 0 for k in LR}
+    for it in range(5):
+        lr = dict(LR, SG=0.0 if it < 2 else LR["SG"])  # lobes frozen for two steps
+        for k in steps:
+            steps[k] += 1 if (k != "SG" or it >= 2) else 0
+        g = {p: (None if t is None else torch.from_numpy(rng.normal(0, 1, t.shape).astype(np.float32)).cuda())
+             for p, t in raw.items()}
+        cfg = B.AdamConfig()
+        for j, k in enumerate(B.GROUPS):
+            cfg.lr[j], cfg.step[j] = lr[k], max(1, steps[k])
+        cfg.beta1, cfg.beta2, cfg.eps = 0.9, 0.999, 1e-15
+        gs = B.Grads(*[B.ptr(g[p]) for p in PLANES])
+        ms, vs = (B.Grads(*[B.ptr(d[p]) for p in PLANES]) for d in (m, v))
+        B.adam_step(model.struct(), structs[0], structs[1], gs, ms, vs, cfg, torch.cuda.current_stream().cuda_stream)
+        g64 = {p: (None if t is None else t.cpu().numpy().astype(np.float64)) for p, t in g.items()}
+        x64, a64, m64, v64 = A.adam_step(x64, g64, m64, v64, lr, {k: max(1, s) for k, s in steps.items()}, sc.n)
+    torch.cuda.synchronize()
+    n = sc.n
+    for p in PLANES:
+        if raw[p] is None:
+            continue
+        x = raw[p].cpu().numpy()[..., :n]
+        assert np.abs(x - x64[p][..., :n]).max() <= 2e-6 * np.abs(x64[p][..., :n]).max() + 5e-7, p
+        assert np.abs(m[p].cpu().numpy()[..., :n] - m64[p][..., :n]).max() <= 1e-5, p
+        assert np.abs(v[p].cpu().numpy()[..., :n] - v64[p][..., :n]).max() <= 1e-5, p
+        a = act[p].cpu().numpy()[..., :n]
+        assert np.abs(a - a64[p][..., :n]).max() <= 1e-5 * max(1.0, np.abs(a64[p][..., :n]).max()), p
+
+
+def test_training_fits_and_introduces_lobes_late():
+    truth = random_small_scene(50, seed=70, sh_degree=1, K=3, axis_mode=I.AXIS_ORTHO_FRAME)
+    cams = [axis_camera(64, 48, 60.0, 3.2), I.look_at((1.2, 0.6, 3.0), (0, 0, 0), 48, 64, 55.0)]
+    tm = GaussianModel.from_scene(truth)
+    tr = Rasterizer(tm, cams, RenderSettings())
+    target = tr.forward(tm).clone()
+    start = random_small_scene(50, seed=70, sh_degree=1, K=3, axis_mode=I.AXIS_ORTHO_FRAME)
+    rng = np.random.default_rng(71)
+    start.mean[:, :50] += rng.normal(0, 0.05, (3, 50)).astype(np.float32)
+    start.sh[:, :, :50] = rng.normal(0, 0.2, (4, 3, 50)).astype(np.float32)
+    start.sg_amp[:] = 0.0
+    model = GaussianModel.from_scene(start)
+    cfg = TrainConfig(iterations=200, sg_start=60, lr_mean=1e-3, lr_mean_final=1e-4)
+    tr = Trainer(model, cams, target, RenderSettings(), cfg)
+    losses = [float(tr.step(sync=True).item())]
+    sg0 = {p: model.planes[p].clone() for p in ("sg_amp", "sg_axis", "sg_sharp")}
+    for it in range(1, 200):
+        loss = tr.step()
+        if it == 59:
+            torch.cuda.synchronize()
+            for p, t in sg0.items():
+                assert torch.equal(model.planes[p], t), p  # lobes frozen before sg_start
+        losses.append(float(loss.item()) if it % 20 == 0 or it == 199 else losses[-1])
+    torch.cuda.synchronize()
+    assert not torch.equal(model.planes["sg_amp"], sg0["sg_amp"])  # and trained after
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+    assert tr.rast.device_status() == 0
