@@ -140,7 +140,7 @@ def run_gpu(args):
 
     stream = torch.cuda.current_stream()
     settings = RenderSettings(tile_w=args.tile[0], tile_h=args.tile[1], batch_depth=args.batch_depth,
-                              digit_bits=args.digit_bits)
+                              digit_bits=args.digit_bits, fwd_pixels=args.fwd_pixels, bwd_pixels=args.bwd_pixels)
     from paper_2501_00342_b300.autotune import autotune
     if args.workload == "single":  # small profiling case: 1 M Gaussians, one 1280x720 view
         scene, cams = I.workload(1, sh_degree=1, num_lobes=4)
@@ -294,7 +294,8 @@ def run_gpu(args):
                    "resolutions": [[c.width, c.height] for c in cams], "pixels": int(rast.num_pixels),
                    "instances": M, "sort_passes": P, "key_bits": int(rast.plan.key_bits),
                    "tile": [settings.tile_w, settings.tile_h], "batch_depth": settings.batch_depth,
-                   "digit_bits": settings.digit_bits,
+                   "digit_bits": settings.digit_bits, "fwd_pixels": settings.fwd_pixels,
+                   "bwd_pixels": settings.bwd_pixels,
                    "l2": f"inputs larger than L2: {n * p_bytes / 1e6:.0f} MB parameters, "
                          f"{rast.nbytes / 1e9:.2f} GB workspace",
                    "parallelism": f"view batches per rank x{world}"},
@@ -615,6 +616,8 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=(16, 32))
     ap.add_argument("--batch-depth", type=int, default=512)
     ap.add_argument("--digit-bits", type=int, default=9)
+    ap.add_argument("--fwd-pixels", type=int, default=0, help="pixels per thread, forward blend (0: library's)")
+    ap.add_argument("--bwd-pixels", type=int, default=0, help="pixels per thread, backward blend (0: library's)")
     ap.add_argument("--workload", default="batched", choices=("batched", "single", "medium"),
                     help="single: 1M Gaussians, one 1280x720 view; medium: the 3M scene, two "
                          "1920x1080 views (smaller cases for profilers)")

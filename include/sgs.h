@@ -118,13 +118,17 @@ typedef struct {
 } sgs_grads;
 
 typedef struct {
-    int32_t tile_w, tile_h; /* screen tile, pixels; tile_w * tile_h in {64,128,256,512} */
+    int32_t tile_w, tile_h; /* screen tile, pixels; powers of two >= 8, 64..512 pixels */
     int32_t batch_depth;    /* Gaussians staged in shared memory per blend batch: 32..1024 */
     int32_t digit_bits;     /* widest radix-sort digit, 4..10: a sort of b bits takes
                                ceil(b / digit_bits) passes of equal, narrowest width */
     int32_t memory_mode;    /* 0: backward recomputes per tile from the sorted list
                                (no per-pixel contributor lists are ever stored) */
     float bg[3];            /* background colour added as T_final * bg */
+    int32_t fwd_pixels;     /* pixels per thread of the forward blend: 0 (auto: 2), 1 or 2 */
+    int32_t bwd_pixels;     /* pixels per thread of the backward blend: 0 (auto: 2), 1, 2 or 4
+                               (4 needs tile_h a multiple of 16).  Results do not depend on
+                               either (the backward's float atomics may add in another order). */
 } sgs_settings;
 
 /* Host-side plan: sizes and workspace offsets.  Filled by sgs_workspace_size(); the

@@ -1,10 +1,10 @@
 """Autotuner for the rasterizer's launch settings: tile size, Gaussians per shared-memory
-batch and radix-sort digit width.
+batch, radix-sort digit width and the blend kernels' pixels per thread.
 
 The image does not depend on any of them (the support is the 3-sigma ellipse, not the
 tile), so they can be chosen for speed alone.  The tuner times one forward + backward
 step per candidate on the caller's own Gaussians and cameras (coordinate descent: tile
-size first, then batch depth, then digit width) and caches the winner per workload
+size first, then batch depth, digit width and pixels per thread) and caches the winner per workload
 signature in a JSON file.
 """
 from __future__ import annotations
@@ -17,11 +17,14 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
+from . import binding as B
 from .render import GaussianModel, Rasterizer, RenderSettings
 
 TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 16), (16, 32), (32, 8), (16, 8), (64, 8), (8, 8))
 BATCHES: Tuple[int, ...] = (128, 256, 512)
 DIGITS: Tuple[int, ...] = (8, 9, 10)
+FWD_PIXELS: Tuple[int, ...] = (1, 2)
+BWD_PIXELS: Tuple[int, ...] = (2, 4)
 
 
 def signature(model: GaussianModel, cams) -> str:
@@ -63,7 +66,8 @@ def time_step(model: GaussianModel, cams, settings: RenderSettings, steps: int =
 def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings(),
              cache_path: Optional[str] = None, steps: int = 3,
              tiles: Sequence[Tuple[int, int]] = TILES, batches: Sequence[int] = BATCHES,
-             digits: Sequence[int] = DIGITS, log: Optional[List[Dict]] = None) -> RenderSettings:
+             digits: Sequence[int] = DIGITS, fwd_pixels: Sequence[int] = FWD_PIXELS,
+             bwd_pixels: Sequence[int] = BWD_PIXELS, log: Optional[List[Dict]] = None) -> RenderSettings:
     """Best settings for this workload (from the cache when present)."""
     key = signature(model, cams)
     cache: Dict[str, Dict] = {}
@@ -76,7 +80,8 @@ def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings()
     best = base
     best_ms = time_step(model, cams, best, steps)
     trials = [dict(settings=dataclasses.asdict(best), ms=best_ms)]
-    for field, values in (("tile", tiles), ("batch_depth", batches), ("digit_bits", digits)):
+    for field, values in (("tile", tiles), ("batch_depth", batches), ("digit_bits", digits),
+                          ("fwd_pixels", fwd_pixels), ("bwd_pixels", bwd_pixels)):
         for v in values:
             if field == "tile":
                 cand = dataclasses.replace(best, tile_w=v[0], tile_h=v[1])
@@ -84,7 +89,10 @@ def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings()
                 cand = dataclasses.replace(best, **{field: v})
             if cand == best:
                 continue
-            ms = time_step(model, cams, cand, steps)
+            try:
+                ms = time_step(model, cams, cand, steps)
+            except B.SgsError:  # a combination the library rejects (e.g. 4 rows of 8-high tiles)
+                continue
             trials.append(dict(settings=dataclasses.asdict(cand), ms=ms))
             if ms < best_ms:
                 best, best_ms = cand, ms

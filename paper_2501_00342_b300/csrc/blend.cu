@@ -434,12 +434,6 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 
 }  // namespace
 
-// Pixels per thread of the backward kernel: 2 when the tile splits into warp blocks of
-// 8 x 8 pixels (tile sides are multiples of 8), else 1.
-static int pixels_per_thread(const ViewTable& vt) {
-    return (vt.tile_h % 8 == 0 && vt.tile_w % 8 == 0) ? 2 : 1;
-}
-
 template <int PPT>
 static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uint32_t* vals, int64_t R,
                              const RecordPtrs& p, int batch, float bg0, float bg1, float bg2, float* out_rgb,
@@ -477,7 +471,9 @@ cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_
                          float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
                          uint2* pix_count, const DeviceStatus* st, cudaStream_t s) {
     if (vt.num_tiles == 0) return cudaSuccess;
-    // one pixel per thread: the forward's early exit loses more than the shared reads save
+    if (vt.fwd_ppt == 2)
+        return blend_ppt<2>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last,
+                            pix_count, st, s);
     return blend_ppt<1>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, pix_count,
                         st, s);
 }
@@ -488,7 +484,10 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                   const float* dL_drgb, float4* grad2d, int64_t R,
                                   const DeviceStatus* st, cudaStream_t s) {
     if (vt.num_tiles == 0 || R == 0) return cudaSuccess;
-    if (pixels_per_thread(vt) == 2)
+    if (vt.bwd_ppt == 4)
+        return blend_backward_ppt<4>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d,
+                                     R, st, s);
+    if (vt.bwd_ppt == 2)
         return blend_backward_ppt<2>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d,
                                      R, st, s);
     return blend_backward_ppt<1>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d, R,

@@ -22,11 +22,14 @@ class RenderSettings:
     batch_depth: int = 256
     digit_bits: int = 9
     bg: tuple = (0.0, 0.0, 0.0)
+    fwd_pixels: int = 0  # pixels per thread of the blend kernels (0: the library's choice)
+    bwd_pixels: int = 0
 
     def struct(self) -> B.Settings:
         s = B.Settings()
         s.tile_w, s.tile_h = self.tile_w, self.tile_h
         s.batch_depth, s.digit_bits, s.memory_mode = self.batch_depth, self.digit_bits, 0
+        s.fwd_pixels, s.bwd_pixels = self.fwd_pixels, self.bwd_pixels
         for k in range(3):
             s.bg[k] = float(self.bg[k])
         return s

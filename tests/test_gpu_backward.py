@@ -86,6 +86,18 @@ def test_gradients_adaptive_sh_vs_adjoint():
         assert np.all(g["sh"][(top[i] + 1) ** 2:, :, i] == 0.0)
 
 
+@pytest.mark.parametrize("tile,bwd", [((16, 16), 4), ((16, 32), 4), ((16, 32), 1), ((8, 8), 2)])
+def test_backward_pixels_per_thread(tile, bwd):
+    sc, cams = I.workload(0)
+    ws = _weights(sc, cams, 8)
+    g = _gpu_grads(sc, cams, ws, RenderSettings(tile_w=tile[0], tile_h=tile[1], bwd_pixels=bwd))
+    _compare(sc, cams, ws, g, _oracle_grads(sc, cams, ws))
+    ref = _gpu_grads(sc, cams, ws)
+    for p in PLANES:
+        if ref[p] is not None:  # the same sums, added in another order
+            assert np.abs(g[p] - ref[p]).max() <= 1e-5 * np.abs(ref[p]).max(), p
+
+
 def _slice_200():
     """200 clustered Gaussians (the training-step distribution), one 32x32 view."""
     sc = I.cluster_scene(200, 1, 4, config=2, num_clusters=8)

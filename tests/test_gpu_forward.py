@@ -122,6 +122,14 @@ def test_batch_depth_does_not_change_image(batch):
     assert torch.equal(img, ref_img)
 
 
+@pytest.mark.parametrize("tile,fwd", [((16, 16), 2), ((16, 32), 2), ((32, 16), 1), ((8, 8), 2)])
+def test_pixels_per_thread_does_not_change_image(tile, fwd):
+    sc, cams = I.workload(0)
+    _, _, img, _ = _run(sc, cams, RenderSettings(tile_w=tile[0], tile_h=tile[1], fwd_pixels=fwd))
+    _, _, ref_img, _ = _run(sc, cams)
+    assert torch.equal(img, ref_img)
+
+
 @pytest.mark.parametrize("digit", [4, 5, 6, 7, 9, 10])
 def test_digit_width_gives_identical_sort(digit):
     sc, cams = I.workload(0)
