@@ -355,31 +355,36 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                 BwdPixel& p = P[q];
                 if ((uint32_t)k >= p.last) continue;
                 const float dx = a.x - p.pxc, dy = a.y - p.pyc;
-                const float power = support_power(a.z, a.w, b.x, dx, dy);
-                const float G = __expf(power);
+                const SupportTerms st = support_terms(a.z, a.w, b.x, dx, dy);
+                if (!(st.power >= kSupportPower)) continue;  // also skips a NaN exponent
+                const float G = __expf(st.power);
                 const float oG = b.y * G;
                 const float alpha = fminf(kAlphaMax, oG);
-                if (!(power >= kSupportPower && alpha >= kAlphaMin)) continue;
+                if (!(alpha >= kAlphaMin)) continue;
                 any = true;
                 p.T = __fdividef(p.T, 1.0f - alpha);
                 const float w = alpha * p.T;
-                d[6] += p.g0 * w;
-                d[7] += p.g1 * w;
-                d[8] += p.g2 * w;
-                const float dalpha =
-                    p.T * (p.g0 * (c.x - p.acc0) + p.g1 * (c.y - p.acc1) + p.g2 * (c.z - p.acc2));
-                p.acc0 = p.acc0 * (1.0f - alpha) + c.x * alpha;
-                p.acc1 = p.acc1 * (1.0f - alpha) + c.y * alpha;
-                p.acc2 = p.acc2 * (1.0f - alpha) + c.z * alpha;
+                d[6] = fmaf(p.g0, w, d[6]);
+                d[7] = fmaf(p.g1, w, d[7]);
+                d[8] = fmaf(p.g2, w, d[8]);
+                // colour behind minus this Gaussian's colour; acc += alpha (c - acc)
+                const float e0 = c.x - p.acc0, e1 = c.y - p.acc1, e2 = c.z - p.acc2;
+                const float dalpha = p.T * fmaf(p.g0, e0, fmaf(p.g1, e1, p.g2 * e2));
+                p.acc0 = fmaf(alpha, e0, p.acc0);
+                p.acc1 = fmaf(alpha, e1, p.acc1);
+                p.acc2 = fmaf(alpha, e2, p.acc2);
                 if (oG <= kAlphaMax) {
-                    const float gpow = dalpha * b.y * G;
-                    // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2)
-                    d[0] += gpow * (2.0f * a.z * dx + a.w * dy);
-                    d[1] += gpow * (a.w * dx + 2.0f * b.x * dy);
-                    d[2] += gpow * (-0.5f * dx * dx);
-                    d[3] += gpow * (-dx * dy);
-                    d[4] += gpow * (-0.5f * dy * dy);
-                    d[5] += dalpha * G;
+                    // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2):
+                    // d/d px = u + qa dx, d/d py = qb dx + 2 qc dy, d/d(qa, qb, qc) = (dx^2, dx dy, dy^2)
+                    const float gG = dalpha * G;
+                    const float gpow = gG * b.y;
+                    d[0] = fmaf(gpow, fmaf(a.z, dx, st.u), d[0]);
+                    d[1] = fmaf(gpow, fmaf(a.w, dx, st.t + st.t), d[1]);
+                    const float h = -0.5f * gpow;
+                    d[2] = fmaf(h * dx, dx, d[2]);
+                    d[3] = fmaf(-gpow * dx, dy, d[3]);
+                    d[4] = fmaf(h * dy, dy, d[4]);
+                    d[5] += gG;
                 }
             }
             if (__any_sync(kFullMask, any)) {

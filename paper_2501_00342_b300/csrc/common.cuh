@@ -108,6 +108,19 @@ __device__ __forceinline__ float support_power(float qa, float qb, float qc, flo
     return __fmaf_rn(dx, u, w);
 }
 
+// The same exponent with its intermediates u = qa dx + qb dy and t = qc dy kept for the
+// backward pass (d power/d dx = u + qa dx, d power/d dy = qb dx + 2 t).
+struct SupportTerms {
+    float power, u, t;
+};
+__device__ __forceinline__ SupportTerms support_terms(float qa, float qb, float qc, float dx, float dy) {
+    SupportTerms s;
+    s.u = __fmaf_rn(qa, dx, __fmul_rn(qb, dy));
+    s.t = __fmul_rn(qc, dy);
+    s.power = __fmaf_rn(dx, s.u, __fmul_rn(s.t, dy));
+    return s;
+}
+
 // Tiles the Gaussian's 3-sigma ellipse reaches, row by row.  E = {d : Q(d) <= k} with
 // Q(d) = A dx^2 + 2 B dx dy + C dy^2 (the conic), k = 9.01: the support is Q <= 9, and the
 // 0.1 % slack plus a 1/64-pixel pad cover rounding, so no tile holding a supported pixel
