@@ -276,14 +276,15 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
                             2 * (size_t)((R + kScanTile - 1) / kScanTile + 1), stream));
     // (c, depth half) stable sort of the records by view depth bits
     const int rpasses = sort_passes(0, 32, plan->settings.digit_bits);
-    SGS_TRY(launch_record_keys(rp.tiles, rp.rec1, R, region<uint32_t>(plan, O_RK0),
-                               region<uint32_t>(plan, O_RV0), st, stream));
+    SGS_TRY(launch_record_keys(rp.tiles, rp.rec1, R, region<uint32_t>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
+                               st, plan->settings.digit_bits, region<uint32_t>(plan, O_HIST), stream));
     if (R > 0)
         SGS_TRY(launch_sort(region<uint32_t>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
                             region<uint32_t>(plan, O_RK1), region<uint32_t>(plan, O_RV1),
                             &st->num_records, R, 0, 32, plan->settings.digit_bits, region<uint32_t>(plan, O_HIST),
                             region<uint32_t>(plan, O_GOFF), region<uint32_t>(plan, O_COUNTERS),
-                            region<unsigned long long>(plan, O_RLB), st, stream, nullptr));
+                            region<unsigned long long>(plan, O_RLB), st, stream, nullptr,
+                            /*histogram_ready=*/true));
     const uint32_t* perm = region<uint32_t>(plan, (rpasses & 1) ? O_RV1 : O_RV0);
     // (b) counts and instances in depth order
     SGS_TRY(launch_scan(rp.tiles, perm, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));

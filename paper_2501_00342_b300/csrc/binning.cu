@@ -127,14 +127,66 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // Keys of the record sort: the float bits of the view depth of a record with instances
 // (depth > near > 0, so the bits order like the values), 0xffffffff for the others.
-__global__ void record_keys_kernel(const uint32_t* __restrict__ tiles, const float4* __restrict__ rec1,
-                                   int64_t R, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                   DeviceStatus* st) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0) st->num_records = (uint32_t)R;
-    if (r >= R) return;
-    keys[r] = tiles[r] ? __float_as_uint(rec1[r].z) : 0xffffffffu;
-    vals[r] = (uint32_t)r;
+// The lanes holding the same value d (d < 2^BITS), from one ballot per bit.
+template <int BITS>
+__device__ __forceinline__ uint32_t same_value_lanes(uint32_t d) {
+    uint32_t peers = kFullMask;
+#pragma unroll
+    for (int i = 0; i < BITS; ++i) {
+        const uint32_t bit = (d >> i) & 1u;
+        const uint32_t b = __ballot_sync(kFullMask, bit);
+        peers &= bit ? b : ~b;
+    }
+    return peers;
+}
+
+// Keys of the record sort (view depth bits; 0xffffffff for a record without instances) and
+// ids, with the digit histograms of every pass of that sort counted on the way (per-warp
+// shared copies).  The low digits of depth bits are spread: one shared atomic each; the
+// high ones (exponent and top mantissa bits) repeat within a warp: the warp adds each
+// distinct digit once.
+template <int RB>
+__global__ void __launch_bounds__(256) record_keys_kernel(const uint32_t* __restrict__ tiles,
+                                                           const float4* __restrict__ rec1, int64_t R,
+                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                           DeviceStatus* st, int passes, uint32_t* __restrict__ hist) {
+    constexpr int RADIX = 1 << RB;
+    extern __shared__ uint32_t h[];  // [8 warps][passes][RADIX]
+    for (int j = threadIdx.x; j < 8 * passes * RADIX; j += blockDim.x) h[j] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* hw = h + warp * passes * RADIX;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->num_records = (uint32_t)R;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: every lane of a warp runs the same iterations
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < R; base += stride) {
+        const int64_t r = base + lane;
+        const bool valid = r < R;
+        uint32_t key = 0xffffffffu;
+        if (valid) {
+            key = tiles[r] ? __float_as_uint(rec1[r].z) : 0xffffffffu;
+            keys[r] = key;
+            vals[r] = (uint32_t)r;
+        }
+        const uint32_t live = __ballot_sync(kFullMask, valid);
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = (key >> (p * RB)) & (RADIX - 1);
+            if (2 * p < passes) {
+                if (valid) atomicAdd(&hw[p * RADIX + d], 1u);
+            } else {
+                const uint32_t peers = same_value_lanes<RB>(d) & live;
+                if (valid && lane == 31 - __clz(peers)) hw[p * RADIX + d] += __popc(peers);
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) acc += h[w * passes * RADIX + j];
+        if (acc) atomicAdd(&hist[j], acc);
+    }
 }
 
 // Digit counts of the tile sort (its digits cover the tile id, bits 32 and up of a key) for
@@ -404,10 +456,27 @@ cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t 
 
 namespace sgs {
 cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
-                               uint32_t* vals, DeviceStatus* st, cudaStream_t s) {
+                               uint32_t* vals, DeviceStatus* st, int digit_bits, uint32_t* hist, cudaStream_t s) {
+    int passes, rb;
+    sort_digit_plan(0, 32, digit_bits, &passes, &rb);
+    cudaError_t e = launch_fill_u32(hist, 0u, (size_t)passes << rb, s);
+    if (e != cudaSuccess) return e;
     const int threads = 256;
-    const int64_t blocks = (R + threads - 1) / threads;
-    record_keys_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), threads, 0, s>>>(tiles, rec1, R, keys, vals, st);
+    const int64_t want = (R + threads - 1) / threads;
+    const unsigned blocks = (unsigned)(want < 1 ? 1 : (want < 148 * 8 ? want : 148 * 8));
+    const size_t smem = (size_t)8 * passes * ((size_t)1 << rb) * sizeof(uint32_t);
+    switch (rb) {
+#define SGS_RK(RB)                                                                                              \
+    case RB:                                                                                                     \
+        if ((e = cudaFuncSetAttribute(record_keys_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                      (int)smem)) != cudaSuccess)                                                \
+            return e;                                                                                            \
+        record_keys_kernel<RB><<<blocks, threads, smem, s>>>(tiles, rec1, R, keys, vals, st, passes, hist);      \
+        break;
+        SGS_RK(4) SGS_RK(5) SGS_RK(6) SGS_RK(7) SGS_RK(8)
+#undef SGS_RK
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 }  // namespace sgs

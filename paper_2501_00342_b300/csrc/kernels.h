@@ -43,7 +43,7 @@ cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n,
 // Keys (view depth bits; 0xffffffff without instances) and ids of the record sort; also
 // stores R in st->num_records.
 cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
-                               uint32_t* vals, DeviceStatus* st, cudaStream_t s);
+                               uint32_t* vals, DeviceStatus* st, int digit_bits, uint32_t* hist, cudaStream_t s);
 // Exclusive scan of tiles[perm[j]] (or tiles[j] when perm is null).
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
