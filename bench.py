@@ -38,6 +38,29 @@ WORKLOAD = ("3M clustered Gaussians, SH-1 + 4 SG lobes (free axes), 16 orbit vie
             "{640x360,1280x720,1600x900,1920x1080}, L1 vs U(0,1) targets, forward + backward")
 
 
+# DRAM bytes per unit of the profiled kernels (profiles/dram_traffic.md), valid while the
+# kernel's source file keeps the hash recorded there
+def _traffic_rates():
+    import hashlib
+    import re
+    rates = {}
+    try:
+        text = open(os.path.join(ROOT, "profiles", "dram_traffic.md")).read()
+    except OSError:
+        return rates
+    for m in re.finditer(r"^\| (\w+)(?: \([^)]*\))? \| (\w+\.cu) \| ([0-9a-f]{12}) \| [^|]+ \| (\w+) \| ([0-9.]+) \|",
+                         text, re.M):
+        kernel, src, sha, unit, rate = m.groups()
+        path = os.path.join(ROOT, "paper_2501_00342_b300", "csrc", src)
+        try:
+            now = hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+        except OSError:
+            continue
+        if now == sha:
+            rates[kernel] = (unit, float(rate))
+    return rates
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -264,6 +287,14 @@ def run_gpu(args):
                                            work=2 * n * p_bytes + visible * 48),
     }
     dom_name = max(kernels, key=lambda k: kernels[k]["ms"] * kernels[k]["launches"])
+    units = {"pixel": rast.num_pixels, "instance": M}
+    rates = _traffic_rates()
+
+    def traffic(name):
+        if name not in rates or rates[name][0] not in units:
+            return None
+        return int(rates[name][1] * units[rates[name][0]])
+
     roofs = {}
     for name, k in kernels.items():
         if k["work"] is None:
@@ -271,16 +302,18 @@ def run_gpu(args):
         if k["bound"] == "hbm":
             achieved = k["work"] / (k["ms"] / 1e3) / 1e9
             roofs[name] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                           "frac": round(achieved / hbm, 4), "traffic": None,
+                           "frac": round(achieved / hbm, 4), "traffic": traffic(name),
                            "algorithmic_bytes_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
         else:
             achieved = k["work"] / (k["ms"] / 1e3) / 1e12
             roofs[name] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
-                           "unit": "Tops/s (FP32 ops)", "frac": round(achieved / alu_peak, 4), "traffic": None,
+                           "unit": "Tops/s (FP32 ops)", "frac": round(achieved / alu_peak, 4), "traffic": traffic(name),
                            "algorithmic_ops_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
     dominant = dict(roofs.get(dom_name, {}))
     dominant["kernel"] = dom_name
     dominant["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs; alu = 148 SMs x 128 lanes x sm_max_mhz)"
+    dominant["traffic_source"] = ("ncu DRAM bytes per unit on a smaller case, scaled by this workload's units "
+                                  "(profiles/dram_traffic.md)")
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
