@@ -10,6 +10,7 @@ signature in a JSON file.
 from __future__ import annotations
 
 import dataclasses
+import gc
 import hashlib
 import json
 import os
@@ -59,8 +60,17 @@ def time_step(model: GaussianModel, cams, settings: RenderSettings, steps: int =
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
-    del rast, img, grads
     return ms
+
+
+def _measure(model, cams, settings, steps) -> float:
+    """time_step, then release the trial's workspace at once (workspaces are tens of GB; a
+    reference cycle anywhere would otherwise keep several alive until the next collection)."""
+    try:
+        return time_step(model, cams, settings, steps)
+    finally:
+        gc.collect()
+        torch.cuda.empty_cache()
 
 
 def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings(),
@@ -78,7 +88,7 @@ def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings()
             return RenderSettings(**{**dataclasses.asdict(base), **cache[key]["settings"],
                                      "bg": base.bg})
     best = base
-    best_ms = time_step(model, cams, best, steps)
+    best_ms = _measure(model, cams, best, steps)
     trials = [dict(settings=dataclasses.asdict(best), ms=best_ms)]
     for field, values in (("tile", tiles), ("batch_depth", batches), ("digit_bits", digits),
                           ("fwd_pixels", fwd_pixels), ("bwd_pixels", bwd_pixels)):
@@ -90,7 +100,7 @@ def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings()
             if cand == best:
                 continue
             try:
-                ms = time_step(model, cams, cand, steps)
+                ms = _measure(model, cams, cand, steps)
             except B.SgsError:  # a combination the library rejects (e.g. 4 rows of 8-high tiles)
                 continue
             trials.append(dict(settings=dataclasses.asdict(cand), ms=ms))

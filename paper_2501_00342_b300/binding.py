@@ -84,9 +84,10 @@ class Plan(C.Structure):
 
 
 class SgsError(RuntimeError):
-    def __init__(self, call, code):
+    def __init__(self, call, code, instances=None):
         super().__init__(f"{call} failed: {status_string(code)} (status {code})")
         self.code = code
+        self.instances = instances  # the instance count an overflowing bin_sort needed
 
 
 _lib = None
@@ -196,9 +197,9 @@ def bin_sort(plan, stream, sync: bool):
         m = C.c_int64(0)
         code = lib().sgs_bin_sort(C.byref(plan), C.byref(m), stream)
         if code == SGS_ERR_CAPACITY:
-            err = SgsError("sgs_bin_sort", code)
-            err.instances = m.value
-            raise err
+            # raised without a local name: a local holding the exception would form a cycle
+            # with its traceback and keep the caller's workspace alive until a collection
+            raise SgsError("sgs_bin_sort", code, instances=m.value)
         check("sgs_bin_sort", code)
         return m.value
     check("sgs_bin_sort", lib().sgs_bin_sort(C.byref(plan), None, stream))

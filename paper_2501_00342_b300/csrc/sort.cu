@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t e = wbase + k * 32 + lane;
         const uint32_t d = e < count ? (uint32_t)(key[k] >> shift) & dmask : RADIX;
-        const uint32_t peers = digit_peers<RB + 1>(d);
+        // alternate the two ways of finding the lanes with the same digit so that the
+        // ballots (ALU pipe) and match-any (shared pipe) run side by side
+        const uint32_t peers = (k & 1) ? digit_peers<RB + 1>(d) : __match_any_sync(kFullMask, d);
         const int leader = 31 - __clz(peers);
         uint32_t prior = 0;
         if (lane == leader) {

@@ -216,6 +216,25 @@ def test_capacity_overflow_is_reported_not_written():
     _check_image(sc, cams, out, rast=rast)
 
 
+def test_overflow_regrow_releases_workspace_without_gc():
+    """The capacity-overflow path must not leave a reference cycle that keeps a (possibly
+    tens of GB) workspace alive until the next garbage collection."""
+    import gc
+    sc, cams = I.workload(0)
+    model = GaussianModel.from_scene(sc)
+    torch.cuda.synchronize()
+    gc.collect()
+    gc.disable()
+    try:
+        base = torch.cuda.memory_allocated()
+        r = Rasterizer(model, cams, RenderSettings(), capacity=1000)
+        img = r.forward(model, sync=True)  # overflows, grows the workspace, renders
+        del r, img
+        assert torch.cuda.memory_allocated() == base
+    finally:
+        gc.enable()
+
+
 def test_graph_capture_replay_matches_eager():
     sc, cams = I.workload(0)
     model = GaussianModel.from_scene(sc)
