@@ -89,9 +89,44 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// The staged batch entries [0, cnt) whose support box reaches the warp's block (and, in
+// The staged batch entries [0, cnt) whose support reaches the warp's block (and, in
 // the backward, lie below `limit`), in increasing order, written to list[0, count); the
 // lanes test 32 entries at a time.  Warp-collective; returns count.
+// Minimum of Q(d) = A dx^2 + 2B dx dy + C dy^2 over the rectangle [x0, x1] x [y0, y1] of
+// offsets from the Gaussian's centre (A, C > 0): 0 if the centre is inside, else the least
+// of the four edge minima (Q is convex, so the rectangle minimum lies on its boundary; on
+// an edge Q is a quadratic in one offset, minimised at the clamped vertex).
+__device__ __forceinline__ float rect_min_q(float A, float B, float C, float x0, float x1, float y0, float y1) {
+    if (x0 <= 0.0f && 0.0f <= x1 && y0 <= 0.0f && 0.0f <= y1) return 0.0f;
+    const float iA = 1.0f / A, iC = 1.0f / C;
+    float q = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float xe = e ? x1 : x0;  // vertical edge x = xe
+        const float t = fminf(fmaxf(-B * xe * iC, y0), y1);
+        q = fminf(q, fmaf(A * xe, xe, fmaf(2.0f * B * xe, t, C * t * t)));
+        const float ye = e ? y1 : y0;  // horizontal edge y = ye
+        const float u = fminf(fmaxf(-B * ye * iA, x0), x1);
+        q = fminf(q, fmaf(A * u, u, fmaf(2.0f * B * u, ye, C * ye * ye)));
+    }
+    return q;
+}
+
+// True when some pixel centre of the block may be in the Gaussian's support: the padded
+// 3-sigma box reaches the block, and the least Q over the block's pixel-centre rectangle
+// (padded by 1/64 pixel) is at most 9.01.  A supported pixel centre has Q <= 9 up to
+// single-precision rounding, which the 0.1 % slack and the pad cover, so a Gaussian that
+// fails the test has no supported pixel in the block.  Records store (qa, qb, qc) =
+// (-A/2, -B, -C/2).
+__device__ __forceinline__ bool reaches_block(const WarpBlock& wb, const float4& a, const float4& b) {
+    if (misses_block(wb, a.x, a.y, b.z, b.w)) return false;
+    const float A = -2.0f * a.z, B = -a.w, C = -2.0f * b.x;
+    if (!(A > 0.0f && C > 0.0f)) return true;  // degenerate conic: keep it
+    const float q = rect_min_q(A, B, C, wb.fx0 - kSpanPad - a.x, wb.fx1 + kSpanPad - a.x, wb.fy0 - kSpanPad - a.y,
+                               wb.fy1 + kSpanPad - a.y);
+    return !(q > kSpanQ);  // NaN keeps the Gaussian
+}
+
 __device__ __forceinline__ int warp_hits(const WarpBlock& wb, const float4* s0, const float4* s1, int cnt,
                                          int limit, uint16_t* list) {
     const uint32_t lt = lanemask_lt();
@@ -101,7 +136,7 @@ __device__ __forceinline__ int warp_hits(const WarpBlock& wb, const float4* s0, 
         bool hit = false;
         if (j < cnt && j < limit) {
             const float4 a = s0[j], b = s1[j];
-            hit = !misses_block(wb, a.x, a.y, b.z, b.w);
+            hit = reaches_block(wb, a, b);
         }
         const uint32_t bal = __ballot_sync(kFullMask, hit);
         if (hit) list[count + __popc(bal & lt)] = (uint16_t)j;
