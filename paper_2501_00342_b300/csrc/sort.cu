@@ -101,11 +101,11 @@ __global__ void histogram_scan_kernel(const uint32_t* __restrict__ hist, uint32_
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x) goff[p * RADIX + d] = s[d];
 }
 
-// Items per thread: 15 for 64-bit keys, 22 for 32-bit keys (about the same registers; with
-// 9-bit digits three CTAs fit an SM's shared memory).
+// Items per thread: 15 for 64-bit keys (3 CTAs per SM), 16 for 32-bit keys (4 CTAs per SM:
+// 64 registers, about 52 KB of shared memory with 9-bit digits).
 template <typename KeyT>
 struct SortShape {
-    static constexpr int ITEMS = sizeof(KeyT) == 8 ? 15 : 22;
+    static constexpr int ITEMS = sizeof(KeyT) == 8 ? 15 : 16;
     static constexpr int TILE = kSortThreads * ITEMS;
 };
 
@@ -138,7 +138,7 @@ struct OnesweepSmem {
 };
 
 template <typename KeyT, int RB>
-__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesweep_kernel(
     const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* m_ptr, const uint32_t* __restrict__ goff,
     unsigned long long* lookback, uint32_t* counter, int shift, int width, int pass, DeviceStatus* st) {
