@@ -269,6 +269,11 @@ def run_gpu(args):
     # algorithmic work of each kernel
     tiles = rast.region("TILES", torch.int32)[:n * nv]
     visible = int((tiles != 0).sum().item())
+    # one more forward with the per-pixel pair counters on (the timed kernels skip them)
+    rast.plan.settings.count_pairs = 1
+    rast.forward(model, out_rgb=img, sync=False)
+    rast.plan.settings.count_pairs = 0
+    torch.cuda.synchronize()
     counts = rast.region("PIX_COUNT", torch.int32)[:2 * rast.num_pixels].view(-1, 2).to(torch.int64)
     e_eval, e_contrib = int(counts[:, 0].sum().item()), int(counts[:, 1].sum().item())
     p_bytes = 4 * scene.floats_per_gaussian()

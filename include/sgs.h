@@ -129,6 +129,10 @@ typedef struct {
     int32_t bwd_pixels;     /* pixels per thread of the backward blend: 0 (auto: 2), 1, 2 or 4
                                (4 needs tile_h a multiple of 16).  Results do not depend on
                                either (the backward's float atomics may add in another order). */
+    int32_t count_pairs;    /* 1: sgs_render also writes, per pixel, the number of Gaussians
+                               whose support holds it before it finished and the number it
+                               blended (region SGS_REGION_PIX_COUNT); 0: not (faster).  May be
+                               changed in the plan between calls. */
 } sgs_settings;
 
 /* Host-side plan: sizes and workspace offsets.  Filled by sgs_workspace_size(); the

@@ -85,6 +85,7 @@ ViewTable view_table(const sgs_plan* p) {
     vt.inv_tile_h = 1.0f / (float)vt.tile_h;
     vt.fwd_ppt = p->settings.fwd_pixels ? p->settings.fwd_pixels : 2;
     vt.bwd_ppt = p->settings.bwd_pixels ? p->settings.bwd_pixels : 2;
+    vt.count_pairs = p->settings.count_pairs ? 1 : 0;
     vt.num_tiles = p->num_tiles;
     for (int v = 0; v < p->B; ++v) {
         const sgs_camera& c = p->cams[v];
@@ -170,6 +171,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     if (settings->fwd_pixels < 0 || settings->fwd_pixels > 2) return SGS_ERR_INVALID;
     if (settings->bwd_pixels < 0 || settings->bwd_pixels == 3 || settings->bwd_pixels > 4) return SGS_ERR_INVALID;
     if (settings->bwd_pixels == 4 && settings->tile_h % 16 != 0) return SGS_ERR_INVALID;
+    if (settings->count_pairs != 0 && settings->count_pairs != 1) return SGS_ERR_INVALID;
     if (settings->digit_bits < kMinDigitBits || settings->digit_bits > kMaxDigitBits) return SGS_ERR_INVALID;
     if (settings->memory_mode != 0) return SGS_ERR_INVALID;
     if (instance_capacity < 0 || instance_capacity > 0xffffffffll) return SGS_ERR_INVALID;

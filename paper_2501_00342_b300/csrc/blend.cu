@@ -163,7 +163,7 @@ struct FwdPixel {
 
 // PPT pixels per thread: pixel q of thread t is (t % tile_w, t / tile_w + q * tile_h / PPT)
 // inside the tile, so one shared-memory read of a Gaussian serves PPT pixels.
-template <int PPT>
+template <int PPT, bool COUNT>
 __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const uint2* __restrict__ ranges,
                                                      const uint32_t* __restrict__ vals, uint32_t R,
                                                      const float4* __restrict__ rec0,
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
                 if (!p.done) {
                     const float power = support_power(a.z, a.w, b.x, a.x - p.pxc, a.y - p.pyc);
                     if (power >= kSupportPower) {  // also skips a NaN exponent
-                        ++p.evaluated;
+                        if (COUNT) ++p.evaluated;
                         const float alpha = fminf(kAlphaMax, b.y * __expf(power));
                         if (alpha >= kAlphaMin) {
                             const float Tn = p.T * (1.0f - alpha);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
                                 p.C2 += c.z * w;
                                 p.T = Tn;
                                 p.last = (uint32_t)(base + k + 1);
-                                ++p.contributed;
+                                if (COUNT) ++p.contributed;
                             }
                         }
                     }
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         if (out_T) out_T[cam.pixel_base + pi] = p.T;
         pix_T[cam.pixel_base + pi] = p.T;
         pix_last[cam.pixel_base + pi] = p.last;
-        pix_count[cam.pixel_base + pi] = make_uint2(p.evaluated, p.contributed);
+        if (COUNT) pix_count[cam.pixel_base + pi] = make_uint2(p.evaluated, p.contributed);
     }
 }
 
@@ -463,17 +463,18 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 
 }  // namespace
 
-template <int PPT>
+template <int PPT, bool COUNT>
 static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uint32_t* vals, int64_t R,
                              const RecordPtrs& p, int batch, float bg0, float bg1, float bg2, float* out_rgb,
                              float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
                              const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
     const size_t smem = (size_t)batch * (3 * sizeof(float4) + (threads / 32) * sizeof(uint16_t));
-    cudaError_t e = cudaFuncSetAttribute(blend_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(blend_kernel<PPT, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // with no records every range is empty and no id is read; the kernel still writes bg
-    blend_kernel<PPT><<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1,
+    blend_kernel<PPT, COUNT><<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1,
                                                                     p.rec2, batch, bg0, bg1, bg2, out_rgb, out_T,
                                                                     pix_T, pix_last, pix_count, st);
     return cudaGetLastError();
@@ -500,11 +501,16 @@ cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_
                          float* out_rgb, float* out_T, float* pix_T, uint32_t* pix_last,
                          uint2* pix_count, const DeviceStatus* st, cudaStream_t s) {
     if (vt.num_tiles == 0) return cudaSuccess;
-    if (vt.fwd_ppt == 2)
-        return blend_ppt<2>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last,
-                            pix_count, st, s);
-    return blend_ppt<1>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, pix_count,
-                        st, s);
+#define SGS_BLEND(PPT, COUNT)                                                                                 \
+    return blend_ppt<PPT, COUNT>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, \
+                                 pix_count, st, s)
+    if (vt.fwd_ppt == 2) {
+        if (vt.count_pairs) SGS_BLEND(2, true);
+        SGS_BLEND(2, false);
+    }
+    if (vt.count_pairs) SGS_BLEND(1, true);
+    SGS_BLEND(1, false);
+#undef SGS_BLEND
 }
 
 cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, const uint32_t* vals,

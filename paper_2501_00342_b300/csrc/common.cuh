@@ -31,6 +31,7 @@ struct ViewTable {
     int32_t tile_w, tile_h;    // powers of two
     float inv_tile_w, inv_tile_h;  // exact reciprocals: x * inv == x / tile, bit for bit
     int32_t fwd_ppt, bwd_ppt;      // pixels per thread of the blend kernels
+    int32_t count_pairs;           // the forward blend writes per-pixel pair counts
     int64_t num_tiles;
     View v[SGS_MAX_VIEWS];
 };

@@ -42,10 +42,10 @@ def _g(n=100, L=1, K=3, mode=0):
     return g
 
 
-def _s(tw=16, th=16, batch=256, digit=8, fwd=0, bwd=0):
+def _s(tw=16, th=16, batch=256, digit=8, fwd=0, bwd=0, count=0):
     s = B.Settings()
     s.tile_w, s.tile_h, s.batch_depth, s.digit_bits, s.memory_mode = tw, th, batch, digit, 0
-    s.fwd_pixels, s.bwd_pixels = fwd, bwd
+    s.fwd_pixels, s.bwd_pixels, s.count_pairs = fwd, bwd, count
     return s
 
 
@@ -71,7 +71,7 @@ def test_plan_sizes_and_key_bits():
 @pytest.mark.parametrize("bad", [
     dict(tw=16, th=12), dict(tw=0, th=16), dict(tw=4, th=32), dict(tw=2, th=32), dict(tw=64, th=4),
     dict(tw=32, th=32), dict(batch=16), dict(batch=4096), dict(digit=3), dict(digit=11),
-    dict(fwd=3), dict(fwd=-1), dict(bwd=3), dict(bwd=8), dict(tw=32, th=8, bwd=4),
+    dict(fwd=3), dict(fwd=-1), dict(bwd=3), dict(bwd=8), dict(tw=32, th=8, bwd=4), dict(count=2),
 ])
 def test_invalid_settings_rejected(bad):
     cams = [I.look_at((0, 0, 4), (0, 0, 0), 64, 64, 60)]
