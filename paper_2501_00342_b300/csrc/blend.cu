@@ -46,41 +46,16 @@ __device__ __forceinline__ TileCoord tile_of(const ViewTable& vt, uint32_t g) {
 // q < PPT.  Compact warp footprints let a whole warp skip a Gaussian whose ellipse misses
 // its block.  Needs tile_w % 8 == 0 and tile_h % (4 PPT) == 0.
 struct WarpBlock {
-    int x0, y0;                // block origin inside the tile
-    float fx0, fx1, fy0, fy1;  // first and last pixel-centre coordinates of the block (image)
+    int x0, y0;  // block origin inside the tile
 };
 
 template <int PPT>
-__device__ __forceinline__ WarpBlock warp_block(const ViewTable& vt, const TileCoord& tc) {
+__device__ __forceinline__ WarpBlock warp_block(const ViewTable& vt) {
     const int w = threadIdx.x >> 5, per_row = vt.tile_w >> 3;
     WarpBlock b;
     b.x0 = (w % per_row) * 8;
     b.y0 = (w / per_row) * 4 * PPT;
-    b.fx0 = (float)(tc.tx * vt.tile_w + b.x0) + 0.5f;
-    b.fx1 = b.fx0 + 7.0f;
-    b.fy0 = (float)(tc.ty * vt.tile_h + b.y0) + 0.5f;
-    b.fy1 = b.fy0 + (float)(4 * PPT - 1);
     return b;
-}
-
-// Half-extents of the box around the ellipse Q(d) <= 9.01 (Q = A dx^2 + 2B dx dy + C dy^2,
-// the conic), padded by 1/64 pixel: ex = sqrt(9.01 C / det), ey = sqrt(9.01 A / det).  A
-// pixel centre whose support exponent passes the -4.5 test (Q <= 9 up to single-precision
-// rounding, which the 0.1 % slack and the pad cover) lies inside the box, so a warp whose
-// block misses the box would skip the Gaussian at every pixel: skipping it whole changes no
-// result.  A degenerate conic gives an infinite box (never skipped).  Records store
-// (qa, qb, qc) = (-A/2, -B, -C/2).
-__device__ __forceinline__ float2 support_box(float qa, float qb, float qc) {
-    const float A = -2.0f * qa, B = -qb, C = -2.0f * qc;
-    const float det = A * C - B * B;
-    if (!(det > 0.0f)) return make_float2(INFINITY, INFINITY);
-    const float k = kSpanQ / det;
-    return make_float2(sqrtf(k * C) + kSpanPad, sqrtf(k * A) + kSpanPad);
-}
-
-// True when the box of the Gaussian centred at (gx, gy) misses the block (warp-uniform).
-__device__ __forceinline__ bool misses_block(const WarpBlock& wb, float gx, float gy, float ex, float ey) {
-    return gx + ex < wb.fx0 || gx - ex > wb.fx1 || gy + ey < wb.fy0 || gy - ey > wb.fy1;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -89,55 +64,65 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// The staged batch entries [0, cnt) whose support reaches the warp's block (and, in
-// the backward, lie below `limit`), in increasing order, written to list[0, count); the
-// lanes test 32 entries at a time.  Warp-collective; returns count.
-// Minimum of Q(d) = A dx^2 + 2B dx dy + C dy^2 over the rectangle [x0, x1] x [y0, y1] of
-// offsets from the Gaussian's centre (A, C > 0): 0 if the centre is inside, else the least
-// of the four edge minima (Q is convex, so the rectangle minimum lies on its boundary; on
-// an edge Q is a quadratic in one offset, minimised at the clamped vertex).
-__device__ __forceinline__ float rect_min_q(float A, float B, float C, float x0, float x1, float y0, float y1) {
-    if (x0 <= 0.0f && 0.0f <= x1 && y0 <= 0.0f && 0.0f <= y1) return 0.0f;
-    const float iA = 1.0f / A, iC = 1.0f / C;
-    float q = INFINITY;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float xe = e ? x1 : x0;  // vertical edge x = xe
-        const float t = fminf(fmaxf(-B * xe * iC, y0), y1);
-        q = fminf(q, fmaf(A * xe, xe, fmaf(2.0f * B * xe, t, C * t * t)));
-        const float ye = e ? y1 : y0;  // horizontal edge y = ye
-        const float u = fminf(fmaxf(-B * ye * iA, x0), x1);
-        q = fminf(q, fmaf(A * u, u, fmaf(2.0f * B * u, ye, C * ye * ye)));
-    }
-    return q;
-}
-
-// True when some pixel centre of the block may be in the Gaussian's support: the padded
-// 3-sigma box reaches the block, and the least Q over the block's pixel-centre rectangle
-// (padded by 1/64 pixel) is at most 9.01.  A supported pixel centre has Q <= 9 up to
-// single-precision rounding, which the 0.1 % slack and the pad cover, so a Gaussian that
-// fails the test has no supported pixel in the block.  Records store (qa, qb, qc) =
-// (-A/2, -B, -C/2).
-__device__ __forceinline__ bool reaches_block(const WarpBlock& wb, const float4& a, const float4& b) {
-    if (misses_block(wb, a.x, a.y, b.z, b.w)) return false;
-    const float A = -2.0f * a.z, B = -a.w, C = -2.0f * b.x;
-    if (!(A > 0.0f && C > 0.0f)) return true;  // degenerate conic: keep it
-    const float q = rect_min_q(A, B, C, wb.fx0 - kSpanPad - a.x, wb.fx1 + kSpanPad - a.x, wb.fy0 - kSpanPad - a.y,
-                               wb.fy1 + kSpanPad - a.y);
-    return !(q > kSpanQ);  // NaN keeps the Gaussian
-}
-
-__device__ __forceinline__ int warp_hits(const WarpBlock& wb, const float4* s0, const float4* s1, int cnt,
-                                         int limit, uint16_t* list) {
-    const uint32_t lt = lanemask_lt();
-    int count = 0;
-    for (int j0 = 0; j0 < cnt; j0 += 32) {
-        const int j = j0 + (int)(threadIdx.x & 31);
-        bool hit = false;
-        if (j < cnt && j < limit) {
-            const float4 a = s0[j], b = s1[j];
-            hit = reaches_block(wb, a, b);
+// The warp blocks of the CTA's tile that the Gaussian's support may reach: bit w for warp w.
+// With Q(d) = A dx^2 + 2B dx dy + C dy^2 (the conic; records store (qa, qb, qc) =
+// (-A/2, -B, -C/2)), the ellipse Q <= 9.01 is cut into the tile's bands of block rows.  Over
+// a band's pixel-centre rows (padded by 1/64 pixel) its x-extent is exact: the rightmost
+// x is the ellipse's rightmost point ex when that point's row -B ex / C falls in the band,
+// else the larger chord end (-B y + sqrt(9.01 A - det y^2)) / A at the band's two edge rows
+// (the chord end is concave in y), and the leftmost mirrors it.  Each block column whose
+// padded pixel-centre columns meet the extent gets its bit.  A supported pixel centre has
+// Q <= 9 up to single-precision rounding, which the 0.1 % slack and the pad cover (inside
+// the Q <= 9 rows the chord's own rounding is far below that slack), so a warp without its
+// bit has no supported pixel.  A degenerate conic or a non-finite centre sets every bit.
+template <int PPT>
+__device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCoord& tc, float px, float py,
+                                               float qa, float qb, float qc) {
+    constexpr int BH = 4 * PPT;  // pixel rows per block
+    const float A = -2.0f * qa, B = -qb, C = -2.0f * qc;
+    const float det = A * C - B * B;
+    // Centre relative to the tile's first pixel centre.
+    const float gx = px - ((float)(tc.tx * vt.tile_w) + 0.5f);
+    const float gy = py - ((float)(tc.ty * vt.tile_h) + 0.5f);
+    if (!(det > 0.0f && A > 0.0f && C > 0.0f && fabsf(gx) < 1e30f && fabsf(gy) < 1e30f)) return ~0u;
+    const int nbx = vt.tile_w >> 3, nby = vt.tile_h / BH;
+    const float k = kSpanQ / det;
+    const float ex = sqrtf(k * C), ey = sqrtf(k * A);
+    const float dyr = -B * ex / C;  // row offset of the rightmost point
+    const float iA = 1.0f / A, Ak = A * kSpanQ;
+    const float b0 = fmaxf(ceilf((gy - ey - kSpanPad - (float)(BH - 1)) * (1.0f / BH)), 0.0f);
+    const float b1 = fminf(floorf((gy + ey + kSpanPad) * (1.0f / BH)), (float)(nby - 1));
+    uint32_t mask = 0;
+    for (int b = (int)b0; b <= (int)b1; ++b) {
+        const float u0 = fmaxf((float)(b * BH) - kSpanPad - gy, -ey);
+        const float u1 = fminf((float)(b * BH + BH - 1) + kSpanPad - gy, ey);
+        if (!(u0 <= u1)) continue;
+        const float s0 = sqrtf(fmaxf(0.0f, Ak - det * u0 * u0));
+        const float s1 = sqrtf(fmaxf(0.0f, Ak - det * u1 * u1));
+        const float xmax = (u0 <= dyr && dyr <= u1) ? ex : fmaxf(s0 - B * u0, s1 - B * u1) * iA;
+        const float xmin = (u0 <= -dyr && -dyr <= u1) ? -ex : fminf(-B * u0 - s0, -B * u1 - s1) * iA;
+        // Block column c holds pixel-centre columns [8c, 8c + 7].
+        const float c0 = fmaxf(ceilf((gx + xmin - kSpanPad - 7.0f) * 0.125f), 0.0f);
+        const float c1 = fminf(floorf((gx + xmax + kSpanPad) * 0.125f), (float)(nbx - 1));
+        if (c0 <= c1) {
+            const int n = (int)c1 - (int)c0 + 1;
+            mask |= ((1u << n) - 1u) << (b * nbx + (int)c0);
         }
+    }
+    return mask;
+}
+
+// The staged batch entries [0, cnt) whose block mask has the warp's bit (and, in the
+// backward, lie below `limit`), in increasing order, written to list[0, count); the lanes
+// test 32 entries at a time.  Warp-collective; returns count.
+__device__ __forceinline__ int warp_hits(const uint32_t* smask, int cnt, int limit, uint16_t* list) {
+    const uint32_t lt = lanemask_lt();
+    const uint32_t bit = 1u << (threadIdx.x >> 5);
+    const int n = min(cnt, limit);
+    int count = 0;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + (int)(threadIdx.x & 31);
+        const bool hit = j < n && (smask[j] & bit) != 0;
         const uint32_t bal = __ballot_sync(kFullMask, hit);
         if (hit) list[count + __popc(bal & lt)] = (uint16_t)j;
         count += __popc(bal);
@@ -180,10 +165,11 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     float4* s0 = sbuf;
     float4* s1 = sbuf + batch;
     float4* s2 = sbuf + 2 * batch;
-    uint16_t* wlist = reinterpret_cast<uint16_t*>(sbuf + 3 * batch) + (threadIdx.x >> 5) * batch;
+    uint32_t* smask = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
+    uint16_t* wlist = reinterpret_cast<uint16_t*>(smask + batch) + (threadIdx.x >> 5) * batch;
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
-    const WarpBlock wb = warp_block<PPT>(vt, tc);
+    const WarpBlock wb = warp_block<PPT>(vt);
     const int lx = wb.x0 + (threadIdx.x & 7), ly = wb.y0 + ((threadIdx.x >> 3) & 3);
     FwdPixel P[PPT];
     bool all_done = true;
@@ -207,13 +193,13 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
             const uint32_t id = min(vals[range.x + base + j], R - 1);  // ids are < R by construction
             const float4 r0 = rec0[id], r1 = rec1[id];
-            const float2 box = support_box(r0.z, r0.w, r1.x);
             s0[j] = r0;
-            s1[j] = make_float4(r1.x, r1.y, box.x, box.y);  // depth and radius are not needed here
+            s1[j] = r1;
             s2[j] = rec2[id];
+            smask[j] = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
         }
         __syncthreads();
-        const int hits = warp_hits(wb, s0, s1, cnt, cnt, wlist);
+        const int hits = warp_hits(smask, cnt, cnt, wlist);
         for (int i = 0; !all_done && i < hits; ++i) {
             const int k = wlist[i];
             const float4 a = s0[k];
@@ -320,11 +306,12 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     float4* s1 = sbuf + batch;
     float4* s2 = sbuf + 2 * batch;
     uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
-    uint16_t* wlist = reinterpret_cast<uint16_t*>(sid + batch) + (threadIdx.x >> 5) * batch;
+    uint32_t* smask = sid + batch;
+    uint16_t* wlist = reinterpret_cast<uint16_t*>(smask + batch) + (threadIdx.x >> 5) * batch;
     __shared__ uint32_t s_max_last;
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
-    const WarpBlock wb = warp_block<PPT>(vt, tc);
+    const WarpBlock wb = warp_block<PPT>(vt);
     const int lx = wb.x0 + (threadIdx.x & 7), ly = wb.y0 + ((threadIdx.x >> 3) & 3);
     const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
     if (threadIdx.x == 0) s_max_last = 0;
@@ -367,14 +354,14 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
         for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) {
             const uint32_t id = min(vals[range.x + lo + j], R32 - 1);  // ids are < R by construction
             const float4 r0 = rec0[id], r1 = rec1[id];
-            const float2 box = support_box(r0.z, r0.w, r1.x);
             sid[j] = id;
             s0[j] = r0;
-            s1[j] = make_float4(r1.x, r1.y, box.x, box.y);
+            s1[j] = r1;
             s2[j] = rec2[id];
+            smask[j] = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
         }
         __syncthreads();
-        const int hits = warp_hits(wb, s0, s1, hi - lo, warp_last - lo, wlist);
+        const int hits = warp_hits(smask, hi - lo, warp_last - lo, wlist);
         for (int i = hits - 1; i >= 0; --i) {
             const int j = wlist[i];
             const int k = lo + j;
@@ -469,7 +456,7 @@ static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uin
                              float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
                              const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
-    const size_t smem = (size_t)batch * (3 * sizeof(float4) + (threads / 32) * sizeof(uint16_t));
+    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t) + (threads / 32) * sizeof(uint16_t));
     cudaError_t e =
         cudaFuncSetAttribute(blend_kernel<PPT, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -486,7 +473,7 @@ static cudaError_t blend_backward_ppt(const ViewTable& vt, const uint2* ranges, 
                                       const float* pix_T, const uint32_t* pix_last, const float* dL_drgb,
                                       float4* grad2d, int64_t R, const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
-    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t) + (threads / 32) * sizeof(uint16_t));
+    const size_t smem = (size_t)batch * (3 * sizeof(float4) + 2 * sizeof(uint32_t) + (threads / 32) * sizeof(uint16_t));
     cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
