@@ -651,8 +651,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--tile", type=int, nargs=2, default=(16, 32))
-    ap.add_argument("--batch-depth", type=int, default=512)
+    ap.add_argument("--tile", type=int, nargs=2, default=(32, 32))
+    ap.add_argument("--batch-depth", type=int, default=1024)
     ap.add_argument("--digit-bits", type=int, default=9)
     ap.add_argument("--fwd-pixels", type=int, default=0, help="pixels per thread, forward blend (0: library's)")
     ap.add_argument("--bwd-pixels", type=int, default=0, help="pixels per thread, backward blend (0: library's)")

@@ -118,7 +118,8 @@ typedef struct {
 } sgs_grads;
 
 typedef struct {
-    int32_t tile_w, tile_h; /* screen tile, pixels; powers of two >= 8, 64..512 pixels */
+    int32_t tile_w, tile_h; /* screen tile, pixels; powers of two 8..64, 64..1024 pixels;
+                               over 512 pixels needs fwd_pixels and bwd_pixels >= 2 (or 0) */
     int32_t batch_depth;    /* Gaussians staged in shared memory per blend batch: 32..1024 */
     int32_t digit_bits;     /* widest radix-sort digit, 4..10: a sort of b bits takes
                                ceil(b / digit_bits) passes of equal, narrowest width */

@@ -21,7 +21,7 @@ import torch
 from . import binding as B
 from .render import GaussianModel, Rasterizer, RenderSettings
 
-TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 16), (16, 32), (32, 8), (16, 8), (64, 8), (8, 8))
+TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 16), (16, 32), (32, 32), (64, 16), (32, 8), (16, 8), (64, 8), (8, 8))
 BATCHES: Tuple[int, ...] = (128, 256, 512, 1024)
 DIGITS: Tuple[int, ...] = (8, 9, 10)
 FWD_PIXELS: Tuple[int, ...] = (1, 2)

@@ -30,13 +30,17 @@ int ceil_log2(int64_t x) {
 }
 
 // Tile sides are powers of two of at least 8 (the blend's warps own 8-wide blocks of 4 or
-// 8 rows), with 64-512 pixels per tile (one CTA of at most 512 threads).
-bool valid_tile(int32_t w, int32_t h) {
+// 8 rows), with 64-1024 pixels per tile; each blend pass runs one CTA of at most 512
+// threads per tile, so a tile of more than 512 pixels needs 2 or more pixels per thread in
+// both passes (fwd, bwd: the resolved pixels per thread).
+bool valid_tile(int32_t w, int32_t h, int32_t fwd, int32_t bwd) {
     auto pow2 = [](int32_t x) { return x >= 8 && x <= 64 && (x & (x - 1)) == 0; };
     if (!pow2(w) || !pow2(h)) return false;
     const int32_t t = w * h;
-    return t >= 64 && t <= 512;
+    return t >= 64 && t <= 1024 && t / fwd <= 512 && t / bwd <= 512;
 }
+
+int32_t resolved_pixels(int32_t setting) { return setting ? setting : 2; }
 
 sgs_status check_gaussians(const sgs_gaussians* g) {
     if (!g || g->n < 0 || g->stride < g->n || (g->stride & 3) != 0) return SGS_ERR_INVALID;
@@ -83,8 +87,8 @@ ViewTable view_table(const sgs_plan* p) {
     vt.tile_h = p->settings.tile_h;
     vt.inv_tile_w = 1.0f / (float)vt.tile_w;  // exact: powers of two
     vt.inv_tile_h = 1.0f / (float)vt.tile_h;
-    vt.fwd_ppt = p->settings.fwd_pixels ? p->settings.fwd_pixels : 2;
-    vt.bwd_ppt = p->settings.bwd_pixels ? p->settings.bwd_pixels : 2;
+    vt.fwd_ppt = resolved_pixels(p->settings.fwd_pixels);
+    vt.bwd_ppt = resolved_pixels(p->settings.bwd_pixels);
     vt.count_pairs = p->settings.count_pairs ? 1 : 0;
     vt.num_tiles = p->num_tiles;
     for (int v = 0; v < p->B; ++v) {
@@ -166,10 +170,12 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     if (!plan || !bytes || !cams || !settings) return SGS_ERR_INVALID;
     if (check_gaussians(g) != SGS_OK) return SGS_ERR_INVALID;
     if (B < 1 || B > SGS_MAX_VIEWS) return SGS_ERR_INVALID;
-    if (!valid_tile(settings->tile_w, settings->tile_h)) return SGS_ERR_INVALID;
     if (settings->batch_depth < 32 || settings->batch_depth > 1024) return SGS_ERR_INVALID;
     if (settings->fwd_pixels < 0 || settings->fwd_pixels > 2) return SGS_ERR_INVALID;
     if (settings->bwd_pixels < 0 || settings->bwd_pixels == 3 || settings->bwd_pixels > 4) return SGS_ERR_INVALID;
+    if (!valid_tile(settings->tile_w, settings->tile_h, resolved_pixels(settings->fwd_pixels),
+                    resolved_pixels(settings->bwd_pixels)))
+        return SGS_ERR_INVALID;
     if (settings->bwd_pixels == 4 && settings->tile_h % 16 != 0) return SGS_ERR_INVALID;
     if (settings->count_pairs != 0 && settings->count_pairs != 1) return SGS_ERR_INVALID;
     if (settings->digit_bits < kMinDigitBits || settings->digit_bits > kMaxDigitBits) return SGS_ERR_INVALID;

@@ -58,12 +58,6 @@ __device__ __forceinline__ WarpBlock warp_block(const ViewTable& vt) {
     return b;
 }
 
-__device__ __forceinline__ uint32_t lanemask_lt() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
 // The warp blocks of the CTA's tile that the Gaussian's support may reach: bit w for warp w.
 // With Q(d) = A dx^2 + 2B dx dy + C dy^2 (the conic; records store (qa, qb, qc) =
 // (-A/2, -B, -C/2)), the ellipse Q <= 9.01 is cut into the tile's bands of block rows.  Over
@@ -112,23 +106,35 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
     return mask;
 }
 
-// The staged batch entries [0, cnt) whose block mask has the warp's bit (and, in the
-// backward, lie below `limit`), in increasing order, written to list[0, count); the lanes
-// test 32 entries at a time.  Warp-collective; returns count.
-__device__ __forceinline__ int warp_hits(const uint32_t* smask, int cnt, int limit, uint16_t* list) {
-    const uint32_t lt = lanemask_lt();
-    const uint32_t bit = 1u << (threadIdx.x >> 5);
-    const int n = min(cnt, limit);
-    int count = 0;
-    for (int j0 = 0; j0 < n; j0 += 32) {
-        const int j = j0 + (int)(threadIdx.x & 31);
-        const bool hit = j < n && (smask[j] & bit) != 0;
-        const uint32_t bal = __ballot_sync(kFullMask, hit);
-        if (hit) list[count + __popc(bal & lt)] = (uint16_t)j;
-        count += __popc(bal);
+// Stages one group of 32 batch entries (this warp's group g: entries 32 g + lane < cnt,
+// from the tile's sorted list at `first`) in shared memory, and writes for every warp w of
+// the CTA the 32-bit word of the group's entries whose support may reach w's block
+// (bits[w * words + g]; bit b = entry 32 g + b): a transpose of the entries' block masks by
+// one ballot per warp.  Returns the record id of the lane's entry.  Warp-collective.
+template <int PPT>
+__device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileCoord& tc, int g, int cnt,
+                                                const uint32_t* __restrict__ first, uint32_t R,
+                                                const float4* __restrict__ rec0, const float4* __restrict__ rec1,
+                                                const float4* __restrict__ rec2, float4* s0, float4* s1,
+                                                float4* s2, uint32_t* bits, int words) {
+    const int lane = threadIdx.x & 31, j = g * 32 + lane;
+    uint32_t mask = 0, id = 0;
+    if (j < cnt) {
+        id = min(first[j], R - 1);  // ids are < R by construction
+        const float4 r0 = rec0[id], r1 = rec1[id];
+        s0[j] = r0;
+        s1[j] = r1;
+        s2[j] = rec2[id];
+        mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
     }
-    __syncwarp();
-    return count;
+    const int nw = (int)(blockDim.x >> 5);
+    uint32_t mine = 0;
+    for (int w = 0; w < nw; ++w) {
+        const uint32_t b = __ballot_sync(kFullMask, (mask >> w) & 1u);
+        if (lane == w) mine = b;
+    }
+    if (lane < nw) bits[lane * words + g] = mine;
+    return id;
 }
 
 // Tile range clipped to the instances actually written (all of them unless overflowed).
@@ -165,8 +171,9 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     float4* s0 = sbuf;
     float4* s1 = sbuf + batch;
     float4* s2 = sbuf + 2 * batch;
-    uint32_t* smask = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
-    uint16_t* wlist = reinterpret_cast<uint16_t*>(smask + batch) + (threadIdx.x >> 5) * batch;
+    const int words = (batch + 31) >> 5;
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
+    const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<PPT>(vt);
@@ -189,48 +196,44 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     const int n = (int)(range.y - range.x);
     for (int base = 0; base < n; base += batch) {
         if (__syncthreads_count(!all_done) == 0) break;
-        const int cnt = min(batch, n - base);
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            const uint32_t id = min(vals[range.x + base + j], R - 1);  // ids are < R by construction
-            const float4 r0 = rec0[id], r1 = rec1[id];
-            s0[j] = r0;
-            s1[j] = r1;
-            s2[j] = rec2[id];
-            smask[j] = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
-        }
+        const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
+        for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
+            stage_group<PPT>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, s0, s1, s2, bits, words);
         __syncthreads();
-        const int hits = warp_hits(smask, cnt, cnt, wlist);
-        for (int i = 0; !all_done && i < hits; ++i) {
-            const int k = wlist[i];
-            const float4 a = s0[k];
-            const float4 b = s1[k];
-            all_done = true;
+        // this warp's entries in increasing order: the set bits of its words
+        for (int g = 0; g < groups && !all_done; ++g) {
+            for (uint32_t word = my_bits[g]; word != 0 && !all_done; word &= word - 1) {
+                const int k = g * 32 + __ffs(word) - 1;
+                const float4 a = s0[k];
+                const float4 b = s1[k];
+                all_done = true;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                FwdPixel& p = P[q];
-                if (!p.done) {
-                    const float power = support_power(a.z, a.w, b.x, a.x - p.pxc, a.y - p.pyc);
-                    if (power >= kSupportPower) {  // also skips a NaN exponent
-                        if (COUNT) ++p.evaluated;
-                        const float alpha = fminf(kAlphaMax, b.y * __expf(power));
-                        if (alpha >= kAlphaMin) {
-                            const float Tn = p.T * (1.0f - alpha);
-                            if (Tn < kTransmittanceMin) {
-                                p.done = true;
-                            } else {
-                                const float4 c = s2[k];
-                                const float w = alpha * p.T;
-                                p.C0 += c.x * w;
-                                p.C1 += c.y * w;
-                                p.C2 += c.z * w;
-                                p.T = Tn;
-                                p.last = (uint32_t)(base + k + 1);
-                                if (COUNT) ++p.contributed;
+                for (int q = 0; q < PPT; ++q) {
+                    FwdPixel& p = P[q];
+                    if (!p.done) {
+                        const float power = support_power(a.z, a.w, b.x, a.x - p.pxc, a.y - p.pyc);
+                        if (power >= kSupportPower) {  // also skips a NaN exponent
+                            if (COUNT) ++p.evaluated;
+                            const float alpha = fminf(kAlphaMax, b.y * __expf(power));
+                            if (alpha >= kAlphaMin) {
+                                const float Tn = p.T * (1.0f - alpha);
+                                if (Tn < kTransmittanceMin) {
+                                    p.done = true;
+                                } else {
+                                    const float4 c = s2[k];
+                                    const float w = alpha * p.T;
+                                    p.C0 += c.x * w;
+                                    p.C1 += c.y * w;
+                                    p.C2 += c.z * w;
+                                    p.T = Tn;
+                                    p.last = (uint32_t)(base + k + 1);
+                                    if (COUNT) ++p.contributed;
+                                }
                             }
                         }
                     }
+                    all_done &= p.done;
                 }
-                all_done &= p.done;
             }
         }
     }
@@ -305,9 +308,10 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     float4* s0 = sbuf;
     float4* s1 = sbuf + batch;
     float4* s2 = sbuf + 2 * batch;
+    const int words = (batch + 31) >> 5;
     uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
-    uint32_t* smask = sid + batch;
-    uint16_t* wlist = reinterpret_cast<uint16_t*>(smask + batch) + (threadIdx.x >> 5) * batch;
+    uint32_t* bits = sid + batch;
+    const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
     __shared__ uint32_t s_max_last;
     const TileCoord tc = tile_of(vt, blockIdx.x);
     const View& cam = vt.v[tc.v];
@@ -351,75 +355,78 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     for (int hi = top; hi > 0; hi -= batch) {
         const int lo = max(0, hi - batch);
         __syncthreads();
-        for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) {
-            const uint32_t id = min(vals[range.x + lo + j], R32 - 1);  // ids are < R by construction
-            const float4 r0 = rec0[id], r1 = rec1[id];
-            sid[j] = id;
-            s0[j] = r0;
-            s1[j] = r1;
-            s2[j] = rec2[id];
-            smask[j] = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
+        const int cnt = hi - lo, groups = (cnt + 31) >> 5;
+        for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5)) {
+            const uint32_t id =
+                stage_group<PPT>(vt, tc, g, cnt, vals + range.x + lo, R32, rec0, rec1, rec2, s0, s1, s2, bits, words);
+            if (g * 32 + lane < cnt) sid[g * 32 + lane] = id;
         }
         __syncthreads();
-        const int hits = warp_hits(smask, hi - lo, warp_last - lo, wlist);
-        for (int i = hits - 1; i >= 0; --i) {
-            const int j = wlist[i];
-            const int k = lo + j;
-            const float4 a = s0[j];
-            const float4 b = s1[j];
-            const float4 c = s2[j];
-            float d[9];
+        // this warp's entries below its last contributor, back to front
+        const int lim = min(cnt, warp_last - lo);
+        for (int g = ((lim + 31) >> 5) - 1; g >= 0; --g) {
+            const int rem = lim - g * 32;
+            for (uint32_t word = my_bits[g] & (rem >= 32 ? ~0u : (1u << rem) - 1u); word != 0;) {
+                const int bit = 31 - __clz(word);
+                word ^= 1u << bit;
+                const int j = g * 32 + bit;
+                const int k = lo + j;
+                const float4 a = s0[j];
+                const float4 b = s1[j];
+                const float4 c = s2[j];
+                float d[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) d[i] = 0.0f;
-            bool any = false;
+                for (int i = 0; i < 9; ++i) d[i] = 0.0f;
+                bool any = false;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                BwdPixel& p = P[q];
-                if ((uint32_t)k >= p.last) continue;
-                const float dx = a.x - p.pxc, dy = a.y - p.pyc;
-                const SupportTerms st = support_terms(a.z, a.w, b.x, dx, dy);
-                if (!(st.power >= kSupportPower)) continue;  // also skips a NaN exponent
-                const float G = __expf(st.power);
-                const float oG = b.y * G;
-                const float alpha = fminf(kAlphaMax, oG);
-                if (!(alpha >= kAlphaMin)) continue;
-                any = true;
-                p.T = __fdividef(p.T, 1.0f - alpha);
-                const float w = alpha * p.T;
-                d[6] = fmaf(p.g0, w, d[6]);
-                d[7] = fmaf(p.g1, w, d[7]);
-                d[8] = fmaf(p.g2, w, d[8]);
-                // colour behind minus this Gaussian's colour; acc += alpha (c - acc)
-                const float e0 = c.x - p.acc0, e1 = c.y - p.acc1, e2 = c.z - p.acc2;
-                const float dalpha = p.T * fmaf(p.g0, e0, fmaf(p.g1, e1, p.g2 * e2));
-                p.acc0 = fmaf(alpha, e0, p.acc0);
-                p.acc1 = fmaf(alpha, e1, p.acc1);
-                p.acc2 = fmaf(alpha, e2, p.acc2);
-                if (oG <= kAlphaMax) {
-                    // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2):
-                    // d/d px = u + qa dx, d/d py = qb dx + 2 qc dy, d/d(qa, qb, qc) = (dx^2, dx dy, dy^2)
-                    const float gG = dalpha * G;
-                    const float gpow = gG * b.y;
-                    d[0] = fmaf(gpow, fmaf(a.z, dx, st.u), d[0]);
-                    d[1] = fmaf(gpow, fmaf(a.w, dx, st.t + st.t), d[1]);
-                    const float h = -0.5f * gpow;
-                    d[2] = fmaf(h * dx, dx, d[2]);
-                    d[3] = fmaf(-gpow * dx, dy, d[3]);
-                    d[4] = fmaf(h * dy, dy, d[4]);
-                    d[5] += gG;
+                for (int q = 0; q < PPT; ++q) {
+                    BwdPixel& p = P[q];
+                    if ((uint32_t)k >= p.last) continue;
+                    const float dx = a.x - p.pxc, dy = a.y - p.pyc;
+                    const SupportTerms st = support_terms(a.z, a.w, b.x, dx, dy);
+                    if (!(st.power >= kSupportPower)) continue;  // also skips a NaN exponent
+                    const float G = __expf(st.power);
+                    const float oG = b.y * G;
+                    const float alpha = fminf(kAlphaMax, oG);
+                    if (!(alpha >= kAlphaMin)) continue;
+                    any = true;
+                    p.T = __fdividef(p.T, 1.0f - alpha);
+                    const float w = alpha * p.T;
+                    d[6] = fmaf(p.g0, w, d[6]);
+                    d[7] = fmaf(p.g1, w, d[7]);
+                    d[8] = fmaf(p.g2, w, d[8]);
+                    // colour behind minus this Gaussian's colour; acc += alpha (c - acc)
+                    const float e0 = c.x - p.acc0, e1 = c.y - p.acc1, e2 = c.z - p.acc2;
+                    const float dalpha = p.T * fmaf(p.g0, e0, fmaf(p.g1, e1, p.g2 * e2));
+                    p.acc0 = fmaf(alpha, e0, p.acc0);
+                    p.acc1 = fmaf(alpha, e1, p.acc1);
+                    p.acc2 = fmaf(alpha, e2, p.acc2);
+                    if (oG <= kAlphaMax) {
+                        // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2):
+                        // d/d px = u + qa dx, d/d py = qb dx + 2 qc dy, d/d(qa, qb, qc) = (dx^2, dx dy, dy^2)
+                        const float gG = dalpha * G;
+                        const float gpow = gG * b.y;
+                        d[0] = fmaf(gpow, fmaf(a.z, dx, st.u), d[0]);
+                        d[1] = fmaf(gpow, fmaf(a.w, dx, st.t + st.t), d[1]);
+                        const float h = -0.5f * gpow;
+                        d[2] = fmaf(h * dx, dx, d[2]);
+                        d[3] = fmaf(-gpow * dx, dy, d[3]);
+                        d[4] = fmaf(h * dy, dy, d[4]);
+                        d[5] += gG;
+                    }
                 }
-            }
-            if (__any_sync(kFullMask, any)) {
-                // lanes 0, 4, ..., 28 hold the sums of values 0..7; lanes 0 and 16 gather
-                // values 0-3 and 4-7 and add them with one 16-byte vector reduction each
-                const float s8 = warp_sum8(d, lane);
-                const float s9 = warp_sum(d[8]);
-                const float u1 = __shfl_down_sync(kFullMask, s8, 4);
-                const float u2 = __shfl_down_sync(kFullMask, s8, 8);
-                const float u3 = __shfl_down_sync(kFullMask, s8, 12);
-                const uint32_t id = sid[j];
-                if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
-                if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
+                if (__any_sync(kFullMask, any)) {
+                    // lanes 0, 4, ..., 28 hold the sums of values 0..7; lanes 0 and 16 gather
+                    // values 0-3 and 4-7 and add them with one 16-byte vector reduction each
+                    const float s8 = warp_sum8(d, lane);
+                    const float s9 = warp_sum(d[8]);
+                    const float u1 = __shfl_down_sync(kFullMask, s8, 4);
+                    const float u2 = __shfl_down_sync(kFullMask, s8, 8);
+                    const float u3 = __shfl_down_sync(kFullMask, s8, 12);
+                    const uint32_t id = sid[j];
+                    if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
+                    if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
+                }
             }
         }
     }
@@ -456,7 +463,7 @@ static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uin
                              float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
                              const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
-    const size_t smem = (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t) + (threads / 32) * sizeof(uint16_t));
+    const size_t smem = (size_t)batch * 3 * sizeof(float4) + (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
     cudaError_t e =
         cudaFuncSetAttribute(blend_kernel<PPT, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -473,7 +480,8 @@ static cudaError_t blend_backward_ppt(const ViewTable& vt, const uint2* ranges, 
                                       const float* pix_T, const uint32_t* pix_last, const float* dL_drgb,
                                       float4* grad2d, int64_t R, const DeviceStatus* st, cudaStream_t s) {
     const int threads = vt.tile_w * vt.tile_h / PPT;
-    const size_t smem = (size_t)batch * (3 * sizeof(float4) + 2 * sizeof(uint32_t) + (threads / 32) * sizeof(uint16_t));
+    const size_t smem =
+        (size_t)batch * (3 * sizeof(float4) + sizeof(uint32_t)) + (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
     cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

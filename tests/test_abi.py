@@ -70,7 +70,7 @@ def test_plan_sizes_and_key_bits():
 
 @pytest.mark.parametrize("bad", [
     dict(tw=16, th=12), dict(tw=0, th=16), dict(tw=4, th=32), dict(tw=2, th=32), dict(tw=64, th=4),
-    dict(tw=32, th=32), dict(batch=16), dict(batch=4096), dict(digit=3), dict(digit=11),
+    dict(tw=64, th=32), dict(tw=32, th=32, fwd=1), dict(tw=64, th=16, bwd=1), dict(batch=16), dict(batch=4096), dict(digit=3), dict(digit=11),
     dict(fwd=3), dict(fwd=-1), dict(bwd=3), dict(bwd=8), dict(tw=32, th=8, bwd=4), dict(count=2),
 ])
 def test_invalid_settings_rejected(bad):
@@ -80,6 +80,16 @@ def test_invalid_settings_rejected(bad):
     with pytest.raises(B.SgsError) as e:
         B.workspace_size(_g(), cams, _s(**kw), 1000)
     assert e.value.code == B.SGS_ERR_INVALID
+
+
+@pytest.mark.parametrize("ok", [dict(tw=32, th=32), dict(tw=64, th=16, fwd=2, bwd=4), dict(tw=8, th=64),
+                                dict(tw=32, th=16, fwd=1, bwd=1)])
+def test_tile_shapes_accepted(ok):
+    cams = [I.look_at((0, 0, 4), (0, 0, 0), 64, 64, 60)]
+    kw = dict(tw=16, th=16, batch=256, digit=8)
+    kw.update(ok)
+    plan, _ = B.workspace_size(_g(), cams, _s(**kw), 1000)
+    assert plan.num_tiles == -(-64 // kw["tw"]) * -(-64 // kw["th"])
 
 
 def _adaptive(flag, r0, r1):

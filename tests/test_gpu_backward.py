@@ -86,7 +86,7 @@ def test_gradients_adaptive_sh_vs_adjoint():
         assert np.all(g["sh"][(top[i] + 1) ** 2:, :, i] == 0.0)
 
 
-@pytest.mark.parametrize("tile,bwd", [((16, 16), 4), ((16, 32), 4), ((16, 32), 1), ((8, 8), 2)])
+@pytest.mark.parametrize("tile,bwd", [((16, 16), 4), ((16, 32), 4), ((16, 32), 1), ((8, 8), 2), ((32, 32), 2), ((64, 16), 4)])
 def test_backward_pixels_per_thread(tile, bwd):
     sc, cams = I.workload(0)
     ws = _weights(sc, cams, 8)

@@ -103,7 +103,7 @@ def test_config0_records_bins_and_image():
     _check_image(sc, cams, img, rast=rast, out_T=out_T)
 
 
-@pytest.mark.parametrize("tile", [(8, 8), (16, 8), (8, 16), (32, 16), (16, 32)])
+@pytest.mark.parametrize("tile", [(8, 8), (16, 8), (8, 16), (32, 16), (16, 32), (32, 32), (64, 16)])
 def test_tile_size_bins_exact_and_image_unchanged(tile):
     sc, cams = I.workload(0)
     st = RenderSettings(tile_w=tile[0], tile_h=tile[1])
@@ -122,7 +122,7 @@ def test_batch_depth_does_not_change_image(batch):
     assert torch.equal(img, ref_img)
 
 
-@pytest.mark.parametrize("tile,fwd", [((16, 16), 2), ((16, 32), 2), ((32, 16), 1), ((8, 8), 2)])
+@pytest.mark.parametrize("tile,fwd", [((16, 16), 2), ((16, 32), 2), ((32, 16), 1), ((8, 8), 2), ((32, 32), 2)])
 def test_pixels_per_thread_does_not_change_image(tile, fwd):
     sc, cams = I.workload(0)
     _, _, img, _ = _run(sc, cams, RenderSettings(tile_w=tile[0], tile_h=tile[1], fwd_pixels=fwd))
