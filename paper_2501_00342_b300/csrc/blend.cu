@@ -106,25 +106,47 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
     return mask;
 }
 
+// Staged layouts of a batch entry in shared memory (field f of entry j at sb[f * batch + j]):
+// kPlain: the three records as read, (px, py, qa, qb), (qc, o, depth, radius),
+//         (r, g, b, clamp mask);
+// kPairs: each scalar the two-pixel kernels combine with a pair of pixels duplicated into
+//         a packed pair, (qa qa, qb qb), (qc qc, o o), (px px, py py), then the colour
+//         record as read;
+// kPairsColour: as kPairs, with the colour as pairs too: (r r, g g), (b b, 0 0).
+enum StageLayout { kPlain = 0, kPairs = 1, kPairsColour = 2 };
+constexpr int stage_fields(int layout) { return layout == kPlain ? 3 : layout == kPairs ? 4 : 5; }
+
 // Stages one group of 32 batch entries (this warp's group g: entries 32 g + lane < cnt,
 // from the tile's sorted list at `first`) in shared memory, and writes for every warp w of
 // the CTA the 32-bit word of the group's entries whose support may reach w's block
 // (bits[w * words + g]; bit b = entry 32 g + b): a transpose of the entries' block masks by
 // one ballot per warp.  Returns the record id of the lane's entry.  Warp-collective.
-template <int PPT>
+template <int PPT, int LAYOUT>
 __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileCoord& tc, int g, int cnt,
                                                 const uint32_t* __restrict__ first, uint32_t R,
                                                 const float4* __restrict__ rec0, const float4* __restrict__ rec1,
-                                                const float4* __restrict__ rec2, float4* s0, float4* s1,
-                                                float4* s2, uint32_t* bits, int words) {
+                                                const float4* __restrict__ rec2, float4* sb, int batch,
+                                                uint32_t* bits, int words) {
     const int lane = threadIdx.x & 31, j = g * 32 + lane;
     uint32_t mask = 0, id = 0;
     if (j < cnt) {
         id = min(first[j], R - 1);  // ids are < R by construction
-        const float4 r0 = rec0[id], r1 = rec1[id];
-        s0[j] = r0;
-        s1[j] = r1;
-        s2[j] = rec2[id];
+        const float4 r0 = rec0[id], r1 = rec1[id], r2 = rec2[id];
+        if (LAYOUT == kPlain) {
+            sb[j] = r0;
+            sb[batch + j] = r1;
+            sb[2 * batch + j] = r2;
+        } else {
+            sb[j] = make_float4(r0.z, r0.z, r0.w, r0.w);
+            sb[batch + j] = make_float4(r1.x, r1.x, r1.y, r1.y);
+            sb[2 * batch + j] = make_float4(r0.x, r0.x, r0.y, r0.y);
+            if (LAYOUT == kPairs) {
+                sb[3 * batch + j] = r2;
+            } else {
+                sb[3 * batch + j] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                sb[4 * batch + j] = make_float4(r2.z, r2.z, 0.0f, 0.0f);
+            }
+        }
         mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
     }
     const int nw = (int)(blockDim.x >> 5);
@@ -136,6 +158,43 @@ __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileC
     if (lane < nw) bits[lane * words + g] = mine;
     return id;
 }
+
+// Packed pairs of single-precision values for the f32x2 instructions of sm_100 and later:
+// one instruction applies the operation to both halves, each half rounded exactly as the
+// scalar operation (round to nearest even, subnormals kept).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk(f32x2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// A staged float4 field as its two packed pairs (x, y) and (z, w).
+__device__ __forceinline__ ulonglong2 pairs(const float4* f) { return *reinterpret_cast<const ulonglong2*>(f); }
 
 // Tile range clipped to the instances actually written (all of them unless overflowed).
 __device__ __forceinline__ uint2 clamp_range(uint2 r, uint32_t m) {
@@ -198,7 +257,8 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         if (__syncthreads_count(!all_done) == 0) break;
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
-            stage_group<PPT>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, s0, s1, s2, bits, words);
+            stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
+                                     words);
         __syncthreads();
         // this warp's entries in increasing order: the set bits of its words
         for (int g = 0; g < groups && !all_done; ++g) {
@@ -251,6 +311,114 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         pix_T[cam.pixel_base + pi] = p.T;
         pix_last[cam.pixel_base + pi] = p.last;
         if (COUNT) pix_count[cam.pixel_base + pi] = make_uint2(p.evaluated, p.contributed);
+    }
+}
+
+// The forward with two pixels per thread in packed pairs: a lane's pixels share their
+// column (rows r and r + 4 of its warp's 8x8 block), so the Gaussian's exponent, opacity
+// product and transmittance update of both run as f32x2 instructions on the staged pairs,
+// each half rounded exactly as the scalar pass rounds it; the decisions and the colour
+// sums stay per pixel.
+template <bool COUNT>
+__global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, const uint2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ vals, uint32_t R,
+                                                          const float4* __restrict__ rec0,
+                                                          const float4* __restrict__ rec1,
+                                                          const float4* __restrict__ rec2, int batch,
+                                                          float bg0, float bg1, float bg2,
+                                                          float* __restrict__ out_rgb,
+                                                          float* __restrict__ out_T,
+                                                          float* __restrict__ pix_T,
+                                                          uint32_t* __restrict__ pix_last,
+                                                          uint2* __restrict__ pix_count,
+                                                          const DeviceStatus* __restrict__ st) {
+    extern __shared__ float4 sbuf[];
+    const float4* e_q = sbuf;              // (qa qa, qb qb)
+    const float4* e_c = sbuf + batch;      // (qc qc, o o)
+    const float4* e_p = sbuf + 2 * batch;  // (px px, py py)
+    const float4* e_rgb = sbuf + 3 * batch;
+    const int words = (batch + 31) >> 5;
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairs) * batch);
+    const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
+    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const View& cam = vt.v[tc.v];
+    const WarpBlock wb = warp_block<2>(vt);
+    const int x = tc.tx * vt.tile_w + wb.x0 + (threadIdx.x & 7);
+    const int y0 = tc.ty * vt.tile_h + wb.y0 + ((threadIdx.x >> 3) & 3), y1 = y0 + 4;
+    const bool in0 = x < cam.W && y0 < cam.H, in1 = x < cam.W && y1 < cam.H;
+    const f32x2 pcx = pk((float)x + 0.5f, (float)x + 0.5f), pcy = pk((float)y0 + 0.5f, (float)y1 + 0.5f);
+    const f32x2 one = pk(1.0f, 1.0f);
+    float T0 = 1.0f, T1 = 1.0f;
+    float c00 = 0.0f, c01 = 0.0f, c02 = 0.0f, c10 = 0.0f, c11 = 0.0f, c12 = 0.0f;
+    uint32_t last0 = 0, last1 = 0, ev0 = 0, ev1 = 0, ct0 = 0, ct1 = 0;
+    bool done0 = !in0, done1 = !in1;
+    bool all_done = done0 && done1;
+    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    const int n = (int)(range.y - range.x);
+    for (int base = 0; base < n; base += batch) {
+        if (__syncthreads_count(!all_done) == 0) break;
+        const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
+        for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
+            stage_group<2, kPairs>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
+                                   words);
+        __syncthreads();
+        for (int g = 0; g < groups && !all_done; ++g) {
+            for (uint32_t word = my_bits[g]; word != 0 && !all_done; word &= word - 1) {
+                const int k = g * 32 + __ffs(word) - 1;
+                const ulonglong2 q = pairs(e_q + k), c = pairs(e_c + k), pp = pairs(e_p + k);
+                // the exponent of support_power for both pixels
+                const f32x2 dx = sub2(pp.x, pcx), dy = sub2(pp.y, pcy);
+                const float2 pw = upk(fma2(dx, fma2(q.x, dx, mul2(q.y, dy)), mul2(mul2(c.x, dy), dy)));
+                const float2 oG = upk(mul2(c.y, pk(__expf(pw.x), __expf(pw.y))));
+                const float a0 = fminf(kAlphaMax, oG.x), a1 = fminf(kAlphaMax, oG.y);
+                const bool s0 = !done0 && pw.x >= kSupportPower, s1 = !done1 && pw.y >= kSupportPower;
+                const bool ok0 = s0 && a0 >= kAlphaMin, ok1 = s1 && a1 >= kAlphaMin;
+                const f32x2 alpha = pk(a0, a1), T = pk(T0, T1);
+                const float2 Tn = upk(mul2(T, sub2(one, alpha)));
+                const float2 w = upk(mul2(alpha, T));
+                const bool end0 = ok0 && Tn.x < kTransmittanceMin, end1 = ok1 && Tn.y < kTransmittanceMin;
+                const bool add0 = ok0 && !end0, add1 = ok1 && !end1;
+                if (COUNT) {
+                    ev0 += s0;
+                    ev1 += s1;
+                    ct0 += add0;
+                    ct1 += add1;
+                }
+                done0 |= end0;
+                done1 |= end1;
+                const float4 rgb = e_rgb[k];
+                if (add0) {
+                    c00 = fmaf(rgb.x, w.x, c00);
+                    c01 = fmaf(rgb.y, w.x, c01);
+                    c02 = fmaf(rgb.z, w.x, c02);
+                    T0 = Tn.x;
+                    last0 = (uint32_t)(base + k + 1);
+                }
+                if (add1) {
+                    c10 = fmaf(rgb.x, w.y, c10);
+                    c11 = fmaf(rgb.y, w.y, c11);
+                    c12 = fmaf(rgb.z, w.y, c12);
+                    T1 = Tn.y;
+                    last1 = (uint32_t)(base + k + 1);
+                }
+                all_done = done0 && done1;
+            }
+        }
+    }
+    const int64_t hw = (int64_t)cam.W * cam.H;
+    float* img = out_rgb + 3 * cam.pixel_base;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (!(q ? in1 : in0)) continue;
+        const int64_t pi = (int64_t)(q ? y1 : y0) * cam.W + x;
+        const float T = q ? T1 : T0;
+        img[pi] = (q ? c10 : c00) + T * bg0;
+        img[hw + pi] = (q ? c11 : c01) + T * bg1;
+        img[2 * hw + pi] = (q ? c12 : c02) + T * bg2;
+        if (out_T) out_T[cam.pixel_base + pi] = T;
+        pix_T[cam.pixel_base + pi] = T;
+        pix_last[cam.pixel_base + pi] = q ? last1 : last0;
+        if (COUNT) pix_count[cam.pixel_base + pi] = q ? make_uint2(ev1, ct1) : make_uint2(ev0, ct0);
     }
 }
 
@@ -357,8 +525,8 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
         __syncthreads();
         const int cnt = hi - lo, groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5)) {
-            const uint32_t id =
-                stage_group<PPT>(vt, tc, g, cnt, vals + range.x + lo, R32, rec0, rec1, rec2, s0, s1, s2, bits, words);
+            const uint32_t id = stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + lo, R32, rec0, rec1, rec2,
+                                                         sbuf, batch, bits, words);
             if (g * 32 + lane < cnt) sid[g * 32 + lane] = id;
         }
         __syncthreads();
@@ -432,6 +600,157 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     }
 }
 
+// The reverse walk with two pixels per thread in packed pairs (the pixel map of
+// blend_pair_kernel).  The exponent, opacity product and gradient terms of both pixels run
+// as f32x2 instructions, each half rounded exactly as the scalar pass rounds it, so every
+// skip decision matches the forward.  The transmittance and the colour behind are updated
+// per pixel; a pixel that does not blend the Gaussian contributes zero-weighted terms.
+__global__ void __launch_bounds__(512) blend_pair_backward_kernel(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, uint32_t R32,
+    const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
+    int batch, float bg0, float bg1, float bg2, const float* __restrict__ pix_T,
+    const uint32_t* __restrict__ pix_last, const float* __restrict__ dL_drgb,
+    float4* __restrict__ grad2d, int64_t R, const DeviceStatus* __restrict__ st) {
+    extern __shared__ float4 sbuf[];
+    const float4* e_q = sbuf;               // (qa qa, qb qb)
+    const float4* e_c = sbuf + batch;       // (qc qc, o o)
+    const float4* e_p = sbuf + 2 * batch;   // (px px, py py)
+    const float4* e_rg = sbuf + 3 * batch;  // (r r, g g)
+    const float4* e_b = sbuf + 4 * batch;   // (b b, 0 0)
+    const int words = (batch + 31) >> 5;
+    uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairsColour) * batch);
+    uint32_t* bits = sid + batch;
+    const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
+    __shared__ uint32_t s_max_last;
+    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const View& cam = vt.v[tc.v];
+    const WarpBlock wb = warp_block<2>(vt);
+    const int x = tc.tx * vt.tile_w + wb.x0 + (threadIdx.x & 7);
+    const int y0 = tc.ty * vt.tile_h + wb.y0 + ((threadIdx.x >> 3) & 3), y1 = y0 + 4;
+    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    if (threadIdx.x == 0) s_max_last = 0;
+    __syncthreads();
+    const int64_t hw = (int64_t)cam.W * cam.H;
+    const float* gi = dL_drgb + 3 * cam.pixel_base;
+    float g[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    float T[2] = {1.0f, 1.0f};
+    uint32_t last[2] = {0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int y = q ? y1 : y0;
+        if (x < cam.W && y < cam.H) {
+            const int64_t pi = (int64_t)y * cam.W + x;
+            g[q][0] = gi[pi];
+            g[q][1] = gi[hw + pi];
+            g[q][2] = gi[2 * hw + pi];
+            T[q] = pix_T[cam.pixel_base + pi];
+            last[q] = min(pix_last[cam.pixel_base + pi], range.y - range.x);
+        }
+    }
+    const f32x2 pcx = pk((float)x + 0.5f, (float)x + 0.5f), pcy = pk((float)y0 + 0.5f, (float)y1 + 0.5f);
+    const f32x2 gr = pk(g[0][0], g[1][0]), gg = pk(g[0][1], g[1][1]), gb = pk(g[0][2], g[1][2]);
+    const f32x2 one = pk(1.0f, 1.0f), neg_half = pk(-0.5f, -0.5f);
+    float acc[2][3] = {{bg0, bg1, bg2}, {bg0, bg1, bg2}};
+    const uint32_t wmax = __reduce_max_sync(kFullMask, max(last[0], last[1]));
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_max_last, wmax);
+    __syncthreads();
+    const int top = (int)s_max_last;
+    const int lane = threadIdx.x & 31;
+    const int warp_last = (int)wmax;  // no pixel of this warp blends an entry at or past it
+    for (int hi = top; hi > 0; hi -= batch) {
+        const int lo = max(0, hi - batch);
+        __syncthreads();
+        const int cnt = hi - lo, groups = (cnt + 31) >> 5;
+        for (int gr_ = (int)(threadIdx.x >> 5); gr_ < groups; gr_ += (int)(blockDim.x >> 5)) {
+            const uint32_t id = stage_group<2, kPairsColour>(vt, tc, gr_, cnt, vals + range.x + lo, R32, rec0, rec1,
+                                                             rec2, sbuf, batch, bits, words);
+            if (gr_ * 32 + lane < cnt) sid[gr_ * 32 + lane] = id;
+        }
+        __syncthreads();
+        // this warp's entries below its last contributor, back to front
+        const int lim = min(cnt, warp_last - lo);
+        for (int grp = ((lim + 31) >> 5) - 1; grp >= 0; --grp) {
+            const int rem = lim - grp * 32;
+            for (uint32_t word = my_bits[grp] & (rem >= 32 ? ~0u : (1u << rem) - 1u); word != 0;) {
+                const int bit = 31 - __clz(word);
+                word ^= 1u << bit;
+                const int j = grp * 32 + bit;
+                const uint32_t k = (uint32_t)(lo + j);
+                const ulonglong2 q = pairs(e_q + j), c = pairs(e_c + j), pp = pairs(e_p + j);
+                // support_terms for both pixels
+                const f32x2 dx = sub2(pp.x, pcx), dy = sub2(pp.y, pcy);
+                const f32x2 u = fma2(q.x, dx, mul2(q.y, dy)), t = mul2(c.x, dy);
+                const float2 pw = upk(fma2(dx, u, mul2(t, dy)));
+                const f32x2 G = pk(__expf(pw.x), __expf(pw.y));
+                const float2 oG = upk(mul2(c.y, G));
+                const float a0 = fminf(kAlphaMax, oG.x), a1 = fminf(kAlphaMax, oG.y);
+                const bool use0 = k < last[0] && pw.x >= kSupportPower && a0 >= kAlphaMin;
+                const bool use1 = k < last[1] && pw.y >= kSupportPower && a1 >= kAlphaMin;
+                if (!__any_sync(kFullMask, use0 || use1)) continue;
+                const float2 om = upk(sub2(one, pk(a0, a1)));
+                if (use0) T[0] = __fdividef(T[0], om.x);
+                if (use1) T[1] = __fdividef(T[1], om.y);
+                const f32x2 alpha = pk(use0 ? a0 : 0.0f, use1 ? a1 : 0.0f);
+                const f32x2 Tp = pk(T[0], T[1]);
+                const f32x2 w = mul2(alpha, Tp);
+                // colour behind minus this Gaussian's colour; acc += alpha (c - acc)
+                const ulonglong2 rg = pairs(e_rg + j), bb = pairs(e_b + j);
+                const f32x2 er = sub2(rg.x, pk(acc[0][0], acc[1][0]));
+                const f32x2 eg = sub2(rg.y, pk(acc[0][1], acc[1][1]));
+                const f32x2 eb = sub2(bb.x, pk(acc[0][2], acc[1][2]));
+                const f32x2 dalpha = mul2(Tp, fma2(gr, er, fma2(gg, eg, mul2(gb, eb))));
+                {
+                    const float2 r = upk(er), gv = upk(eg), b = upk(eb);
+                    if (use0) {
+                        acc[0][0] = fmaf(a0, r.x, acc[0][0]);
+                        acc[0][1] = fmaf(a0, gv.x, acc[0][1]);
+                        acc[0][2] = fmaf(a0, b.x, acc[0][2]);
+                    }
+                    if (use1) {
+                        acc[1][0] = fmaf(a1, r.y, acc[1][0]);
+                        acc[1][1] = fmaf(a1, gv.y, acc[1][1]);
+                        acc[1][2] = fmaf(a1, b.y, acc[1][2]);
+                    }
+                }
+                // through alpha = o G only where the 0.99 clamp is not active
+                const float2 gGv = upk(mul2(dalpha, G));
+                const f32x2 gG = pk(use0 && oG.x <= kAlphaMax ? gGv.x : 0.0f, use1 && oG.y <= kAlphaMax ? gGv.y : 0.0f);
+                const f32x2 gpow = mul2(gG, c.y);
+                // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2):
+                // d/d px = u + qa dx, d/d py = qb dx + 2 qc dy, d/d(qa, qb, qc) = (dx^2, dx dy, dy^2)
+                const f32x2 h = mul2(neg_half, gpow);
+                const float2 t0 = upk(mul2(gpow, fma2(q.x, dx, u)));
+                const float2 t1 = upk(mul2(gpow, fma2(q.y, dx, add2(t, t))));
+                const float2 t2 = upk(mul2(mul2(h, dx), dx));
+                const float2 t3 = upk(mul2(mul2(gpow, dx), dy));
+                const float2 t4 = upk(mul2(mul2(h, dy), dy));
+                const float2 t5 = upk(gG);
+                const float2 t6 = upk(mul2(gr, w)), t7 = upk(mul2(gg, w)), t8 = upk(mul2(gb, w));
+                float d[9];
+                d[0] = t0.x + t0.y;
+                d[1] = t1.x + t1.y;
+                d[2] = t2.x + t2.y;
+                d[3] = -(t3.x + t3.y);
+                d[4] = t4.x + t4.y;
+                d[5] = t5.x + t5.y;
+                d[6] = t6.x + t6.y;
+                d[7] = t7.x + t7.y;
+                d[8] = t8.x + t8.y;
+                // lanes 0, 4, ..., 28 hold the sums of values 0..7; lanes 0 and 16 gather
+                // values 0-3 and 4-7 and add them with one 16-byte vector reduction each
+                const float s8 = warp_sum8(d, lane);
+                const float s9 = warp_sum(d[8]);
+                const float u1 = __shfl_down_sync(kFullMask, s8, 4);
+                const float u2 = __shfl_down_sync(kFullMask, s8, 8);
+                const float u3 = __shfl_down_sync(kFullMask, s8, 12);
+                const uint32_t id = sid[j];
+                if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
+                if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
+            }
+        }
+    }
+}
+
 __global__ void l1_zero_kernel(float* loss) { *loss = 0.0f; }
 
 __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, const float* __restrict__ tgt,
@@ -456,6 +775,24 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 }
 
 }  // namespace
+
+template <bool COUNT>
+static cudaError_t blend_pair(const ViewTable& vt, const uint2* ranges, const uint32_t* vals, int64_t R,
+                              const RecordPtrs& p, int batch, float bg0, float bg1, float bg2, float* out_rgb,
+                              float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
+                              const DeviceStatus* st, cudaStream_t s) {
+    const int threads = vt.tile_w * vt.tile_h / 2;
+    const size_t smem =
+        (size_t)batch * stage_fields(kPairs) * sizeof(float4) + (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
+    cudaError_t e =
+        cudaFuncSetAttribute(blend_pair_kernel<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    blend_pair_kernel<COUNT><<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0,
+                                                                           p.rec1, p.rec2, batch, bg0, bg1, bg2,
+                                                                           out_rgb, out_T, pix_T, pix_last,
+                                                                           pix_count, st);
+    return cudaGetLastError();
+}
 
 template <int PPT, bool COUNT>
 static cudaError_t blend_ppt(const ViewTable& vt, const uint2* ranges, const uint32_t* vals, int64_t R,
@@ -500,8 +837,11 @@ cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_
     return blend_ppt<PPT, COUNT>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, \
                                  pix_count, st, s)
     if (vt.fwd_ppt == 2) {
-        if (vt.count_pairs) SGS_BLEND(2, true);
-        SGS_BLEND(2, false);
+        if (vt.count_pairs)
+            return blend_pair<true>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last,
+                                    pix_count, st, s);
+        return blend_pair<false>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last,
+                                 pix_count, st, s);
     }
     if (vt.count_pairs) SGS_BLEND(1, true);
     SGS_BLEND(1, false);
@@ -517,9 +857,18 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
     if (vt.bwd_ppt == 4)
         return blend_backward_ppt<4>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d,
                                      R, st, s);
-    if (vt.bwd_ppt == 2)
-        return blend_backward_ppt<2>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d,
-                                     R, st, s);
+    if (vt.bwd_ppt == 2) {
+        const int threads = vt.tile_w * vt.tile_h / 2;
+        const size_t smem = (size_t)batch * (stage_fields(kPairsColour) * sizeof(float4) + sizeof(uint32_t)) +
+                            (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
+        cudaError_t e = cudaFuncSetAttribute(blend_pair_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        blend_pair_backward_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(
+            vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb,
+            grad2d, R, st);
+        return cudaGetLastError();
+    }
     return blend_backward_ppt<1>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d, R,
                                  st, s);
 }
