@@ -279,15 +279,16 @@ def run_gpu(args):
     p_bytes = 4 * scene.floats_per_gaussian()
     hbm, sm_max, peak_kind = _peaks()
     alu_peak = 148 * 128 * sm_max * 1e6 / 1e12  # Tops/s: one FP32 op per lane per clock
+    fwd_name = "blend_pair_kernel" if settings.fwd_pixels in (0, 2) else "blend_kernel"
+    bwd_name = "blend_pair_backward_kernel" if settings.bwd_pixels in (0, 2) else "blend_backward_kernel"
     kernels = {
         "preprocess_kernel": dict(ms=stages["preprocess"], launches=1, bound="hbm",
                                   work=n * p_bytes + visible * 48 + n * nv * 12),
         "onesweep_kernel": dict(ms=stages["sort_onesweep_all_passes"] / max(P, 1), launches=P, bound="hbm",
                                 work=16 * M),  # u32 tile id + u32 record id, read and written
-        "blend_kernel": dict(ms=stages["blend"], launches=1, bound="alu",
-                             work=8 * e_eval + 11 * e_contrib),
-        "blend_backward_kernel": dict(ms=stages["backward_blend"], launches=1, bound="alu",
-                                      work=8 * e_eval + 40 * e_contrib),
+        # two pixels per thread run the packed-pair kernels
+        fwd_name: dict(ms=stages["blend"], launches=1, bound="alu", work=8 * e_eval + 11 * e_contrib),
+        bwd_name: dict(ms=stages["backward_blend"], launches=1, bound="alu", work=8 * e_eval + 40 * e_contrib),
         "preprocess_backward_kernel": dict(ms=stages["backward_preprocess"], launches=1, bound="hbm",
                                            work=2 * n * p_bytes + visible * 48),
     }

@@ -35,6 +35,7 @@ __global__ void fill_u32_kernel(uint32_t* p, uint32_t value, size_t count) {
 // the next tile id from a counter, so every predecessor tile is already running.
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __restrict__ in,
                                                              const uint32_t* __restrict__ perm,
+                                                             const RecordValue rv,
                                                              uint32_t* __restrict__ out, int64_t R,
                                                              unsigned long long* lookback,
                                                              DeviceStatus* st, int64_t capacity) {
@@ -46,9 +47,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
     const uint32_t tile = s_tile;
     const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
-    if (perm) {  // counts taken in the order of the depth-sorted records
+    if (perm) {  // counts carried by the depth-sorted record values
 #pragma unroll
-        for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < R) ? in[perm[base + q]] : 0u;
+        for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < R) ? rv.count(perm[base + q], in) : 0u;
     } else if (base + kScanItems <= R) {
         const uint4* p4 = reinterpret_cast<const uint4*>(in + base);
 #pragma unroll
@@ -149,7 +150,8 @@ template <int RB>
 __global__ void __launch_bounds__(256) record_keys_kernel(const uint32_t* __restrict__ tiles,
                                                            const float4* __restrict__ rec1, int64_t R,
                                                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                           DeviceStatus* st, int passes, uint32_t* __restrict__ hist) {
+                                                           const RecordValue rv, DeviceStatus* st, int passes,
+                                                           uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
     extern __shared__ uint32_t h[];  // [8 warps][passes][RADIX]
     for (int j = threadIdx.x; j < 8 * passes * RADIX; j += blockDim.x) h[j] = 0;
@@ -164,9 +166,10 @@ __global__ void __launch_bounds__(256) record_keys_kernel(const uint32_t* __rest
         const bool valid = r < R;
         uint32_t key = 0xffffffffu;
         if (valid) {
-            key = tiles[r] ? __float_as_uint(rec1[r].z) : 0xffffffffu;
+            const uint32_t t = tiles[r];
+            key = t ? __float_as_uint(rec1[r].z) : 0xffffffffu;
             keys[r] = key;
-            vals[r] = (uint32_t)r;
+            vals[r] = rv.pack((uint32_t)r, t);
         }
         const uint32_t live = __ballot_sync(kFullMask, valid);
         for (int p = 0; p < passes; ++p) {
@@ -209,10 +212,11 @@ __device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, uint3
 }
 
 // Writes the (tile id, record) instances in the order of the depth-sorted records
-// (perm): sorted position j emits its record's tiles at offsets[j] (the scan taken in that
-// order), tiles row-major.  One warp per 32 consecutive sorted positions, whose instances
-// fill one contiguous output range 32 slots at a time: for slot e a 5-step shuffle search
-// finds the record (inclusive scan of the counts), its packed row table (written by
+// (perm, RecordValue ids): sorted position j emits its record's offsets[j + 1] - offsets[j]
+// tiles at offsets[j] (the scan taken in that order), tiles row-major.  One warp per 32
+// consecutive sorted positions, whose instances fill one contiguous output range 32 slots
+// at a time: for slot e a 5-step shuffle search finds the record (the offsets relative to
+// the warp's first are the inclusive scan of the counts), its packed row table (written by
 // preprocess, staged in shared memory) gives the row, and consecutive lanes write
 // consecutive slots.  A record whose table overflowed is filled afterwards by the whole
 // warp, recomputing its rows with row_span.  Since every instance of a record has the same
@@ -222,7 +226,7 @@ __device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, uint3
 // counted here (count_tile_digits).
 template <int RB>
 __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, const uint4* __restrict__ spans,
-                                                         const uint32_t* __restrict__ tiles,
+                                                         const RecordValue rv,
                                                          const float4* __restrict__ rec0,
                                                          const float4* __restrict__ rec1,
                                                          const uint32_t* __restrict__ perm,
@@ -246,9 +250,14 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < R;
          base += warps * 32) {
         const int64_t j = base + lane;
-        const uint32_t r = j < R ? perm[j] : 0u;
-        const uint32_t cnt = (j < R && !overflow && r < (uint32_t)R) ? tiles[r] : 0u;
+        // the record's count from the scan: the difference of consecutive offsets
+        const uint32_t m_end = st->m_clamped;
+        const uint32_t o = j < R ? offsets[j] : m_end;
+        uint32_t o_next = __shfl_down_sync(kFullMask, o, 1);
+        if (lane == 31) o_next = base + 32 < R ? offsets[base + 32] : m_end;
+        const uint32_t cnt = overflow ? 0u : o_next - o;
         if (!__ballot_sync(kFullMask, cnt != 0u)) continue;
+        const uint32_t r = cnt ? rv.id(perm[j]) : 0u;
         uint32_t tbase = 0, hdr = 0;
         int TW = 0;
         if (cnt) {
@@ -261,14 +270,9 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
         }
         __syncwarp();
         const bool slow = cnt && (hdr >> 16) == kSpanRowsOverflow;
-        uint32_t incl = cnt;  // inclusive warp scan of the counts
-#pragma unroll
-        for (int k = 1; k < 32; k <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFullMask, incl, k);
-            if (lane >= k) incl += y;
-        }
+        const uint32_t obase = __shfl_sync(kFullMask, o, 0);
+        const uint32_t incl = overflow ? 0u : o_next - obase;  // inclusive warp scan of the counts
         const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-        const uint32_t obase = __shfl_sync(kFullMask, lane == 0 ? offsets[base] : 0u, 0);
         for (uint32_t e0 = 0; e0 < total; e0 += 32) {
             const uint32_t e = e0 + lane;
             int q = 0;  // records whose range ends at or before slot e
@@ -412,13 +416,20 @@ cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStrea
     return cudaGetLastError();
 }
 
+RecordValue record_value(int64_t R) {
+    RecordValue rv;
+    rv.id_bits = 1;
+    while (rv.id_bits < 32 && ((int64_t)1 << rv.id_bits) < R) ++rv.id_bits;
+    return rv;
+}
+
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
                         cudaStream_t s) {
     const int64_t num_tiles = (R + kScanTile - 1) / kScanTile;
     if (num_tiles == 0) return cudaSuccess;
-    scan_kernel<<<(unsigned)num_tiles, kScanThreads, 0, s>>>(tiles, perm, offsets, R, scan_lookback, st,
-                                                             capacity);
+    scan_kernel<<<(unsigned)num_tiles, kScanThreads, 0, s>>>(tiles, perm, record_value(R), offsets, R,
+                                                             scan_lookback, st, capacity);
     return cudaGetLastError();
 }
 
@@ -433,7 +444,7 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
     const int64_t want = (R + threads - 1) / threads;
     const unsigned blocks = (unsigned)(want < 148 * 8 ? want : 148 * 8);
     switch (digit_bits) {
-#define SGS_DUP(RB) case RB: duplicate_kernel<RB><<<blocks, threads, 0, s>>>(vt, p.spans, p.tiles, p.rec0, \
+#define SGS_DUP(RB) case RB: duplicate_kernel<RB><<<blocks, threads, 0, s>>>(vt, p.spans, record_value(R), p.rec0, \
         p.rec1, perm, offsets, n, R, st, capacity, keys, vals, passes, hist); break;
         SGS_DUP(4) SGS_DUP(5) SGS_DUP(6) SGS_DUP(7) SGS_DUP(8) SGS_DUP(9) SGS_DUP(10)
 #undef SGS_DUP
@@ -471,7 +482,8 @@ cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_
         if ((e = cudaFuncSetAttribute(record_keys_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem)) != cudaSuccess)                                                \
             return e;                                                                                            \
-        record_keys_kernel<RB><<<blocks, threads, smem, s>>>(tiles, rec1, R, keys, vals, st, passes, hist);      \
+        record_keys_kernel<RB><<<blocks, threads, smem, s>>>(tiles, rec1, R, keys, vals, record_value(R), st,     \
+                                                             passes, hist);                                      \
         break;
         SGS_RK(4) SGS_RK(5) SGS_RK(6) SGS_RK(7) SGS_RK(8)
 #undef SGS_RK

@@ -40,11 +40,31 @@ cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStrea
 // The scan's bounded look-back over slots[0, n) from slot n-1 (sum and status word out).
 cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n, unsigned long long* sum,
                                      int32_t* status, cudaStream_t s);
-// Keys (view depth bits; 0xffffffff without instances) and ids of the record sort; also
-// stores R in st->num_records.
+// Values of the record sort: the record id in the low id_bits bits (id_bits = bits of
+// R - 1, at least 1) and, in the 32 - id_bits bits above, the record's tile count, or the
+// all-ones count (also when no bit is left) for "read tiles[id]".  The scan then takes the
+// counts in depth order without gathering them.
+struct RecordValue {
+    int id_bits;
+    __host__ __device__ uint32_t id_mask() const { return (uint32_t)((1ull << id_bits) - 1ull); }
+    __host__ __device__ uint32_t count_max() const { return (uint32_t)((1ull << (32 - id_bits)) - 1ull); }
+    __host__ __device__ uint32_t pack(uint32_t id, uint32_t count) const {
+        return id_bits == 32 ? id : id | (min(count, count_max()) << id_bits);
+    }
+    __host__ __device__ uint32_t id(uint32_t v) const { return v & id_mask(); }
+    // the count of value v (tiles: the per-record counts it falls back to)
+    __device__ uint32_t count(uint32_t v, const uint32_t* tiles) const {
+        const uint32_t c = (uint32_t)((unsigned long long)v >> id_bits);
+        return c == count_max() ? tiles[v & id_mask()] : c;
+    }
+};
+RecordValue record_value(int64_t R);
+// Keys (view depth bits; 0xffffffff without instances) and packed values (RecordValue) of
+// the record sort; also stores R in st->num_records.
 cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
                                uint32_t* vals, DeviceStatus* st, int digit_bits, uint32_t* hist, cudaStream_t s);
-// Exclusive scan of tiles[perm[j]] (or tiles[j] when perm is null).
+// Exclusive scan of the counts of the depth-sorted record values perm (RecordValue), or of
+// tiles[j] when perm is null.
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
                         cudaStream_t s);

@@ -44,7 +44,8 @@ def test_cache_hit_skips_timing(tmp_path, monkeypatch):
 
 def test_coordinate_descent_keeps_the_fastest(tmp_path, monkeypatch):
     """With a synthetic cost the tuner visits each axis once and keeps the minimum."""
-    cost = {(16, 16): 5.0, (16, 8): 4.0, (32, 8): 6.0, (8, 8): 7.0, (32, 16): 4.5, (16, 32): 4.6, (64, 8): 6.5}
+    cost = {(16, 16): 5.0, (16, 8): 4.0, (32, 8): 6.0, (8, 8): 7.0, (32, 16): 4.5, (16, 32): 4.6, (64, 8): 6.5,
+            (32, 32): 4.2, (64, 16): 4.8}
     seen = []
 
     def fake_time(model, cams, st, steps=3, grad=None):
@@ -59,7 +60,7 @@ def test_coordinate_descent_keeps_the_fastest(tmp_path, monkeypatch):
     got = autotune(_fake_model(), I.orbit_cameras(1, 64, 64), cache_path=str(path), log=log)
     assert (got.tile_w, got.tile_h, got.batch_depth, got.digit_bits) == (16, 8, 256, 9)
     assert (got.fwd_pixels, got.bwd_pixels) == (1, 2)
-    assert len(seen) == len(log) == 1 + 6 + 3 + 2 + 2 + 2
+    assert len(seen) == len(log) == 1 + 8 + 3 + 2 + 2 + 2
     stored = json.loads(path.read_text())
     assert list(stored.values())[0]["settings"] == {k: v for k, v in dataclasses.asdict(got).items() if k != "bg"}
 
