@@ -124,6 +124,9 @@ RecordPtrs records(const sgs_plan* p) {
     r.rect = region<uint2>(p, O_RECT);
     r.tiles = region<uint32_t>(p, O_TILES);
     r.spans = region<uint4>(p, O_SPANS);
+    r.sort_keys = region<uint32_t>(p, O_RK0);
+    r.sort_vals = region<uint32_t>(p, O_RV0);
+    r.rv = record_value(p->num_records);
     return r;
 }
 
@@ -284,8 +287,9 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
                             2 * (size_t)((R + kScanTile - 1) / kScanTile + 1), stream));
     // (c, depth half) stable sort of the records by view depth bits
     const int rpasses = sort_passes(0, 32, plan->settings.digit_bits);
-    SGS_TRY(launch_record_keys(rp.tiles, rp.rec1, R, region<uint32_t>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
-                               st, plan->settings.digit_bits, region<uint32_t>(plan, O_HIST), stream));
+    // the preprocess wrote the pairs (keys: depth bits; values: RecordValue)
+    SGS_TRY(launch_record_hist(region<uint32_t>(plan, O_RK0), R, st, plan->settings.digit_bits,
+                               region<uint32_t>(plan, O_HIST), stream));
     if (R > 0)
         SGS_TRY(launch_sort(region<uint32_t>(plan, O_RK0), region<uint32_t>(plan, O_RV0),
                             region<uint32_t>(plan, O_RK1), region<uint32_t>(plan, O_RV1),

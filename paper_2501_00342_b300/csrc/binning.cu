@@ -141,17 +141,14 @@ __device__ __forceinline__ uint32_t same_value_lanes(uint32_t d) {
     return peers;
 }
 
-// Keys of the record sort (view depth bits; 0xffffffff for a record without instances) and
-// ids, with the digit histograms of every pass of that sort counted on the way (per-warp
-// shared copies).  The low digits of depth bits are spread: one shared atomic each; the
-// high ones (exponent and top mantissa bits) repeat within a warp: the warp adds each
-// distinct digit once.
+// Digit histograms of every pass of the record sort over its keys (view depth bits;
+// 0xffffffff for a record without instances), per-warp shared copies.  The low digits of
+// depth bits are spread: one shared atomic each; the high ones (exponent and top mantissa
+// bits) repeat within a warp: the warp adds each distinct digit once.  Also stores R in
+// st->num_records.
 template <int RB>
-__global__ void __launch_bounds__(256) record_keys_kernel(const uint32_t* __restrict__ tiles,
-                                                           const float4* __restrict__ rec1, int64_t R,
-                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                           const RecordValue rv, DeviceStatus* st, int passes,
-                                                           uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(256) record_hist_kernel(const uint32_t* __restrict__ keys, int64_t R,
+                                                          DeviceStatus* st, int passes, uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
     extern __shared__ uint32_t h[];  // [8 warps][passes][RADIX]
     for (int j = threadIdx.x; j < 8 * passes * RADIX; j += blockDim.x) h[j] = 0;
@@ -164,13 +161,7 @@ __global__ void __launch_bounds__(256) record_keys_kernel(const uint32_t* __rest
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < R; base += stride) {
         const int64_t r = base + lane;
         const bool valid = r < R;
-        uint32_t key = 0xffffffffu;
-        if (valid) {
-            const uint32_t t = tiles[r];
-            key = t ? __float_as_uint(rec1[r].z) : 0xffffffffu;
-            keys[r] = key;
-            vals[r] = rv.pack((uint32_t)r, t);
-        }
+        const uint32_t key = valid ? keys[r] : 0xffffffffu;
         const uint32_t live = __ballot_sync(kFullMask, valid);
         for (int p = 0; p < passes; ++p) {
             const uint32_t d = (key >> (p * RB)) & (RADIX - 1);
@@ -466,8 +457,8 @@ cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t 
 }  // namespace sgs
 
 namespace sgs {
-cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
-                               uint32_t* vals, DeviceStatus* st, int digit_bits, uint32_t* hist, cudaStream_t s) {
+cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st, int digit_bits, uint32_t* hist,
+                               cudaStream_t s) {
     int passes, rb;
     sort_digit_plan(0, 32, digit_bits, &passes, &rb);
     cudaError_t e = launch_fill_u32(hist, 0u, (size_t)passes << rb, s);
@@ -477,16 +468,15 @@ cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_
     const unsigned blocks = (unsigned)(want < 1 ? 1 : (want < 148 * 8 ? want : 148 * 8));
     const size_t smem = (size_t)8 * passes * ((size_t)1 << rb) * sizeof(uint32_t);
     switch (rb) {
-#define SGS_RK(RB)                                                                                              \
+#define SGS_RH(RB)                                                                                              \
     case RB:                                                                                                     \
-        if ((e = cudaFuncSetAttribute(record_keys_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+        if ((e = cudaFuncSetAttribute(record_hist_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem)) != cudaSuccess)                                                \
             return e;                                                                                            \
-        record_keys_kernel<RB><<<blocks, threads, smem, s>>>(tiles, rec1, R, keys, vals, record_value(R), st,     \
-                                                             passes, hist);                                      \
+        record_hist_kernel<RB><<<blocks, threads, smem, s>>>(keys, R, st, passes, hist);                         \
         break;
-        SGS_RK(4) SGS_RK(5) SGS_RK(6) SGS_RK(7) SGS_RK(8)
-#undef SGS_RK
+        SGS_RH(4) SGS_RH(5) SGS_RH(6) SGS_RH(7) SGS_RH(8)
+#undef SGS_RH
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

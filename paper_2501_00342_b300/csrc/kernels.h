@@ -16,30 +16,6 @@ inline cudaError_t record_probe(cudaEvent_t ev, cudaStream_t s) {
         ev, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
-struct RecordPtrs {
-    float4* rec0;  // px, py, -A/2, -B
-    float4* rec1;  // -C/2, opacity, depth, radius
-    float4* rec2;  // r, g, b, clamp mask
-    uint2* rect;
-    uint32_t* tiles;
-    uint4* spans;  // [4][R] packed tile-row table per record (see count_tiles)
-};
-
-// (a) preprocess and its backward
-cudaError_t launch_preprocess(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
-                              cudaStream_t s);
-cudaError_t launch_preprocess_backward(const sgs_gaussians& g, const ViewTable& vt,
-                                       const RecordPtrs& p, const float4* grad2d, int64_t R,
-                                       const sgs_grads& out, cudaStream_t s);
-
-// (b), (d): scan + duplicate, ranges
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;
-cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStream_t s);
-// The scan's bounded look-back over slots[0, n) from slot n-1 (sum and status word out).
-cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n, unsigned long long* sum,
-                                     int32_t* status, cudaStream_t s);
 // Values of the record sort: the record id in the low id_bits bits (id_bits = bits of
 // R - 1, at least 1) and, in the 32 - id_bits bits above, the record's tile count, or the
 // all-ones count (also when no bit is left) for "read tiles[id]".  The scan then takes the
@@ -59,10 +35,41 @@ struct RecordValue {
     }
 };
 RecordValue record_value(int64_t R);
-// Keys (view depth bits; 0xffffffff without instances) and packed values (RecordValue) of
-// the record sort; also stores R in st->num_records.
-cudaError_t launch_record_keys(const uint32_t* tiles, const float4* rec1, int64_t R, uint32_t* keys,
-                               uint32_t* vals, DeviceStatus* st, int digit_bits, uint32_t* hist, cudaStream_t s);
+
+struct RecordPtrs {
+    float4* rec0;  // px, py, -A/2, -B
+    float4* rec1;  // -C/2, opacity, depth, radius
+    float4* rec2;  // r, g, b, clamp mask
+    uint2* rect;
+    uint32_t* tiles;
+    uint4* spans;  // [4][R] packed tile-row table per record (see count_tiles)
+    // the record sort's input, written by the preprocess: keys (view depth bits of a record
+    // with instances, 0xffffffff for the others) and values (RecordValue)
+    uint32_t* sort_keys;
+    uint32_t* sort_vals;
+    RecordValue rv;
+};
+
+// (a) preprocess and its backward
+cudaError_t launch_preprocess(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
+                              cudaStream_t s);
+cudaError_t launch_preprocess_backward(const sgs_gaussians& g, const ViewTable& vt,
+                                       const RecordPtrs& p, const float4* grad2d, int64_t R,
+                                       const sgs_grads& out, cudaStream_t s);
+
+// (b), (d): scan + duplicate, ranges
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStream_t s);
+// The scan's bounded look-back over slots[0, n) from slot n-1 (sum and status word out).
+cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n, unsigned long long* sum,
+                                     int32_t* status, cudaStream_t s);
+
+// Digit histograms of the record sort over its keys (written by the preprocess); also stores
+// R in st->num_records.
+cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st, int digit_bits, uint32_t* hist,
+                               cudaStream_t s);
 // Exclusive scan of the counts of the depth-sorted record values perm (RecordValue), or of
 // tiles[j] when perm is null.
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,

@@ -261,7 +261,10 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
                                                                  float4* __restrict__ rec2,
                                                                  uint2* __restrict__ rect,
                                                                  uint32_t* __restrict__ tiles,
-                                                                 uint4* __restrict__ spans) {
+                                                                 uint4* __restrict__ spans,
+                                                                 uint32_t* __restrict__ sort_keys,
+                                                                 uint32_t* __restrict__ sort_vals,
+                                                                 const RecordValue rv) {
     using CS = ColourShared<L, K, AX>;
     __shared__ float s_colour[CS::COUNT * kPreThreads];
     __shared__ uint32_t s_table[16 * kPreThreads];
@@ -281,6 +284,9 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         Projected P;
         project_exact(cam, X, G, vt.inv_tile_w, vt.inv_tile_h, P);
         const uint32_t hits = P.visible ? count_tiles(P, cam, vt, table, kPreThreads) : 0u;
+        // the record sort's pair: depth bits (depth > near > 0 orders like the floats)
+        sort_keys[r] = hits ? __float_as_uint(P.t[2]) : 0xffffffffu;
+        sort_vals[r] = rv.pack((uint32_t)r, hits);
         if (hits == 0u) {
             rect[r] = make_uint2(0u, 0u);
             tiles[r] = 0u;
@@ -451,7 +457,8 @@ cudaError_t launch_pre(const sgs_gaussians& g, const ViewTable& vt, const Record
     const int blocks = (int)((g.n + threads - 1) / threads);
     if (blocks > 0)
         preprocess_kernel<L, K, AX><<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.rec2, p.rect,
-                                                                 p.tiles, p.spans);
+                                                                 p.tiles, p.spans, p.sort_keys, p.sort_vals,
+                                                                 p.rv);
     return cudaGetLastError();
 }
 
