@@ -196,6 +196,25 @@ __device__ __forceinline__ bool row_span(const RowSpans& r, float px, float py, 
     return true;
 }
 
+// Asynchronous global -> shared copies of 4 or 16 bytes (16: both addresses 16-byte
+// aligned), committed as one group per async_commit; async_wait<N> waits until at most N
+// of the thread's groups are still in flight.
+__device__ __forceinline__ void async_copy4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void async_copy16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 constexpr float kSupportPower = -4.5f;     // Mahalanobis distance 3
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;

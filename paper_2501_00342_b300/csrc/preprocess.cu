@@ -339,10 +339,29 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
 #pragma unroll
         for (int c = 0; c < 3; ++c) gSig[r][c] = 0.0f;
     float gop = 0.0f;
-    for (int v = 0; v < vt.B; ++v) {
+    // the next view's tile count and 2D gradients travel to shared memory while this view's
+    // chain rule runs (double-buffered, one slot per thread)
+    __shared__ __align__(16) float4 s_g[2][3][kPreThreads];
+    __shared__ uint32_t s_t[2][kPreThreads];
+    const int tx = threadIdx.x;
+    auto prefetch = [&](int v, int b) {
         const int64_t r = (int64_t)v * g.n + i;
-        if (tiles[r] == 0u) continue;
-        const float4 g0 = grad2d[r], g1 = grad2d[R + r], g2 = grad2d[2 * R + r];
+        async_copy4(&s_t[b][tx], tiles + r);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) async_copy16(&s_g[b][c][tx], grad2d + c * R + r);
+        async_commit();
+    };
+    if (vt.B > 0) prefetch(0, 0);
+    for (int v = 0; v < vt.B; ++v) {
+        const int b = v & 1;
+        if (v + 1 < vt.B) {
+            prefetch(v + 1, b ^ 1);
+            async_wait<1>();
+        } else {
+            async_wait<0>();
+        }
+        if (s_t[b][tx] == 0u) continue;
+        const float4 g0 = s_g[b][0][tx], g1 = s_g[b][1][tx], g2 = s_g[b][2][tx];
         const View& cam = vt.v[v];
         Projected P;
         project_exact(cam, X, G, vt.inv_tile_w, vt.inv_tile_h, P);
