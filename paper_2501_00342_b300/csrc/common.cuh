@@ -72,8 +72,11 @@ __device__ __forceinline__ unsigned long long slot_load(const unsigned long long
 // slot[j * stride], j = first, first - 1, ..., 0: a slot tagged `agg` (the tile's own
 // count) is added and the walk goes on, a slot tagged `inc` (the tile's inclusive prefix)
 // is added and ends it, any other tag means the tile has not published yet and the slot is
-// polled again.  After `limit` such polls in all, SGS_ERR_TIMEOUT is set in the status
-// word and the partial sum is returned: the wait never hangs, the result is then invalid.
+// polled again.  The slots are read kLookbackWindow at a time (independent loads, one
+// round trip per window).  After `limit` polls that met an unpublished slot, SGS_ERR_TIMEOUT
+// is set in the status word and the partial sum is returned: the wait never hangs, the
+// result is then invalid.
+constexpr int kLookbackWindow = 4;
 __device__ __forceinline__ unsigned long long lookback_sum(const unsigned long long* slot, int64_t first,
                                                            size_t stride, unsigned long long value_mask,
                                                            unsigned long long tag_agg,
@@ -83,15 +86,25 @@ __device__ __forceinline__ unsigned long long lookback_sum(const unsigned long l
     uint32_t spins = 0;
     int64_t j = first;
     while (j >= 0) {
-        const unsigned long long e = slot_load(slot + (size_t)j * stride);
-        const unsigned long long tag = e & ~value_mask;
-        if (tag == tag_inc) {
-            acc += e & value_mask;
-            break;
-        } else if (tag == tag_agg) {
-            acc += e & value_mask;
-            --j;
-        } else if (++spins > limit) {
+        unsigned long long e[kLookbackWindow];
+#pragma unroll
+        for (int w = 0; w < kLookbackWindow; ++w)  // before slot 0: an inclusive prefix of 0
+            e[w] = j - w >= 0 ? slot_load(slot + (size_t)(j - w) * stride) : tag_inc;
+        int w = 0;
+        bool done = false;
+#pragma unroll
+        for (; w < kLookbackWindow; ++w) {
+            const unsigned long long tag = e[w] & ~value_mask;
+            if (tag != tag_inc && tag != tag_agg) break;  // not published yet: poll it again
+            acc += e[w] & value_mask;
+            if (tag == tag_inc) {
+                done = true;
+                break;
+            }
+        }
+        if (done) break;
+        j -= w;
+        if (w < kLookbackWindow && ++spins > limit) {
             set_status(st, SGS_ERR_TIMEOUT);
             break;
         }
