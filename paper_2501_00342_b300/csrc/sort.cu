@@ -213,6 +213,16 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
         total[i] = acc;
         tsum += acc;
     }
+    // publish this tile's per-digit counts before anything else of the tile (successors
+    // wait for them)
+    const unsigned long long tag_agg = (unsigned long long)(2 * pass + 1) << 56;
+    const unsigned long long tag_inc = (unsigned long long)(2 * pass + 2) << 56;
+    unsigned long long* row = lookback + (size_t)tile * RADIX;
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int d = threadIdx.x * DPT + i;
+        if (d < RADIX) slot_store(row + d, tile == 0 ? (tag_inc | (goff[d] + total[i])) : (tag_agg | total[i]));
+    }
     // exclusive scan of the digit totals over the CTA -> CTA-local digit starts
     {
         uint32_t x = tsum;
@@ -242,15 +252,7 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
             run += total[i];
         }
     }
-    // publish this tile's per-digit counts, then look back for the global prefixes
-    const unsigned long long tag_agg = (unsigned long long)(2 * pass + 1) << 56;
-    const unsigned long long tag_inc = (unsigned long long)(2 * pass + 2) << 56;
-    unsigned long long* row = lookback + (size_t)tile * RADIX;
-#pragma unroll
-    for (int i = 0; i < DPT; ++i) {
-        const int d = threadIdx.x * DPT + i;
-        if (d < RADIX) slot_store(row + d, tile == 0 ? (tag_inc | (goff[d] + total[i])) : (tag_agg | total[i]));
-    }
+    // look back for the global prefixes
 #pragma unroll
     for (int i = 0; i < DPT; ++i) {
         const int d = threadIdx.x * DPT + i;
