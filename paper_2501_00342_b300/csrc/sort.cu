@@ -252,19 +252,6 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
             run += total[i];
         }
     }
-    // look back for the global prefixes
-#pragma unroll
-    for (int i = 0; i < DPT; ++i) {
-        const int d = threadIdx.x * DPT + i;
-        if (d >= RADIX) continue;
-        unsigned long long prefix = goff[d];
-        if (tile != 0) {
-            // the inclusive prefix of a tile includes goff[d]
-            prefix = lookback_sum(lookback + d, (int64_t)tile - 1, RADIX, kCountMask, tag_agg, tag_inc, st);
-            slot_store(row + d, tag_inc | (prefix + total[i]));
-        }
-        sm.gbase[d] = (uint32_t)prefix;
-    }
     __syncthreads();
     // CTA-local sorted position of every item (the warp histograms are read for the last
     // time here; the staging buffer that aliases them is written after the barrier)
@@ -282,6 +269,20 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
             sm.u.stage.keys[rank[k]] = key[k];
             sm.u.stage.vals[rank[k]] = sm.vbuf[wbase + k * 32 + lane];
         }
+    }
+    // look back for the global prefixes (late: the predecessors have had the staging time
+    // to publish)
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int d = threadIdx.x * DPT + i;
+        if (d >= RADIX) continue;
+        unsigned long long prefix = goff[d];
+        if (tile != 0) {
+            // the inclusive prefix of a tile includes goff[d]
+            prefix = lookback_sum(lookback + d, (int64_t)tile - 1, RADIX, kCountMask, tag_agg, tag_inc, st);
+            slot_store(row + d, tag_inc | (prefix + total[i]));
+        }
+        sm.gbase[d] = (uint32_t)prefix;
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
