@@ -282,13 +282,13 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
             prefix = lookback_sum(lookback + d, (int64_t)tile - 1, RADIX, kCountMask, tag_agg, tag_inc, st);
             slot_store(row + d, tag_inc | (prefix + total[i]));
         }
-        sm.gbase[d] = (uint32_t)prefix;
+        sm.gbase[d] = (uint32_t)prefix - sm.digit_start[d];  // global minus CTA-local start
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
         const KeyT kk = sm.u.stage.keys[j];
         const uint32_t d = (uint32_t)(kk >> shift) & dmask;
-        const uint32_t dest = sm.gbase[d] + (j - sm.digit_start[d]);
+        const uint32_t dest = sm.gbase[d] + j;
         if (dest < m) {
             kout[dest] = kk;
             vout[dest] = sm.u.stage.vals[j];
