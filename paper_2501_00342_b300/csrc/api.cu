@@ -296,7 +296,7 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
                             &st->num_records, R, 0, 32, plan->settings.digit_bits, region<uint32_t>(plan, O_HIST),
                             region<uint32_t>(plan, O_GOFF), region<uint32_t>(plan, O_COUNTERS),
                             region<unsigned long long>(plan, O_RLB), st, stream, nullptr,
-                            /*histogram_ready=*/true));
+                            /*histogram_ready=*/true, &st->num_visible, /*drop_first=*/true));
     const uint32_t* perm = region<uint32_t>(plan, (rpasses & 1) ? O_RV1 : O_RV0);
     // (b) counts and instances in depth order
     SGS_TRY(launch_scan(rp.tiles, perm, region<uint32_t>(plan, O_OFFS), R, scan_lb, st, cap, stream));

@@ -35,7 +35,7 @@ __global__ void fill_u32_kernel(uint32_t* p, uint32_t value, size_t count) {
 // the next tile id from a counter, so every predecessor tile is already running.
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __restrict__ in,
                                                              const uint32_t* __restrict__ perm,
-                                                             const RecordValue rv,
+                                                             const RecordValue rv, const uint32_t* n_valid,
                                                              uint32_t* __restrict__ out, int64_t R,
                                                              unsigned long long* lookback,
                                                              DeviceStatus* st, int64_t capacity) {
@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
     const uint32_t tile = s_tile;
     const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
-    if (perm) {  // counts carried by the depth-sorted record values
+    if (perm) {  // counts carried by the depth-sorted record values; none past the kept ones
+        const int64_t nv = n_valid ? (int64_t)*n_valid : R;
 #pragma unroll
-        for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < R) ? rv.count(perm[base + q], in) : 0u;
+        for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < nv) ? rv.count(perm[base + q], in) : 0u;
     } else if (base + kScanItems <= R) {
         const uint4* p4 = reinterpret_cast<const uint4*>(in + base);
 #pragma unroll
@@ -141,11 +142,12 @@ __device__ __forceinline__ uint32_t same_value_lanes(uint32_t d) {
     return peers;
 }
 
-// Digit histograms of every pass of the record sort over its keys (view depth bits;
-// 0xffffffff for a record without instances), per-warp shared copies.  The low digits of
-// depth bits are spread: one shared atomic each; the high ones (exponent and top mantissa
-// bits) repeat within a warp: the warp adds each distinct digit once.  Also stores R in
-// st->num_records.
+// Digit histograms of every pass of the record sort over the keys of the records with
+// instances (view depth bits; 0xffffffff marks the others, which the sort drops), per-warp
+// shared copies.  The low digits of depth bits are spread: one shared atomic each; the
+// high ones (exponent and top mantissa bits) repeat within a warp: the warp adds each
+// distinct digit once.  Also stores R in st->num_records and adds the kept records to
+// st->num_visible (cleared before the launch).
 template <int RB>
 __global__ void __launch_bounds__(256) record_hist_kernel(const uint32_t* __restrict__ keys, int64_t R,
                                                           DeviceStatus* st, int passes, uint32_t* __restrict__ hist) {
@@ -157,23 +159,27 @@ __global__ void __launch_bounds__(256) record_hist_kernel(const uint32_t* __rest
     uint32_t* hw = h + warp * passes * RADIX;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->num_records = (uint32_t)R;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t kept_count = 0;  // warp total (same in every lane)
     // warp-uniform trip count: every lane of a warp runs the same iterations
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < R; base += stride) {
         const int64_t r = base + lane;
         const bool valid = r < R;
         const uint32_t key = valid ? keys[r] : 0xffffffffu;
-        const uint32_t live = __ballot_sync(kFullMask, valid);
+        const bool kept = key != 0xffffffffu;
+        const uint32_t live = __ballot_sync(kFullMask, kept);
+        kept_count += __popc(live);
         for (int p = 0; p < passes; ++p) {
             const uint32_t d = (key >> (p * RB)) & (RADIX - 1);
             if (2 * p < passes) {
-                if (valid) atomicAdd(&hw[p * RADIX + d], 1u);
+                if (kept) atomicAdd(&hw[p * RADIX + d], 1u);
             } else {
                 const uint32_t peers = same_value_lanes<RB>(d) & live;
-                if (valid && lane == 31 - __clz(peers)) hw[p * RADIX + d] += __popc(peers);
+                if (kept && lane == 31 - __clz(peers)) hw[p * RADIX + d] += __popc(peers);
                 __syncwarp();
             }
         }
     }
+    if (lane == 0 && kept_count) atomicAdd(&st->num_visible, kept_count);
     __syncthreads();
     for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) {
         uint32_t acc = 0;
@@ -419,7 +425,8 @@ cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* o
                         cudaStream_t s) {
     const int64_t num_tiles = (R + kScanTile - 1) / kScanTile;
     if (num_tiles == 0) return cudaSuccess;
-    scan_kernel<<<(unsigned)num_tiles, kScanThreads, 0, s>>>(tiles, perm, record_value(R), offsets, R,
+    scan_kernel<<<(unsigned)num_tiles, kScanThreads, 0, s>>>(tiles, perm, record_value(R),
+                                                             perm ? &st->num_visible : nullptr, offsets, R,
                                                              scan_lookback, st, capacity);
     return cudaGetLastError();
 }
@@ -462,6 +469,7 @@ cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st
     int passes, rb;
     sort_digit_plan(0, 32, digit_bits, &passes, &rb);
     cudaError_t e = launch_fill_u32(hist, 0u, (size_t)passes << rb, s);
+    if (e == cudaSuccess) e = launch_fill_u32(&st->num_visible, 0u, 1, s);
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int64_t want = (R + threads - 1) / threads;

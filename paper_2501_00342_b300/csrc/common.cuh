@@ -43,6 +43,7 @@ struct DeviceStatus {
     unsigned long long m;  // exact instance count M
     uint32_t tile_counter[16];  // dynamic tile ids: [0] scan, [1..] sort passes
     uint32_t num_records;       // R, the length of the record sort
+    uint32_t num_visible;       // records with instances: the record sort keeps only these
 };
 
 // Correctly rounded single-precision operations that the compiler may not fuse or

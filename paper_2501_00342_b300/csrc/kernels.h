@@ -70,8 +70,9 @@ cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n,
 // R in st->num_records.
 cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st, int digit_bits, uint32_t* hist,
                                cudaStream_t s);
-// Exclusive scan of the counts of the depth-sorted record values perm (RecordValue), or of
-// tiles[j] when perm is null.
+// Exclusive scan of the counts of the depth-sorted record values perm (RecordValue; the
+// positions at and past st->num_visible, which the record sort left unwritten, count 0),
+// or of tiles[j] when perm is null.
 cudaError_t launch_scan(const uint32_t* tiles, const uint32_t* perm, uint32_t* offsets, int64_t R,
                         unsigned long long* scan_lookback, DeviceStatus* st, int64_t capacity,
                         cudaStream_t s);
@@ -107,11 +108,15 @@ cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long
                         uint32_t* hist, uint32_t* goff, uint32_t* counters,
                         unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
                         cudaEvent_t hist_end, bool histogram_ready = false);
-// The same sort for 32-bit keys (key_bits <= 32; 16 bytes moved per pair and pass).
+// The same sort for 32-bit keys (key_bits <= 32; 16 bytes moved per pair and pass).  With
+// drop_first the first pass removes the pairs whose key is 0xffffffff (stable for the
+// rest); the hist must then count only the kept keys and m_rest holds their number, the
+// length of every later pass.
 cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* m_ptr,
                         int64_t capacity, int first_bit, int key_bits, int digit_bits, uint32_t* hist,
                         uint32_t* goff, uint32_t* counters, unsigned long long* lookback, DeviceStatus* st,
-                        cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready = false);
+                        cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready = false,
+                        const uint32_t* m_rest = nullptr, bool drop_first = false);
 int sort_passes(int key_bits, int digit_bits);
 int sort_passes(int first_bit, int key_bits, int digit_bits);
 

@@ -134,10 +134,11 @@ struct OnesweepSmem {
     uint32_t digit_start[RADIX];
     uint32_t gbase[RADIX];
     uint32_t wsum[WARPS];
+    uint32_t nvalid;  // items of the tile that are kept
     uint32_t tile;
 };
 
-template <typename KeyT, int RB>
+template <typename KeyT, int RB, bool DROP>
 __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesweep_kernel(
     const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* m_ptr, const uint32_t* __restrict__ goff,
@@ -180,7 +181,9 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t e = wbase + k * 32 + lane;
-        const uint32_t d = e < count ? (uint32_t)(key[k] >> shift) & dmask : RADIX;
+        // items past the end, and (drop) all-ones keys, go to the sentinel bucket: not kept
+        const bool keep = e < count && !(DROP && key[k] == (KeyT)~(KeyT)0);
+        const uint32_t d = keep ? (uint32_t)(key[k] >> shift) & dmask : RADIX;
         // alternate the two ways of finding the lanes with the same digit so that the
         // ballots (ALU pipe) and match-any (shared pipe) run side by side
         const uint32_t peers = (k & 1) ? digit_peers<RB + 1>(d) : __match_any_sync(kFullMask, d);
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
                 if (lane >= o) inc += y;
             }
             if (lane < WARPS) sm.wsum[lane] = inc - w;
+            if (lane == WARPS - 1) sm.nvalid = inc;
         }
         __syncthreads();
         uint32_t run = x - tsum + sm.wsum[warp];
@@ -259,7 +263,8 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t e = wbase + k * 32 + lane;
         const uint32_t d = (uint32_t)(key[k] >> shift) & dmask;
-        rank[k] = e < count ? sm.digit_start[d] + sm.u.warp_hist[warp][d] + rank[k] : 0xffffffffu;
+        const bool keep = e < count && !(DROP && key[k] == (KeyT)~(KeyT)0);
+        rank[k] = keep ? sm.digit_start[d] + sm.u.warp_hist[warp][d] + rank[k] : 0xffffffffu;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -285,7 +290,8 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
         sm.gbase[d] = (uint32_t)prefix - sm.digit_start[d];  // global minus CTA-local start
     }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < count; j += kSortThreads) {
+    const uint32_t nvalid = sm.nvalid;
+    for (uint32_t j = threadIdx.x; j < nvalid; j += kSortThreads) {
         const KeyT kk = sm.u.stage.keys[j];
         const uint32_t d = (uint32_t)(kk >> shift) & dmask;
         const uint32_t dest = sm.gbase[d] + j;
@@ -317,7 +323,8 @@ template <typename KeyT, int RB>
 cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
                       const uint32_t* m_ptr, int64_t capacity, int first_bit, int key_bits, uint32_t* hist,
                       uint32_t* goff, uint32_t* counters, unsigned long long* lookback,
-                      DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready) {
+                      DeviceStatus* st, cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready,
+                      const uint32_t* m_rest, bool drop_first) {
     constexpr int RADIX = 1 << RB;
     const int passes = (key_bits - first_bit + RB - 1) / RB;
     cudaError_t e;
@@ -344,17 +351,25 @@ cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
     histogram_scan_kernel<RB><<<passes, RADIX < 32 ? 32 : (RADIX > 1024 ? 1024 : RADIX), 0, s>>>(hist, goff);
     if (hist_end && (e = record_probe(hist_end, s)) != cudaSuccess) return e;
     const size_t smem = sizeof(OnesweepSmem<KeyT, RB>);
-    if ((e = cudaFuncSetAttribute(onesweep_kernel<KeyT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(onesweep_kernel<KeyT, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
+        return e;
+    if (drop_first && (e = cudaFuncSetAttribute(onesweep_kernel<KeyT, RB, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     for (int p = 0; p < passes; ++p) {
         const KeyT* kin = (p & 1) ? k1 : k0;
         const uint32_t* vin = (p & 1) ? v1 : v0;
         KeyT* kout = (p & 1) ? k0 : k1;
         uint32_t* vout = (p & 1) ? v0 : v1;
-        onesweep_kernel<KeyT, RB><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-            kin, vin, kout, vout, m_ptr, goff + p * RADIX, lookback, counters + p, first_bit + p * RB,
-            pass_width(p, RB, first_bit, key_bits), p, st);
+        const uint32_t* mp = p > 0 && m_rest ? m_rest : m_ptr;
+        const uint32_t width = pass_width(p, RB, first_bit, key_bits);
+        if (p == 0 && drop_first)
+            onesweep_kernel<KeyT, RB, true><<<(unsigned)tiles, kSortThreads, smem, s>>>(
+                kin, vin, kout, vout, mp, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, width, p, st);
+        else
+            onesweep_kernel<KeyT, RB, false><<<(unsigned)tiles, kSortThreads, smem, s>>>(
+                kin, vin, kout, vout, mp, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, width, p, st);
     }
     return cudaGetLastError();
 }
@@ -388,14 +403,15 @@ template <typename KeyT>
 cudaError_t launch_sort_t(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* m_ptr, int64_t capacity,
                           int first_bit, int key_bits, int digit_bits, uint32_t* hist, uint32_t* goff,
                           uint32_t* counters, unsigned long long* lookback, DeviceStatus* st, cudaStream_t s,
-                          cudaEvent_t hist_end, bool histogram_ready) {
+                          cudaEvent_t hist_end, bool histogram_ready, const uint32_t* m_rest = nullptr,
+                          bool drop_first = false) {
     int passes, rb;
     sort_digit_plan(first_bit, key_bits, digit_bits, &passes, &rb);
     switch (rb) {
 #define SGS_SORT(RB)                                                                                          \
     case RB:                                                                                                  \
         return sort_impl<KeyT, RB>(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, hist, goff, counters, \
-                                   lookback, st, s, hist_end, histogram_ready);
+                                   lookback, st, s, hist_end, histogram_ready, m_rest, drop_first);
         SGS_SORT(4) SGS_SORT(5) SGS_SORT(6) SGS_SORT(7) SGS_SORT(8) SGS_SORT(9) SGS_SORT(10)
 #undef SGS_SORT
         default: return cudaErrorInvalidValue;
@@ -423,10 +439,11 @@ cudaError_t launch_sort(unsigned long long* k0, uint32_t* v0, unsigned long long
 cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* m_ptr,
                         int64_t capacity, int first_bit, int key_bits, int digit_bits, uint32_t* hist,
                         uint32_t* goff, uint32_t* counters, unsigned long long* lookback, DeviceStatus* st,
-                        cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready) {
+                        cudaStream_t s, cudaEvent_t hist_end, bool histogram_ready, const uint32_t* m_rest,
+                        bool drop_first) {
     if (key_bits > 32) return cudaErrorInvalidValue;
     return launch_sort_t(k0, v0, k1, v1, m_ptr, capacity, first_bit, key_bits, digit_bits, hist, goff, counters,
-                         lookback, st, s, hist_end, histogram_ready);
+                         lookback, st, s, hist_end, histogram_ready, m_rest, drop_first);
 }
 
 cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
