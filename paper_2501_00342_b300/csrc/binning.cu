@@ -121,12 +121,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
     }
 }
 
-__device__ __forceinline__ uint32_t lanemask_lt() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
 // Keys of the record sort: the float bits of the view depth of a record with instances
 // (depth > near > 0, so the bits order like the values), 0xffffffff for the others.
 // The lanes holding the same value d (d < 2^BITS), from one ballot per bit.

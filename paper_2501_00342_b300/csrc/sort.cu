@@ -1,14 +1,16 @@
-// Stage (c): stable LSD radix sort of (uint64 key, uint32 value) pairs, onesweep style.
+// Stage (c): stable LSD radix sort of (uint64 or uint32 key, uint32 value) pairs, onesweep
+// style.
 //
 //   1. digit histograms of every pass at once (one read of the keys), unless the caller
 //      counted them already;
 //   2. an exclusive scan per pass turns them into global bucket offsets;
-//   3. per pass, one kernel: each CTA takes the next tile of kSortTile keys (dynamic tile
-//      id, so every earlier tile is already running), ranks its keys by digit with warp
-//      match-any (stable: input order within the tile), publishes its per-digit counts
-//      and resolves its global per-digit offsets by decoupled look-back over the earlier
-//      tiles, then scatters through shared memory so that each digit's run leaves the CTA
-//      as consecutive stores.
+//   3. per pass, one kernel: each CTA takes the next tile of keys (dynamic tile id, so every
+//      earlier tile is already running), ranks its keys by digit within each warp (stable:
+//      input order within the tile), publishes its per-digit counts, scans them into
+//      CTA-local digit starts, stages the tile in shared memory in digit order, resolves
+//      its global per-digit offsets by decoupled look-back over the earlier tiles, and
+//      writes each digit's run as consecutive stores.  Optionally the first pass drops the
+//      pairs whose key is all ones (the records without instances of the record sort).
 // Digits are 4..10 bits; a sort of n bits uses the fewest passes of at most the requested
 // width and the narrowest uniform width for that many passes (17 bits: 2 passes of 9).
 // Look-back words are 64 bits: an 8-bit tag (2p+1 aggregate, 2p+2 inclusive for pass p)
@@ -24,8 +26,6 @@ namespace {
 // The lanes of the warp whose value d equals this lane's, from one ballot per bit of d
 // (d < 2^BITS).  Same result as a match-any, without its long-latency shared-pipe
 // instruction: a ballot per bit and one logic op per bit.
-constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
-
 template <int BITS>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
     uint32_t peers = kFullMask;
