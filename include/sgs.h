@@ -241,7 +241,8 @@ typedef enum {
     SGS_REGION_PIX_T = 12,  /* float[num_pixels]: final transmittance */
     SGS_REGION_PIX_LAST = 13, /* uint32[num_pixels]: 1 + position of the last contributor
                                  in the tile's list (0: none) */
-    SGS_REGION_GRAD2D = 14, /* float4[3][R]: dL/d(px, py, A, B), (C, opacity, r, g), (b) */
+    SGS_REGION_GRAD2D = 14, /* float4[2][R] then float[R]: dL/d(px, py, A, B), (C, opacity, r, g),
+                               then dL/db */
     SGS_REGION_PIX_COUNT = 15, /* uint2[num_pixels]: list entries the pixel evaluated, and
                                   how many of them it blended */
     SGS_REGION_COUNT = 16

@@ -233,7 +233,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_V0] = sz[O_V1] = 4 * cap;
     sz[O_RANGES] = 8 * (size_t)tiles;
     sz[O_PIXT] = sz[O_PIXLAST] = 4 * (size_t)pixels;
-    sz[O_GRAD2D] = 48 * (size_t)R;
+    sz[O_GRAD2D] = 36 * (size_t)R;  // float4[2][R], float[R]
     sz[O_PIXCOUNT] = 8 * (size_t)pixels;
     sz[O_SPANS] = 64 * (size_t)R;
     sz[O_SCANLB] = 8 * (size_t)((R + kScanTile - 1) / kScanTile + 1);

@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                     const float u3 = __shfl_down_sync(kFullMask, s8, 12);
                     const uint32_t id = sid[j];
                     if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
-                    if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
+                    if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R) + id, s9);
                 }
             }
         }
@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(512) blend_pair_backward_kernel(
                 const float u3 = __shfl_down_sync(kFullMask, s8, 12);
                 const uint32_t id = sid[j];
                 if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
-                if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R + id), s9);
+                if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R) + id, s9);
             }
         }
     }
@@ -875,10 +875,10 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
 
 cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
-    // one plain clear of all three planes streams at full write bandwidth; skipping the
-    // culled records saves little and costs a dependent load per record
+    // one plain clear of the two float4 planes and the float plane streams at full write
+    // bandwidth; skipping the culled records saves little and costs a dependent load each
     (void)tiles;
-    return cudaMemsetAsync(grad2d, 0, (size_t)R * 3 * sizeof(float4), s);
+    return cudaMemsetAsync(grad2d, 0, (size_t)R * (2 * sizeof(float4) + sizeof(float)), s);
 }
 
 cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float* loss,

@@ -130,6 +130,8 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                   const float* pix_T, const uint32_t* pix_last,
                                   const float* dL_drgb, float4* grad2d, int64_t R,
                                   const DeviceStatus* st, cudaStream_t s);
+// grad2d: per record dL/d(px, py, A, B) and dL/d(C, opacity, r, g) as float4[2][R], then
+// dL/db as float[R] (from grad2d + 2 R).
 cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s);
 
 // training: fused Adam step over all parameter planes

@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         const int64_t r = (int64_t)v * g.n + i;
         async_copy4(&s_t[b][tx], tiles + r);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) async_copy16(&s_g[b][c][tx], grad2d + c * R + r);
+        for (int c = 0; c < 2; ++c) async_copy16(&s_g[b][c][tx], grad2d + c * R + r);
+        async_copy4(&s_g[b][2][tx].x, reinterpret_cast<const float*>(grad2d + 2 * R) + r);
         async_commit();
     };
     if (vt.B > 0) prefetch(0, 0);
