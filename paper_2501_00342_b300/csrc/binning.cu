@@ -244,11 +244,13 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
         // the record's count from the scan: the difference of consecutive offsets
         const uint32_t m_end = st->m_clamped;
         const uint32_t o = j < R ? offsets[j] : m_end;
+        // loaded together with the offsets (past the kept records it is stale and unused)
+        const uint32_t pv = j < R ? perm[j] : 0u;
         uint32_t o_next = __shfl_down_sync(kFullMask, o, 1);
         if (lane == 31) o_next = base + 32 < R ? offsets[base + 32] : m_end;
         const uint32_t cnt = overflow ? 0u : o_next - o;
         if (!__ballot_sync(kFullMask, cnt != 0u)) continue;
-        const uint32_t r = cnt ? rv.id(perm[j]) : 0u;
+        const uint32_t r = cnt ? rv.id(pv) : 0u;
         uint32_t tbase = 0, hdr = 0;
         int TW = 0;
         if (cnt) {
