@@ -392,6 +392,22 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
     }
 }
 
+// Keys of the blend's tile order: tiles with longer instance lists first, so that the
+// CTAs of the most expensive tiles start early and the launch does not end on a few long
+// tiles.  key = 0xffff - min(length / 4, 0xffff) (ascending key = descending length),
+// value = the tile id; also stores the tile count in st->num_tiles.
+__global__ void __launch_bounds__(256) tile_order_keys_kernel(const uint2* __restrict__ ranges, uint32_t num_tiles,
+                                                              uint32_t* __restrict__ keys,
+                                                              uint32_t* __restrict__ vals, DeviceStatus* st) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->num_tiles = num_tiles;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        keys[t] = 0xffffu - min(len >> 2, 0xffffu);
+        vals[t] = t;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_lookback_selftest(const unsigned long long* slots, int64_t n, unsigned long long* sum,
@@ -445,6 +461,21 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_tile_order(const uint2* ranges, int64_t num_tiles, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                              uint32_t* v1, uint32_t* hist, uint32_t* goff, uint32_t* counters,
+                              unsigned long long* lookback, DeviceStatus* st, cudaStream_t s) {
+    if (num_tiles == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t want = (num_tiles + threads - 1) / threads;
+    tile_order_keys_kernel<<<(unsigned)(want < 148 * 8 ? want : 148 * 8), threads, 0, s>>>(
+        ranges, (uint32_t)num_tiles, k0, v0, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // 16-bit keys: two passes of 8 bits, the order ends in (k0, v0)
+    return launch_sort(k0, v0, k1, v1, &st->num_tiles, num_tiles, 0, 16, 8, hist, goff, counters, lookback, st, s,
+                       nullptr, false);
 }
 
 cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t capacity,

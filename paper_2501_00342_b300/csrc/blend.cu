@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
     const int words = (batch + 31) >> 5;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
-    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const uint32_t tile = vt.order ? vt.order[blockIdx.x] : blockIdx.x;
+    const TileCoord tc = tile_of(vt, tile);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<PPT>(vt);
     const int lx = wb.x0 + (threadIdx.x & 7), ly = wb.y0 + ((threadIdx.x >> 3) & 3);
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         P[q].done = !P[q].inside;
         all_done &= P[q].done;
     }
-    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    const uint2 range = clamp_range(ranges[tile], st->m_clamped);
     const int n = (int)(range.y - range.x);
     for (int base = 0; base < n; base += batch) {
         if (__syncthreads_count(!all_done) == 0) break;
@@ -340,7 +341,8 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
     const int words = (batch + 31) >> 5;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairs) * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
-    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const uint32_t tile = vt.order ? vt.order[blockIdx.x] : blockIdx.x;
+    const TileCoord tc = tile_of(vt, tile);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<2>(vt);
     const int x = tc.tx * vt.tile_w + wb.x0 + (threadIdx.x & 7);
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
     uint32_t last0 = 0, last1 = 0, ev0 = 0, ev1 = 0, ct0 = 0, ct1 = 0;
     bool done0 = !in0, done1 = !in1;
     bool all_done = done0 && done1;
-    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    const uint2 range = clamp_range(ranges[tile], st->m_clamped);
     const int n = (int)(range.y - range.x);
     for (int base = 0; base < n; base += batch) {
         if (__syncthreads_count(!all_done) == 0) break;
@@ -481,11 +483,12 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     uint32_t* bits = sid + batch;
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
     __shared__ uint32_t s_max_last;
-    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const uint32_t tile = vt.order ? vt.order[blockIdx.x] : blockIdx.x;
+    const TileCoord tc = tile_of(vt, tile);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<PPT>(vt);
     const int lx = wb.x0 + (threadIdx.x & 7), ly = wb.y0 + ((threadIdx.x >> 3) & 3);
-    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    const uint2 range = clamp_range(ranges[tile], st->m_clamped);
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
     const int64_t hw = (int64_t)cam.W * cam.H;
@@ -622,12 +625,13 @@ __global__ void __launch_bounds__(512) blend_pair_backward_kernel(
     uint32_t* bits = sid + batch;
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
     __shared__ uint32_t s_max_last;
-    const TileCoord tc = tile_of(vt, blockIdx.x);
+    const uint32_t tile = vt.order ? vt.order[blockIdx.x] : blockIdx.x;
+    const TileCoord tc = tile_of(vt, tile);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<2>(vt);
     const int x = tc.tx * vt.tile_w + wb.x0 + (threadIdx.x & 7);
     const int y0 = tc.ty * vt.tile_h + wb.y0 + ((threadIdx.x >> 3) & 3), y1 = y0 + 4;
-    const uint2 range = clamp_range(ranges[blockIdx.x], st->m_clamped);
+    const uint2 range = clamp_range(ranges[tile], st->m_clamped);
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
     const int64_t hw = (int64_t)cam.W * cam.H;

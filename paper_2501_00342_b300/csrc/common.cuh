@@ -33,6 +33,7 @@ struct ViewTable {
     int32_t fwd_ppt, bwd_ppt;      // pixels per thread of the blend kernels
     int32_t count_pairs;           // the forward blend writes per-pixel pair counts
     int64_t num_tiles;
+    const uint32_t* order;         // the blend's tile order (CTA b renders tile order[b]), or null
     View v[SGS_MAX_VIEWS];
 };
 
@@ -44,6 +45,7 @@ struct DeviceStatus {
     uint32_t tile_counter[16];  // dynamic tile ids: [0] scan, [1..] sort passes
     uint32_t num_records;       // R, the length of the record sort
     uint32_t num_visible;       // records with instances: the record sort keeps only these
+    uint32_t num_tiles;         // length of the tile-order sort
 };
 
 // Correctly rounded single-precision operations that the compiler may not fuse or
