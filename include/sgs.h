@@ -153,7 +153,7 @@ typedef struct {
     int32_t stage; /* last stage run on the bound workspace: 1 preprocess, 2 bin/sort,
                       3 render; a stage call before its predecessor returns SGS_ERR_INVALID */
     cudaEvent_t* events; /* optional caller-owned array[SGS_EV_COUNT] (see sgs_set_events) */
-    size_t offsets[32]; /* byte offsets of the workspace regions */
+    size_t offsets[40]; /* byte offsets of the workspace regions */
     size_t workspace_bytes;
     void* workspace; /* bound by sgs_preprocess() */
 } sgs_plan;

@@ -79,7 +79,7 @@ class Plan(C.Structure):
                 ("tile_base", C.c_int64 * (MAX_VIEWS + 1)), ("pixel_base", C.c_int64 * (MAX_VIEWS + 1)),
                 ("num_records", C.c_int64), ("num_tiles", C.c_int64), ("num_pixels", C.c_int64),
                 ("instance_capacity", C.c_int64), ("key_bits", C.c_int32), ("sort_passes", C.c_int32),
-                ("stage", C.c_int32), ("events", C.c_void_p), ("offsets", C.c_size_t * 32),
+                ("stage", C.c_int32), ("events", C.c_void_p), ("offsets", C.c_size_t * 40),
                 ("workspace_bytes", C.c_size_t), ("workspace", C.c_void_p)]
 
 

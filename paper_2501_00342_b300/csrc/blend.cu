@@ -203,6 +203,23 @@ __device__ __forceinline__ uint2 clamp_range(uint2 r, uint32_t m) {
     return r;
 }
 
+// The backward's tile-order key of this CTA's tile: the largest position of a last
+// contributor over the tile's pixels (the reverse walk starts there), as
+// 0xffff - min(top / 4, 0xffff) so that an ascending sort starts the longest walks first.
+// Block-collective, at the end of a forward kernel (every thread reaches it).
+__device__ __forceinline__ void write_backward_key(const ViewTable& vt, uint32_t tile, uint32_t my_last) {
+    __shared__ uint32_t s_top;
+    const uint32_t wmax = __reduce_max_sync(kFullMask, my_last);
+    if (threadIdx.x == 0) s_top = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_top, wmax);
+    __syncthreads();
+    if (threadIdx.x == 0 && vt.bwd_keys) {
+        vt.bwd_keys[tile] = 0xffffu - min(s_top >> 2, 0xffffu);
+        vt.bwd_vals[tile] = tile;
+    }
+}
+
 // Per-pixel state of the forward walk.
 struct FwdPixel {
     float pxc, pyc;  // pixel centre
@@ -313,6 +330,10 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         pix_last[cam.pixel_base + pi] = p.last;
         if (COUNT) pix_count[cam.pixel_base + pi] = make_uint2(p.evaluated, p.contributed);
     }
+    uint32_t my_last = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) my_last = max(my_last, P[q].last);
+    write_backward_key(vt, tile, my_last);
 }
 
 // The forward with two pixels per thread in packed pairs: a lane's pixels share their
@@ -422,6 +443,7 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
         pix_last[cam.pixel_base + pi] = q ? last1 : last0;
         if (COUNT) pix_count[cam.pixel_base + pi] = q ? make_uint2(ev1, ct1) : make_uint2(ev0, ct0);
     }
+    write_backward_key(vt, tile, max(last0, last1));
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

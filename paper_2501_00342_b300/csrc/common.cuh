@@ -34,6 +34,8 @@ struct ViewTable {
     int32_t count_pairs;           // the forward blend writes per-pixel pair counts
     int64_t num_tiles;
     const uint32_t* order;         // the blend's tile order (CTA b renders tile order[b]), or null
+    uint32_t* bwd_keys;            // the forward's per-tile keys of the backward's tile order
+    uint32_t* bwd_vals;            // and the tile ids they sort (or null: not written)
     View v[SGS_MAX_VIEWS];
 };
 
