@@ -174,23 +174,78 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
 // duplicate kernel reads (16 words): word 0 = first row | rows << 16; words 1..15 = first
 // column | (tiles in the earlier rows) << 16 per row.  More than kSpanRows rows or more
 // than 65535 tiles mark a table the kernel recomputes instead.  The table is written to
-// table[k * stride] (a thread's column of a shared-memory array).
-__device__ __forceinline__ uint32_t count_tiles(const Projected& P, const View& cam, const ViewTable& vt,
-                                                uint32_t* table, int stride) {
-    const RowSpans rs = row_setup(P.px, P.py, P.A, P.B, P.C, vt.inv_tile_h, cam.tiles_y);
-    uint32_t hits = 0;
-    for (int ty = rs.ty0; ty <= rs.ty1; ++ty) {
-        int a0 = 0, a1 = -1;
-        row_span(rs, P.px, P.py, P.B, ty, vt.inv_tile_w, vt.tile_h, cam.tiles_x, a0, a1);
-        const int k = ty - rs.ty0;
-        if (k < kSpanRows) table[(1 + k) * stride] = (uint32_t)(a1 >= a0 ? a0 : 0) | (min(hits, 0xffffu) << 16);
-        if (a1 >= a0) hits += (uint32_t)(a1 - a0 + 1);
+// table[k * stride] (a thread's column of a shared-memory array).  Done for the 32 records
+// of a warp at once (warp-collective; lanes whose record is not visible pass
+// visible = false and get 0).  The (record, row) pairs of the warp are
+// dealt out 32 at a time, so a lane with many rows does not hold up the warp: each pair's
+// lane finds its record by a 5-step search of the inclusive scan of the row counts, takes
+// the record's ellipse from that lane by shuffles and runs the same row_span (same bits
+// as count_tiles).  Rows are written into the owner's table as first column | tiles in
+// the row << 16 and turned into first column | tiles in the earlier rows << 16 by the
+// owner afterwards.  s_hits: one counter per thread of the block (shared memory).
+__device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool visible, const View& cam,
+                                                     const ViewTable& vt, uint32_t* table, int stride,
+                                                     uint32_t* s_hits) {
+    const int lane = threadIdx.x & 31;
+    RowSpans rs;
+    rs.ok = false;
+    rs.ty0 = 0;
+    rs.ty1 = -1;
+    if (visible) rs = row_setup(P.px, P.py, P.A, P.B, P.C, vt.inv_tile_h, cam.tiles_y);
+    const int rows = rs.ok ? rs.ty1 - rs.ty0 + 1 : 0;
+    s_hits[threadIdx.x] = 0u;
+    int incl = rows;  // inclusive scan of the rows over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += y;
     }
-    const int rows = rs.ty1 - rs.ty0 + 1;
-    for (int k = rows < 0 ? 0 : rows; k < kSpanRows; ++k) table[(1 + k) * stride] = 0xffff0000u;
+    const int total = __shfl_sync(kFullMask, incl, 31);
+    __syncwarp();
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        const int e = e0 + lane;
+        int q = 0;  // records whose rows end at or before pair e
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1) {
+            const int v = __shfl_sync(kFullMask, incl, q + b - 1);
+            if (v <= e) q += b;
+        }
+        q = min(q, 31);
+        const int first = __shfl_sync(kFullMask, incl - rows, q);
+        RowSpans rq;
+        rq.ok = true;
+        rq.ty0 = __shfl_sync(kFullMask, rs.ty0, q);
+        rq.ty1 = __shfl_sync(kFullMask, rs.ty1, q);
+        rq.ex = __shfl_sync(kFullMask, rs.ex, q);
+        rq.ey = __shfl_sync(kFullMask, rs.ey, q);
+        rq.dyr = __shfl_sync(kFullMask, rs.dyr, q);
+        rq.det = __shfl_sync(kFullMask, rs.det, q);
+        rq.invA = __shfl_sync(kFullMask, rs.invA, q);
+        rq.Ak = __shfl_sync(kFullMask, rs.Ak, q);
+        const float px = __shfl_sync(kFullMask, P.px, q), py = __shfl_sync(kFullMask, P.py, q);
+        const float B = __shfl_sync(kFullMask, P.B, q);
+        if (e < total) {
+            const int k = e - first;
+            int a0 = 0, a1 = -1;
+            row_span(rq, px, py, B, rq.ty0 + k, vt.inv_tile_w, vt.tile_h, cam.tiles_x, a0, a1);
+            const uint32_t len = a1 >= a0 ? (uint32_t)(a1 - a0 + 1) : 0u;
+            const int owner = (int)(threadIdx.x & ~31u) + q;
+            if (k < kSpanRows) table[(int)(q - lane) + (1 + k) * stride] = (uint32_t)(len ? a0 : 0) | (len << 16);
+            if (len) atomicAdd(&s_hits[owner], len);
+        }
+    }
+    __syncwarp();
+    uint32_t hits = 0;
+    for (int k = 0; k < min(rows, kSpanRows); ++k) {
+        const uint32_t w = table[(1 + k) * stride];
+        table[(1 + k) * stride] = (w & 0xffffu) | (min(hits, 0xffffu) << 16);
+        hits += w >> 16;
+    }
+    hits = s_hits[threadIdx.x];
+    for (int k = rows; k < kSpanRows; ++k) table[(1 + k) * stride] = 0xffff0000u;
     const bool fits = rows <= kSpanRows && hits <= 0xffffu;
     table[0] = (uint32_t)rs.ty0 | ((fits ? (uint32_t)rows : kSpanRowsOverflow) << 16);
-    return hits;
+    return rs.ok ? hits : 0u;
 }
 
 __device__ __forceinline__ void view_direction(const View& cam, const float X[3], float d[3],
@@ -268,8 +323,13 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
     using CS = ColourShared<L, K, AX>;
     __shared__ float s_colour[CS::COUNT * kPreThreads];
     __shared__ uint32_t s_table[16 * kPreThreads];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    __shared__ uint32_t s_hits[kPreThreads];
+    // the lanes past n stay (the row counting is warp-collective) on a copy of the last
+    // Gaussian and write nothing
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < g.n;
+    if (__all_sync(kFullMask, !live)) return;  // whole warps past n leave
+    const int64_t i = live ? i0 : g.n - 1;
     const int64_t S = g.stride;
     const float X[3] = {__ldg(g.mean + i), __ldg(g.mean + S + i), __ldg(g.mean + 2 * S + i)};
     const float opacity = __ldg(g.opacity + i);
@@ -283,7 +343,8 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         const int64_t r = (int64_t)v * g.n + i;
         Projected P;
         project_exact(cam, X, G, vt.inv_tile_w, vt.inv_tile_h, P);
-        const uint32_t hits = P.visible ? count_tiles(P, cam, vt, table, kPreThreads) : 0u;
+        const uint32_t hits = count_tiles_warp(P, live && P.visible, cam, vt, table, kPreThreads, s_hits);
+        if (!live) continue;
         // the record sort's pair: depth bits (depth > near > 0 orders like the floats)
         sort_keys[r] = hits ? __float_as_uint(P.t[2]) : 0xffffffffu;
         sort_vals[r] = rv.pack((uint32_t)r, hits);
