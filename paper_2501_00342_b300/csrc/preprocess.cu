@@ -176,13 +176,13 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
 // than 65535 tiles mark a table the kernel recomputes instead.  The table is written to
 // table[k * stride] (a thread's column of a shared-memory array).  Done for the 32 records
 // of a warp at once (warp-collective; lanes whose record is not visible pass
-// visible = false and get 0).  The (record, row) pairs of the warp are
-// dealt out 32 at a time, so a lane with many rows does not hold up the warp: each pair's
-// lane finds its record by a 5-step search of the inclusive scan of the row counts, takes
-// the record's ellipse from that lane by shuffles and runs the same row_span (same bits
-// as count_tiles).  Rows are written into the owner's table as first column | tiles in
-// the row << 16 and turned into first column | tiles in the earlier rows << 16 by the
-// owner afterwards.  s_hits: one counter per thread of the block (shared memory).
+// visible = false and get 0).  The (record, row) pairs of the warp are dealt out 32 at a
+// time, so a lane with many rows does not hold up the warp: each pair's lane finds its
+// record by a 5-step search of the inclusive scan of the row counts, takes the record's
+// ellipse from that lane by shuffles and runs row_span on it (the same bits as the
+// record's own lane would get).  Rows are written into the owner's table as first column |
+// tiles in the row << 16 and turned into first column | tiles in the earlier rows << 16
+// by the owner afterwards.  s_hits: one counter per thread of the block (shared memory).
 __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool visible, const View& cam,
                                                      const ViewTable& vt, uint32_t* table, int stride,
                                                      uint32_t* s_hits) {
