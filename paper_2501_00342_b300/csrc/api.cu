@@ -16,8 +16,7 @@ namespace {
 enum Region {
     O_STATUS, O_REC0, O_REC1, O_REC2, O_RECT, O_TILES, O_OFFS, O_K0, O_V0, O_K1, O_V1,
     O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SPANS, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
-    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_TK0, O_TV0, O_TK1, O_TV1, O_TLB,
-    O_BK, O_BV, O_END
+    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_TORDER, O_TTOP, O_BORDER, O_END
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -92,9 +91,8 @@ ViewTable view_table(const sgs_plan* p) {
     vt.bwd_ppt = resolved_pixels(p->settings.bwd_pixels);
     vt.count_pairs = p->settings.count_pairs ? 1 : 0;
     vt.num_tiles = p->num_tiles;
-    vt.order = p->workspace ? region<uint32_t>(p, O_TV0) : nullptr;
-    vt.bwd_keys = p->workspace ? region<uint32_t>(p, O_BK) : nullptr;
-    vt.bwd_vals = p->workspace ? region<uint32_t>(p, O_BV) : nullptr;
+    vt.order = p->workspace ? region<uint32_t>(p, O_TORDER) : nullptr;
+    vt.tile_top = p->workspace ? region<uint32_t>(p, O_TTOP) : nullptr;
     for (int v = 0; v < p->B; ++v) {
         const sgs_camera& c = p->cams[v];
         View& w = vt.v[v];
@@ -250,9 +248,8 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_RK0] = sz[O_RK1] = 4 * (size_t)R;  // depth bits
     sz[O_RV0] = sz[O_RV1] = 4 * (size_t)R;
     sz[O_RLB] = 8 * sort_lookback_entries(R, rrb);
-    sz[O_TK0] = sz[O_TV0] = sz[O_TK1] = sz[O_TV1] = 4 * (size_t)tiles;  // blend tile order
-    sz[O_TLB] = 8 * sort_lookback_entries(tiles, 8);
-    sz[O_BK] = sz[O_BV] = 4 * (size_t)tiles;  // backward tile order (keys from the forward)
+    // the blend's tile orders and the forward's per-tile last contributor
+    sz[O_TORDER] = sz[O_TTOP] = sz[O_BORDER] = 4 * (size_t)tiles;
     size_t off = 0;
     for (int k = 0; k < O_END; ++k) {
         plan->offsets[k] = off;
@@ -332,11 +329,8 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));
     SGS_TRY(launch_ranges(region<uint32_t>(plan, kreg), st, cap, plan->num_tiles,
                           region<uint2>(plan, O_RANGES), stream));
-    SGS_TRY(launch_tile_order(region<uint2>(plan, O_RANGES), plan->num_tiles, region<uint32_t>(plan, O_TK0),
-                              region<uint32_t>(plan, O_TV0), region<uint32_t>(plan, O_TK1),
-                              region<uint32_t>(plan, O_TV1), region<uint32_t>(plan, O_HIST),
-                              region<uint32_t>(plan, O_GOFF), region<uint32_t>(plan, O_COUNTERS),
-                              region<unsigned long long>(plan, O_TLB), st, stream));
+    SGS_TRY(launch_tile_order(region<uint2>(plan, O_RANGES), nullptr, plan->num_tiles,
+                              region<uint32_t>(plan, O_TORDER), stream));
     SGS_TRY(probe(plan, SGS_EV_RANGES_END, stream));
     plan->stage = 2;
     if (num_instances) {
@@ -384,17 +378,12 @@ sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const flo
     SGS_TRY(probe(plan, SGS_EV_BWD_BEGIN, stream));
     SGS_TRY(launch_zero_grad2d(grad2d, rp.tiles, R, stream));
     // the backward's tile order: tiles by decreasing position of their last contributor
-    // (the forward wrote the keys), so the longest reverse walks start first
-    DeviceStatus* st = region<DeviceStatus>(plan, O_STATUS);
-    if (plan->num_tiles > 0)
-        SGS_TRY(launch_sort(region<uint32_t>(plan, O_BK), region<uint32_t>(plan, O_BV),
-                            region<uint32_t>(plan, O_TK1), region<uint32_t>(plan, O_TV1), &st->num_tiles,
-                            plan->num_tiles, 0, 16, 8, region<uint32_t>(plan, O_HIST),
-                            region<uint32_t>(plan, O_GOFF), region<uint32_t>(plan, O_COUNTERS),
-                            region<unsigned long long>(plan, O_TLB), st, stream, nullptr));
+    // (written by the forward), so the longest reverse walks start first
+    SGS_TRY(launch_tile_order(nullptr, region<uint32_t>(plan, O_TTOP), plan->num_tiles,
+                              region<uint32_t>(plan, O_BORDER), stream));
     SGS_TRY(probe(plan, SGS_EV_BWD_ZERO_END, stream));
     ViewTable vtb = vt;
-    vtb.order = region<uint32_t>(plan, O_BV);  // two passes: the sorted ids end in O_BV
+    vtb.order = region<uint32_t>(plan, O_BORDER);
     SGS_TRY(launch_blend_backward(vtb, region<uint2>(plan, O_RANGES), region<uint32_t>(plan, vreg), rp,
                                   s.batch_depth, s.bg[0], s.bg[1], s.bg[2], region<float>(plan, O_PIXT),
                                   region<uint32_t>(plan, O_PIXLAST), dL_drgb, grad2d, R,

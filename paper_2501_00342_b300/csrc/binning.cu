@@ -392,20 +392,43 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
     }
 }
 
-// Keys of the blend's tile order: tiles with longer instance lists first, so that the
-// CTAs of the most expensive tiles start early and the launch does not end on a few long
-// tiles.  key = 0xffff - min(length / 4, 0xffff) (ascending key = descending length),
-// value = the tile id; also stores the tile count in st->num_tiles.
-__global__ void __launch_bounds__(256) tile_order_keys_kernel(const uint2* __restrict__ ranges, uint32_t num_tiles,
-                                                              uint32_t* __restrict__ keys,
-                                                              uint32_t* __restrict__ vals, DeviceStatus* st) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->num_tiles = num_tiles;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x) {
+// The blend's tile order: tile ids by decreasing cost, so that the CTAs of the most
+// expensive tiles start first and a launch does not end on a few long tiles.  The cost of
+// tile t is the length of its instance list (ranges, the forward's order) or the position
+// of its last contributor (top, the backward's order).  One CTA: a counting sort into 64
+// buckets of the cost's magnitude (two per power of two), most expensive bucket first;
+// within a bucket the order is whatever the shared-memory atomics give (the tiles of a
+// launch are independent, so the images do not depend on it).
+__device__ __forceinline__ int cost_bucket(uint32_t c) {
+    if (c < 2u) return (int)c;
+    const int l = 31 - __clz(c);  // 1..31
+    return min(63, 2 * l + (int)((c >> (l - 1)) & 1u));
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ top, uint32_t num_tiles,
+                                                          uint32_t* __restrict__ order) {
+    __shared__ uint32_t hist[64];
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    auto cost = [&](uint32_t t) {
+        if (top) return top[t];
         const uint2 r = ranges[t];
-        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        keys[t] = 0xffffu - min(len >> 2, 0xffffu);
-        vals[t] = t;
+        return r.y > r.x ? r.y - r.x : 0u;
+    };
+    for (uint32_t t = threadIdx.x; t < num_tiles; t += blockDim.x) atomicAdd(&hist[cost_bucket(cost(t))], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // bucket starts, the most expensive bucket first
+        uint32_t acc = 0;
+        for (int b = 63; b >= 0; --b) {
+            const uint32_t c = hist[b];
+            hist[b] = acc;
+            acc += c;
+        }
     }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < num_tiles; t += blockDim.x)
+        order[atomicAdd(&hist[cost_bucket(cost(t))], 1u)] = t;
 }
 
 }  // namespace
@@ -463,19 +486,11 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_order(const uint2* ranges, int64_t num_tiles, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                              uint32_t* v1, uint32_t* hist, uint32_t* goff, uint32_t* counters,
-                              unsigned long long* lookback, DeviceStatus* st, cudaStream_t s) {
+cudaError_t launch_tile_order(const uint2* ranges, const uint32_t* top, int64_t num_tiles, uint32_t* order,
+                              cudaStream_t s) {
     if (num_tiles == 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t want = (num_tiles + threads - 1) / threads;
-    tile_order_keys_kernel<<<(unsigned)(want < 148 * 8 ? want : 148 * 8), threads, 0, s>>>(
-        ranges, (uint32_t)num_tiles, k0, v0, st);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // 16-bit keys: two passes of 8 bits, the order ends in (k0, v0)
-    return launch_sort(k0, v0, k1, v1, &st->num_tiles, num_tiles, 0, 16, 8, hist, goff, counters, lookback, st, s,
-                       nullptr, false);
+    tile_order_kernel<<<1, 1024, 0, s>>>(ranges, top, (uint32_t)num_tiles, order);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t capacity,

@@ -203,10 +203,9 @@ __device__ __forceinline__ uint2 clamp_range(uint2 r, uint32_t m) {
     return r;
 }
 
-// The backward's tile-order key of this CTA's tile: the largest position of a last
-// contributor over the tile's pixels (the reverse walk starts there), as
-// 0xffff - min(top / 4, 0xffff) so that an ascending sort starts the longest walks first.
-// Block-collective, at the end of a forward kernel (every thread reaches it).
+// The backward's tile-order cost of this CTA's tile: the largest position of a last
+// contributor over the tile's pixels (the reverse walk starts there).  Block-collective,
+// at the end of a forward kernel (every thread reaches it).
 __device__ __forceinline__ void write_backward_key(const ViewTable& vt, uint32_t tile, uint32_t my_last) {
     __shared__ uint32_t s_top;
     const uint32_t wmax = __reduce_max_sync(kFullMask, my_last);
@@ -214,10 +213,7 @@ __device__ __forceinline__ void write_backward_key(const ViewTable& vt, uint32_t
     __syncthreads();
     if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_top, wmax);
     __syncthreads();
-    if (threadIdx.x == 0 && vt.bwd_keys) {
-        vt.bwd_keys[tile] = 0xffffu - min(s_top >> 2, 0xffffu);
-        vt.bwd_vals[tile] = tile;
-    }
+    if (threadIdx.x == 0 && vt.tile_top) vt.tile_top[tile] = s_top;
 }
 
 // Per-pixel state of the forward walk.

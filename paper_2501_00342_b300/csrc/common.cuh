@@ -34,8 +34,7 @@ struct ViewTable {
     int32_t count_pairs;           // the forward blend writes per-pixel pair counts
     int64_t num_tiles;
     const uint32_t* order;         // the blend's tile order (CTA b renders tile order[b]), or null
-    uint32_t* bwd_keys;            // the forward's per-tile keys of the backward's tile order
-    uint32_t* bwd_vals;            // and the tile ids they sort (or null: not written)
+    uint32_t* tile_top;            // the forward's per-tile last-contributor position (or null)
     View v[SGS_MAX_VIEWS];
 };
 
@@ -47,7 +46,6 @@ struct DeviceStatus {
     uint32_t tile_counter[16];  // dynamic tile ids: [0] scan, [1..] sort passes
     uint32_t num_records;       // R, the length of the record sort
     uint32_t num_visible;       // records with instances: the record sort keeps only these
-    uint32_t num_tiles;         // length of the tile-order sort
 };
 
 // Correctly rounded single-precision operations that the compiler may not fuse or

@@ -82,12 +82,10 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
                              const uint32_t* offsets, int64_t n, int64_t R, DeviceStatus* st,
                              int64_t capacity, uint32_t* keys, uint32_t* vals, int digit_bits,
                              int passes, uint32_t* hist, cudaStream_t s);
-// The blend's tile order (tile ids by decreasing instance-list length) into v0, sorted with
-// the scratch (k0, k1, v1), the sort's histogram, offsets and counters, and a look-back
-// table of sort_lookback_entries(num_tiles, 8) entries.
-cudaError_t launch_tile_order(const uint2* ranges, int64_t num_tiles, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                              uint32_t* v1, uint32_t* hist, uint32_t* goff, uint32_t* counters,
-                              unsigned long long* lookback, DeviceStatus* st, cudaStream_t s);
+// The blend's tile order: tile ids by decreasing cost into order[num_tiles], the cost being
+// the instance-list length (top null: from ranges) or top[t] (the tile's last contributor).
+cudaError_t launch_tile_order(const uint2* ranges, const uint32_t* top, int64_t num_tiles, uint32_t* order,
+                              cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* tile_ids, const DeviceStatus* st, int64_t capacity,
                           int64_t num_tiles, uint2* ranges, cudaStream_t s);
 
