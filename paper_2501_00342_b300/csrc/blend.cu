@@ -1,23 +1,24 @@
 // Stage (e): front-to-back alpha blending per pixel, and its reverse-mode pass.
 //
-// One CTA per (view, tile); the forward uses one pixel per thread, the backward two.  The
-// tile's depth-sorted instance list
-// [start, end) is staged batch_depth Gaussians at a time in shared memory (three float4
-// records per Gaussian, gathered through the sorted record ids).  Per pixel centre p:
+// One CTA per (view, tile), the tiles taken most expensive first (vt.order).  Each warp
+// owns an 8-pixel-wide block of the tile; a thread has one, two (packed f32x2 pairs in the
+// blend_pair kernels) or four pixels of it.  The tile's depth-sorted instance list
+// [start, end) is staged batch_depth Gaussians at a time in shared memory, gathered
+// through the sorted record ids, with a mask of the warp blocks each Gaussian's support
+// may reach; a warp visits only the Gaussians of its bit words.  Per pixel centre p:
 //   power = -1/2 (A dx^2 + C dy^2) - B dx dy;  skip if power < -4.5 (outside 3 sigma)
 //   alpha = min(0.99, opacity exp(power));      skip if alpha < 1/255
 //   T' = T (1 - alpha);                          stop before this Gaussian if T' < 1e-4
 //   C += rgb alpha T;  T = T'
-// and the pixel is C + T bg.  A thread whose pixel is finished leaves the inner loop (its
-// warp leaves when all 32 lanes have), and the CTA stops fetching batches once
-// __syncthreads_count reports every pixel finished.
+// and the pixel is C + T bg.  A warp stops visiting once all its pixels are finished, and
+// the CTA stops fetching batches once __syncthreads_count reports every pixel finished.
 //
 // The backward pass walks each tile's list from the last contributor to the front,
 // rebuilding T_k = T_{k+1} / (1 - alpha_k) from the stored final transmittance and
-// carrying the normalised colour behind (acc = acc (1 - alpha) + rgb alpha, starting at
-// bg).  It recomputes power and alpha with the same operations as the forward pass, so
-// every skip decision is identical; per Gaussian the warp's 9 gradient terms are summed
-// with shuffles and added with one vector atomic per float4.
+// carrying the normalised colour behind (acc += alpha (rgb - acc), starting at bg).  It
+// recomputes power and alpha with the same operations as the forward pass, so every skip
+// decision is identical; per Gaussian the warp's 9 gradient terms are summed with shuffles
+// and added with two 16-byte vector atomics and one scalar atomic.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
