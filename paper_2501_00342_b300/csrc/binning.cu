@@ -1,5 +1,7 @@
-// Stages (b) and (d): exclusive scan of tiles touched, tile|depth key duplication, and
-// per-tile range identification over the sorted keys.
+// Stages (b) and (d) and their helpers: the digit histograms of the record depth sort, the
+// exclusive scan of tiles touched in depth order, the duplication of the records into
+// (tile id, record) instances in that order, the per-tile ranges over the sorted tile ids,
+// and the blend's tile orders (most expensive tiles first).
 #include <cuda_runtime.h>
 
 #include "common.cuh"

@@ -8,6 +8,8 @@
 //   conic = Sigma2D^-1, radius = ceil(3 sqrt(lambda_max)), screen mean, tile rectangle,
 //   and how many tiles the 3-sigma ellipse reaches (row spans)
 //   colour = max(0, SH(d) + 0.5 + sum_k SG_k(d)), d = (X - campos)/|X - campos| (Eq. 4-9)
+//   and the record depth sort's pair (depth bits, or all ones for a culled record; the
+//   record id with its tile count)
 // Everything up to the tile rectangle and the conic uses correctly rounded operations in
 // one fixed order (mul_rn/add_rn/...), so the cull, depth bits, radius and rectangle are
 // a function of the inputs alone and identical on every run and launch shape.
