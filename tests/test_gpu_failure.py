@@ -36,6 +36,11 @@ def test_published_chain_sums_without_waiting():
     s, st, _ = _lookback([0, INC | 100, AGG | 1])
     assert (s, st) == (101, B.SGS_OK)
     assert _lookback([])[:2] == (0, B.SGS_OK)
+    # chains longer than one read window (slots are read several at a time)
+    s, st, _ = _lookback([INC | 5] + [AGG | k for k in range(1, 11)])
+    assert (s, st) == (60, B.SGS_OK)
+    s, st, _ = _lookback([AGG | 2] * 9)  # back to slot 0, which counts as an aggregate
+    assert (s, st) == (18, B.SGS_OK)
 
 
 def test_unpublished_slot_times_out_and_context_survives():
@@ -45,6 +50,10 @@ def test_unpublished_slot_times_out_and_context_survives():
     # slot 0 is never published: the wait polls it until its limit, then reports
     s, st, secs = _lookback([0, AGG | 7, AGG | 2])
     assert st == B.SGS_ERR_TIMEOUT and s == 9
+    assert secs < 60.0
+    # an unpublished slot past the first read window: the aggregates after it are summed once
+    s, st, secs = _lookback([AGG | 100, 0] + [AGG | 1] * 6)
+    assert st == B.SGS_ERR_TIMEOUT and s == 6
     assert secs < 60.0
     # the context is still usable and gives the same image
     after = Rasterizer(model, cams).forward(model)
