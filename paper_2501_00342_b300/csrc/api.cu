@@ -265,10 +265,15 @@ sgs_status sgs_preprocess(sgs_plan* plan, const sgs_gaussians* g, void* workspac
     if (!plan || !workspace || check_gaussians(g) != SGS_OK || !same_layout(plan, g)) return SGS_ERR_INVALID;
     if (check_pointers(g) != SGS_OK) return SGS_ERR_INVALID;
     if (((uintptr_t)workspace & 255u) != 0 || ws_bytes < plan->workspace_bytes) return SGS_ERR_INVALID;
+    const bool rebind = plan->workspace != workspace;
     plan->workspace = workspace;
     plan->stage = 0;
     DeviceStatus* st = region<DeviceStatus>(plan, O_STATUS);
     SGS_TRY(launch_sort_init(st, 0u, stream));
+    // the forward's tile tops schedule the next forward of this plan (see sgs_bin_sort);
+    // a newly bound workspace has none
+    if (rebind && plan->num_tiles > 0)
+        SGS_TRY(cudaMemsetAsync(region<uint32_t>(plan, O_TTOP), 0, 4 * (size_t)plan->num_tiles, stream));
     const ViewTable vt = view_table(plan);
     SGS_TRY(probe(plan, SGS_EV_PRE_BEGIN, stream));
     if (plan->n > 0) SGS_TRY(launch_preprocess(*g, vt, records(plan), stream));
@@ -329,7 +334,9 @@ sgs_status sgs_bin_sort(sgs_plan* plan, int64_t* num_instances, cudaStream_t str
     SGS_TRY(launch_fill_u32(region<uint32_t>(plan, O_RANGES), 0u, 2 * (size_t)plan->num_tiles, stream));
     SGS_TRY(launch_ranges(region<uint32_t>(plan, kreg), st, cap, plan->num_tiles,
                           region<uint2>(plan, O_RANGES), stream));
-    SGS_TRY(launch_tile_order(region<uint2>(plan, O_RANGES), nullptr, plan->num_tiles,
+    // most expensive tiles first: by the previous forward's last contributors where there
+    // are some, else by list length
+    SGS_TRY(launch_tile_order(region<uint2>(plan, O_RANGES), region<uint32_t>(plan, O_TTOP), plan->num_tiles,
                               region<uint32_t>(plan, O_TORDER), stream));
     SGS_TRY(probe(plan, SGS_EV_RANGES_END, stream));
     plan->stage = 2;

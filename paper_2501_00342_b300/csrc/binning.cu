@@ -396,8 +396,11 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
 
 // The blend's tile order: tile ids by decreasing cost, so that the CTAs of the most
 // expensive tiles start first and a launch does not end on a few long tiles.  The cost of
-// tile t is the length of its instance list (ranges, the forward's order) or the position
-// of its last contributor (top, the backward's order).  One CTA: a counting sort into 64
+// tile t is the position of its last contributor top[t] (how far a walk of the tile's
+// list goes), or, where top is null or top[t] is 0, the length of its instance list
+// (ranges).  The backward passes the tops of the forward it differentiates; the forward
+// passes those of the previous forward of the same plan (zero after a new workspace), a
+// schedule hint only: any order gives the same images.  One CTA: a counting sort into 64
 // buckets of the cost's magnitude (two per power of two), most expensive bucket first;
 // within a bucket the order is whatever the shared-memory atomics give (the tiles of a
 // launch are independent, so the images do not depend on it).
@@ -414,7 +417,8 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
     if (threadIdx.x < 64) hist[threadIdx.x] = 0;
     __syncthreads();
     auto cost = [&](uint32_t t) {
-        if (top) return top[t];
+        const uint32_t c = top ? top[t] : 0u;
+        if (c || !ranges) return c;
         const uint2 r = ranges[t];
         return r.y > r.x ? r.y - r.x : 0u;
     };

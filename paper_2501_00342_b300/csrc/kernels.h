@@ -83,7 +83,8 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
                              int64_t capacity, uint32_t* keys, uint32_t* vals, int digit_bits,
                              int passes, uint32_t* hist, cudaStream_t s);
 // The blend's tile order: tile ids by decreasing cost into order[num_tiles], the cost being
-// the instance-list length (top null: from ranges) or top[t] (the tile's last contributor).
+// top[t] (a tile's last-contributor position) where top is given and non-zero, else the
+// instance-list length from ranges.
 cudaError_t launch_tile_order(const uint2* ranges, const uint32_t* top, int64_t num_tiles, uint32_t* order,
                               cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* tile_ids, const DeviceStatus* st, int64_t capacity,
