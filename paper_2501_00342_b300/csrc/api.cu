@@ -16,7 +16,7 @@ namespace {
 enum Region {
     O_STATUS, O_REC0, O_REC1, O_REC2, O_RECT, O_TILES, O_OFFS, O_K0, O_V0, O_K1, O_V1,
     O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SPANS, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
-    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_TORDER, O_TTOP, O_BORDER, O_END
+    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_TORDER, O_TTOP, O_BORDER, O_MASKS, O_END
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -93,6 +93,7 @@ ViewTable view_table(const sgs_plan* p) {
     vt.num_tiles = p->num_tiles;
     vt.order = p->workspace ? region<uint32_t>(p, O_TORDER) : nullptr;
     vt.tile_top = p->workspace ? region<uint32_t>(p, O_TTOP) : nullptr;
+    vt.masks = p->workspace ? region<uint16_t>(p, O_MASKS) : nullptr;
     for (int v = 0; v < p->B; ++v) {
         const sgs_camera& c = p->cams[v];
         View& w = vt.v[v];
@@ -250,6 +251,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     sz[O_RLB] = 8 * sort_lookback_entries(R, rrb);
     // the blend's tile orders and the forward's per-tile last contributor
     sz[O_TORDER] = sz[O_TTOP] = sz[O_BORDER] = 4 * (size_t)tiles;
+    sz[O_MASKS] = 2 * cap;  // per instance, the warp blocks its support reaches
     size_t off = 0;
     for (int k = 0; k < O_END; ++k) {
         plan->offsets[k] = off;
@@ -391,6 +393,9 @@ sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const flo
     SGS_TRY(probe(plan, SGS_EV_BWD_ZERO_END, stream));
     ViewTable vtb = vt;
     vtb.order = region<uint32_t>(plan, O_BORDER);
+    // the two-pixel kernels of both passes share warp blocks: the backward reads the masks
+    // the forward stored
+    if (!(vt.fwd_ppt == 2 && vt.bwd_ppt == 2)) vtb.masks = nullptr;
     SGS_TRY(launch_blend_backward(vtb, region<uint2>(plan, O_RANGES), region<uint32_t>(plan, vreg), rp,
                                   s.batch_depth, s.bg[0], s.bg[1], s.bg[2], region<float>(plan, O_PIXT),
                                   region<uint32_t>(plan, O_PIXLAST), dL_drgb, grad2d, R,

@@ -121,16 +121,20 @@ constexpr int stage_fields(int layout) { return layout == kPlain ? 3 : layout ==
 // from the tile's sorted list at `first`) in shared memory, and writes for every warp w of
 // the CTA the 32-bit word of the group's entries whose support may reach w's block
 // (bits[w * words + g]; bit b = entry 32 g + b): a transpose of the entries' block masks by
-// one ballot per warp.  Returns the record id of the lane's entry.  Warp-collective.
+// one ballot per warp.  The block masks are computed, or read from mask_in[j] (those a
+// forward with the same warp blocks stored), and optionally stored to mask_out[j].
+// Returns the record id of the lane's entry.  Warp-collective.
 template <int PPT, int LAYOUT>
 __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileCoord& tc, int g, int cnt,
                                                 const uint32_t* __restrict__ first, uint32_t R,
                                                 const float4* __restrict__ rec0, const float4* __restrict__ rec1,
                                                 const float4* __restrict__ rec2, float4* sb, int batch,
-                                                uint32_t* bits, int words) {
+                                                uint32_t* bits, int words, uint16_t* __restrict__ mask_out,
+                                                const uint16_t* __restrict__ mask_in) {
     const int lane = threadIdx.x & 31, j = g * 32 + lane;
     uint32_t mask = 0, id = 0;
     if (j < cnt) {
+        if (mask_in) mask = mask_in[j];
         id = min(first[j], R - 1);  // ids are < R by construction
         const float4 r0 = rec0[id], r1 = rec1[id], r2 = rec2[id];
         if (LAYOUT == kPlain) {
@@ -148,7 +152,8 @@ __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileC
                 sb[4 * batch + j] = make_float4(r2.z, r2.z, 0.0f, 0.0f);
             }
         }
-        mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
+        if (!mask_in) mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
+        if (mask_out) mask_out[j] = (uint16_t)mask;
     }
     const int nw = (int)(blockDim.x >> 5);
     uint32_t mine = 0;
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
             stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
-                                     words);
+                                     words, nullptr, nullptr);
         __syncthreads();
         // this warp's entries in increasing order: the set bits of its words
         for (int g = 0; g < groups && !all_done; ++g) {
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
             stage_group<2, kPairs>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
-                                   words);
+                                   words, vt.masks ? vt.masks + range.x + base : nullptr, nullptr);
         __syncthreads();
         for (int g = 0; g < groups && !all_done; ++g) {
             for (uint32_t word = my_bits[g]; word != 0 && !all_done; word &= word - 1) {
@@ -548,7 +553,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
         const int cnt = hi - lo, groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5)) {
             const uint32_t id = stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + lo, R32, rec0, rec1, rec2,
-                                                         sbuf, batch, bits, words);
+                                                         sbuf, batch, bits, words, nullptr, nullptr);
             if (g * 32 + lane < cnt) sid[g * 32 + lane] = id;
         }
         __syncthreads();
@@ -686,7 +691,8 @@ __global__ void __launch_bounds__(512) blend_pair_backward_kernel(
         const int cnt = hi - lo, groups = (cnt + 31) >> 5;
         for (int gr_ = (int)(threadIdx.x >> 5); gr_ < groups; gr_ += (int)(blockDim.x >> 5)) {
             const uint32_t id = stage_group<2, kPairsColour>(vt, tc, gr_, cnt, vals + range.x + lo, R32, rec0, rec1,
-                                                             rec2, sbuf, batch, bits, words);
+                                                             rec2, sbuf, batch, bits, words, nullptr,
+                vt.masks ? vt.masks + range.x + lo : nullptr);
             if (gr_ * 32 + lane < cnt) sid[gr_ * 32 + lane] = id;
         }
         __syncthreads();

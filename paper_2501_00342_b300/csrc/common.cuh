@@ -35,6 +35,9 @@ struct ViewTable {
     int64_t num_tiles;
     const uint32_t* order;         // the blend's tile order (CTA b renders tile order[b]), or null
     uint32_t* tile_top;            // the forward's per-tile last-contributor position (or null)
+    uint16_t* masks;               // per instance, the warp blocks its support may reach: the
+                                   // two-pixel forward stores them, the two-pixel backward reads
+                                   // them (null: computed)
     View v[SGS_MAX_VIEWS];
 };
 
