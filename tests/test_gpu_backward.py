@@ -86,11 +86,14 @@ def test_gradients_adaptive_sh_vs_adjoint():
         assert np.all(g["sh"][(top[i] + 1) ** 2:, :, i] == 0.0)
 
 
-@pytest.mark.parametrize("tile,bwd", [((16, 16), 4), ((16, 32), 4), ((16, 32), 1), ((8, 8), 2), ((32, 32), 2), ((64, 16), 4)])
-def test_backward_pixels_per_thread(tile, bwd):
+@pytest.mark.parametrize("tile,bwd,fwd", [((16, 16), 4, 0), ((16, 32), 4, 0), ((16, 32), 1, 0), ((8, 8), 2, 0),
+                                          ((32, 32), 2, 0), ((64, 16), 4, 0), ((16, 32), 2, 1)])
+def test_backward_pixels_per_thread(tile, bwd, fwd):
+    # fwd = 1 with bwd = 2: the backward computes its warp-block masks instead of reading
+    # the ones a two-pixel forward stores
     sc, cams = I.workload(0)
     ws = _weights(sc, cams, 8)
-    g = _gpu_grads(sc, cams, ws, RenderSettings(tile_w=tile[0], tile_h=tile[1], bwd_pixels=bwd))
+    g = _gpu_grads(sc, cams, ws, RenderSettings(tile_w=tile[0], tile_h=tile[1], bwd_pixels=bwd, fwd_pixels=fwd))
     _compare(sc, cams, ws, g, _oracle_grads(sc, cams, ws))
     ref = _gpu_grads(sc, cams, ws)
     for p in PLANES:
