@@ -109,6 +109,11 @@ struct SortShape {
     static constexpr int TILE = kSortThreads * ITEMS;
 };
 
+// The look-back tables are sized for tiles of kSortTile keys (sort_lookback_entries): no
+// key width may use a smaller tile, or a sort would have more tiles than table rows.
+static_assert(SortShape<uint32_t>::TILE >= kSortTile && SortShape<unsigned long long>::TILE >= kSortTile,
+              "a sort tile is smaller than the tile the look-back tables are sized for");
+
 // 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
