@@ -156,22 +156,31 @@ __global__ void __launch_bounds__(256) record_hist_kernel(const uint32_t* __rest
     if (blockIdx.x == 0 && threadIdx.x == 0) st->num_records = (uint32_t)R;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t kept_count = 0;  // warp total (same in every lane)
-    // warp-uniform trip count: every lane of a warp runs the same iterations
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < R; base += stride) {
-        const int64_t r = base + lane;
-        const bool valid = r < R;
-        const uint32_t key = valid ? keys[r] : 0xffffffffu;
-        const bool kept = key != 0xffffffffu;
-        const uint32_t live = __ballot_sync(kFullMask, kept);
-        kept_count += __popc(live);
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = (key >> (p * RB)) & (RADIX - 1);
-            if (2 * p < passes) {
-                if (kept) atomicAdd(&hw[p * RADIX + d], 1u);
-            } else {
-                const uint32_t peers = same_value_lanes<RB>(d) & live;
-                if (kept && lane == 31 - __clz(peers)) hw[p * RADIX + d] += __popc(peers);
-                __syncwarp();
+    // warp-uniform trip count: every lane of a warp runs the same iterations; the keys of
+    // kUnroll strides are loaded before any is counted (loads in flight together)
+    constexpr int kUnroll = 4;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < R;
+         base += kUnroll * stride) {
+        uint32_t key[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t r = base + u * stride + lane;
+            key[u] = r < R ? keys[r] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool kept = key[u] != 0xffffffffu;
+            const uint32_t live = __ballot_sync(kFullMask, kept);
+            kept_count += __popc(live);
+            for (int p = 0; p < passes; ++p) {
+                const uint32_t d = (key[u] >> (p * RB)) & (RADIX - 1);
+                if (2 * p < passes) {
+                    if (kept) atomicAdd(&hw[p * RADIX + d], 1u);
+                } else {
+                    const uint32_t peers = same_value_lanes<RB>(d) & live;
+                    if (kept && lane == 31 - __clz(peers)) hw[p * RADIX + d] += __popc(peers);
+                    __syncwarp();
+                }
             }
         }
     }
