@@ -59,20 +59,25 @@ __device__ __forceinline__ WarpBlock warp_block(const ViewTable& vt) {
     return b;
 }
 
-// The warp blocks of the CTA's tile that the Gaussian's support may reach: bit w for warp w.
-// With Q(d) = A dx^2 + 2B dx dy + C dy^2 (the conic; records store (qa, qb, qc) =
-// (-A/2, -B, -C/2)), the ellipse Q <= 9.01 is cut into the tile's bands of block rows.  Over
-// a band's pixel-centre rows (padded by 1/64 pixel) its x-extent is exact: the rightmost
-// x is the ellipse's rightmost point ex when that point's row -B ex / C falls in the band,
-// else the larger chord end (-B y + sqrt(9.01 A - det y^2)) / A at the band's two edge rows
-// (the chord end is concave in y), and the leftmost mirrors it.  Each block column whose
-// padded pixel-centre columns meet the extent gets its bit.  A supported pixel centre has
-// Q <= 9 up to single-precision rounding, which the 0.1 % slack and the pad cover (inside
-// the Q <= 9 rows the chord's own rounding is far below that slack), so a warp without its
-// bit has no supported pixel.  A degenerate conic or a non-finite centre sets every bit.
+// The warp blocks of the CTA's tile in which some pixel may blend the Gaussian: bit w for
+// warp w.  A pixel blends it only inside its support, Q(d) <= 9 (Mahalanobis distance 3),
+// and where its alpha o exp(-Q/2) reaches 1/255, that is Q <= 2 ln(255 o): for opacities
+// below about 0.35 the second bound is the tighter one.  With Q(d) = A dx^2 + 2B dx dy +
+// C dy^2 (the conic; records store (qa, qb, qc) = (-A/2, -B, -C/2)) and Qs the smaller
+// bound widened by 0.11 % (and 0.002 for the alpha bound), the ellipse Q <= Qs is cut into
+// the tile's bands of block rows.  Over a band's pixel-centre rows (padded by 1/64 pixel)
+// its x-extent is exact: the rightmost x is the ellipse's rightmost point ex when that
+// point's row -B ex / C falls in the band, else the larger chord end
+// (-B y + sqrt(Qs A - det y^2)) / A at the band's two edge rows (the chord end is concave
+// in y), and the leftmost mirrors it.  Each block column whose padded pixel-centre columns
+// meet the extent gets its bit.  A blending pixel centre has Q within single-precision
+// rounding of the bounds (the exponential's and logarithm's errors are below 1e-5 there),
+// which the slack and the pad cover (the chord's own rounding is far below that slack), so
+// a warp without its bit has no pixel that blends the Gaussian.  A degenerate conic or a
+// non-finite centre sets every bit; an opacity at which no alpha reaches 1/255 none.
 template <int PPT>
 __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCoord& tc, float px, float py,
-                                               float qa, float qb, float qc) {
+                                               float qa, float qb, float qc, float o) {
     constexpr int BH = 4 * PPT;  // pixel rows per block
     const float A = -2.0f * qa, B = -qb, C = -2.0f * qc;
     const float det = A * C - B * B;
@@ -80,11 +85,14 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
     const float gx = px - ((float)(tc.tx * vt.tile_w) + 0.5f);
     const float gy = py - ((float)(tc.ty * vt.tile_h) + 0.5f);
     if (!(det > 0.0f && A > 0.0f && C > 0.0f && fabsf(gx) < 1e30f && fabsf(gy) < 1e30f)) return ~0u;
+    // fminf keeps the support bound when the logarithm is NaN
+    const float Qs = fminf(kSpanQ, (2.0f * __logf(o * 255.0f) + 0.002f) * (kSpanQ / 9.0f));
+    if (!(Qs > 0.0f)) return 0u;
     const int nbx = vt.tile_w >> 3, nby = vt.tile_h / BH;
-    const float k = kSpanQ / det;
+    const float k = Qs / det;
     const float ex = sqrtf(k * C), ey = sqrtf(k * A);
     const float dyr = -B * ex / C;  // row offset of the rightmost point
-    const float iA = 1.0f / A, Ak = A * kSpanQ;
+    const float iA = 1.0f / A, Ak = A * Qs;
     const float b0 = fmaxf(ceilf((gy - ey - kSpanPad - (float)(BH - 1)) * (1.0f / BH)), 0.0f);
     const float b1 = fminf(floorf((gy + ey + kSpanPad) * (1.0f / BH)), (float)(nby - 1));
     uint32_t mask = 0;
@@ -119,10 +127,12 @@ constexpr int stage_fields(int layout) { return layout == kPlain ? 3 : layout ==
 
 // Stages one group of 32 batch entries (this warp's group g: entries 32 g + lane < cnt,
 // from the tile's sorted list at `first`) in shared memory, and writes for every warp w of
-// the CTA the 32-bit word of the group's entries whose support may reach w's block
+// the CTA the 32-bit word of the group's entries that some pixel of w's block may blend
 // (bits[w * words + g]; bit b = entry 32 g + b): a transpose of the entries' block masks by
 // one ballot per warp.  The block masks are computed, or read from mask_in[j] (those a
-// forward with the same warp blocks stored), and optionally stored to mask_out[j].
+// forward with the same warp blocks stored), and optionally stored to mask_out[j].  Without
+// alpha_bound the masks take the support alone (the counting forwards, whose evaluation
+// counts are those of the support test).
 // Returns the record id of the lane's entry.  Warp-collective.
 template <int PPT, int LAYOUT>
 __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileCoord& tc, int g, int cnt,
@@ -130,7 +140,7 @@ __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileC
                                                 const float4* __restrict__ rec0, const float4* __restrict__ rec1,
                                                 const float4* __restrict__ rec2, float4* sb, int batch,
                                                 uint32_t* bits, int words, uint16_t* __restrict__ mask_out,
-                                                const uint16_t* __restrict__ mask_in) {
+                                                const uint16_t* __restrict__ mask_in, bool alpha_bound = true) {
     const int lane = threadIdx.x & 31, j = g * 32 + lane;
     uint32_t mask = 0, id = 0;
     if (j < cnt) {
@@ -152,7 +162,7 @@ __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileC
                 sb[4 * batch + j] = make_float4(r2.z, r2.z, 0.0f, 0.0f);
             }
         }
-        if (!mask_in) mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x);
+        if (!mask_in) mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x, alpha_bound ? r1.y : 1.0f);
         if (mask_out) mask_out[j] = (uint16_t)mask;
     }
     const int nw = (int)(blockDim.x >> 5);
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
             stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
-                                     words, nullptr, nullptr);
+                                     words, nullptr, nullptr, !COUNT);
         __syncthreads();
         // this warp's entries in increasing order: the set bits of its words
         for (int g = 0; g < groups && !all_done; ++g) {
@@ -385,7 +395,7 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
             stage_group<2, kPairs>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
-                                   words, vt.masks ? vt.masks + range.x + base : nullptr, nullptr);
+                                   words, vt.masks ? vt.masks + range.x + base : nullptr, nullptr, !COUNT);
         __syncthreads();
         for (int g = 0; g < groups && !all_done; ++g) {
             for (uint32_t word = my_bits[g]; word != 0 && !all_done; word &= word - 1) {

@@ -101,6 +101,20 @@ def test_backward_pixels_per_thread(tile, bwd, fwd):
             assert np.abs(g[p] - ref[p]).max() <= 1e-5 * np.abs(ref[p]).max(), p
 
 
+@pytest.mark.parametrize("batch", [32, 96, 100, 1024])
+def test_backward_batch_depth(batch):
+    # the reverse walk over batches of other depths, including one that is not a whole
+    # number of 32-entry groups
+    sc, cams = I.workload(0)
+    ws = _weights(sc, cams, 8)
+    g = _gpu_grads(sc, cams, ws, RenderSettings(tile_w=32, tile_h=32, batch_depth=batch))
+    _compare(sc, cams, ws, g, _oracle_grads(sc, cams, ws))
+    ref = _gpu_grads(sc, cams, ws)
+    for p in PLANES:
+        if ref[p] is not None:  # the same sums, added in another order
+            assert np.abs(g[p] - ref[p]).max() <= 1e-5 * np.abs(ref[p]).max(), p
+
+
 def _slice_200():
     """200 clustered Gaussians (the training-step distribution), one 32x32 view."""
     sc = I.cluster_scene(200, 1, 4, config=2, num_clusters=8)
