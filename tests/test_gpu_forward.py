@@ -114,6 +114,33 @@ def test_tile_size_bins_exact_and_image_unchanged(tile):
     assert torch.equal(img, ref_img)  # same contributors in the same order: bit-identical
 
 
+@pytest.mark.parametrize("case", ["cube", "clusters"])
+@pytest.mark.parametrize("opacity_scale", [1.0, 0.05])
+@pytest.mark.parametrize("fwd", [1, 2])
+def test_alpha_bounded_masks_keep_every_contributor(case, opacity_scale, fwd):
+    # The blend kernels cut each Gaussian's warp-block mask at the alpha bound
+    # Q <= 2 ln(255 o) as well as at the support Q <= 9; the counting forward keeps the
+    # support alone.  Both must blend the same contributors in the same order, so the
+    # images and the transmittance agree bit for bit.  Scaling the opacities down makes
+    # the alpha bound the tighter one for most Gaussians.
+    if case == "cube":
+        sc, cams = I.workload(0)
+    else:
+        sc, cams = I.workload(1, n=200_000)
+        cams = cams[:2]
+    sc.opacity[:sc.n] *= opacity_scale
+    assert (255.0 * sc.opacity[:sc.n] < np.exp(4.5)).mean() > (0.3 if opacity_scale == 1.0 else 0.9)
+    tile = 32 if fwd == 2 else 16  # one pixel per thread: CTAs of at most 512 threads
+    rast, model, img, out_T = _run(sc, cams, RenderSettings(tile_w=tile, tile_h=tile, fwd_pixels=fwd))
+    rast.plan.settings.count_pairs = 1
+    T2 = torch.empty_like(out_T)
+    img2 = rast.forward(model, out_T=T2)
+    rast.plan.settings.count_pairs = 0
+    torch.cuda.synchronize()
+    assert rast.device_status() == 0
+    assert torch.equal(img, img2) and torch.equal(out_T, T2)
+
+
 @pytest.mark.parametrize("batch", [32, 64, 128, 512, 1024])
 def test_batch_depth_does_not_change_image(batch):
     sc, cams = I.workload(0)
