@@ -141,6 +141,36 @@ def test_alpha_bounded_masks_keep_every_contributor(case, opacity_scale, fwd):
     assert torch.equal(img, img2) and torch.equal(out_T, T2)
 
 
+@pytest.mark.parametrize("below", [False, True])
+@pytest.mark.parametrize("fwd", [1, 2])
+def test_alpha_threshold_at_a_pixel_centre(below, fwd):
+    # A Gaussian centred on pixel (64, 64) with opacity fl(1/255) has alpha exactly 1/255
+    # there (G = 1) and below it at every other pixel: it blends at that pixel alone, and
+    # the alpha-bounded masks (a tiny ellipse around the centre) must keep it.  One ulp
+    # less opacity and it blends nowhere.
+    o = np.float32(1.0) / np.float32(255.0)
+    if below:
+        o = np.nextafter(o, np.float32(0.0))
+    sc = make_scene([[0.0, 0.0, 0.0]], [[0.05, 0.05, 0.05]], [[1.0, 0.0, 0.0, 0.0]], [o], np.full((1, 1, 3), 0.8))
+    cam = axis_camera(128, 128, 60.0, 4.0, cx=64.5, cy=64.5)
+    tile = 32 if fwd == 2 else 16
+    rast, model, img, out_T = _run(sc, [cam], RenderSettings(tile_w=tile, tile_h=tile, fwd_pixels=fwd))
+    assert rast.region("REC0", torch.float32)[:2].tolist() == [64.5, 64.5]
+    hit = torch.nonzero(out_T < 1.0).flatten().tolist()
+    assert hit == ([] if below else [64 * 128 + 64])
+    if not below:
+        assert out_T[64 * 128 + 64].item() == np.float32(1.0) - o
+    rast.plan.settings.count_pairs = 1
+    T2 = torch.empty_like(out_T)
+    img2 = rast.forward(model, out_T=T2)
+    rast.plan.settings.count_pairs = 0
+    torch.cuda.synchronize()
+    assert torch.equal(img, img2) and torch.equal(out_T, T2)
+    counts = rast.region("PIX_COUNT", torch.int32)[:2 * rast.num_pixels].view(-1, 2).cpu().numpy()
+    assert counts[:, 1].sum() == (0 if below else 1)
+    assert counts[:, 0].sum() > 9  # the support holds the neighbouring pixels too
+
+
 @pytest.mark.parametrize("batch", [32, 64, 128, 512, 1024])
 def test_batch_depth_does_not_change_image(batch):
     sc, cams = I.workload(0)
