@@ -268,9 +268,15 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
             const int v = (int)(r / n32);
             tbase = vt.v[v].tile_base;
             TW = vt.v[v].tiles_x;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tab[lane][k] = spans[4 * (size_t)r + k];
+            // the table's first sector; the second only for more than kSpanRowsShort rows
+            // (words past a table's last row are never read)
+            tab[lane][0] = spans[4 * (size_t)r];
+            tab[lane][1] = spans[4 * (size_t)r + 1];
             hdr = tab[lane][0].x;
+            if ((hdr >> 16) > kSpanRowsShort && (hdr >> 16) != kSpanRowsOverflow) {
+                tab[lane][2] = spans[4 * (size_t)r + 2];
+                tab[lane][3] = spans[4 * (size_t)r + 3];
+            }
         }
         __syncwarp();
         const bool slow = cnt && (hdr >> 16) == kSpanRowsOverflow;

@@ -152,6 +152,7 @@ __device__ __forceinline__ SupportTerms support_terms(float qa, float qb, float 
 // inside that extent.  One fixed order of correctly rounded operations: the count in
 // preprocess and the keys in duplicate agree exactly.
 constexpr int kSpanRows = 15;                // rows kept in a record's packed table
+constexpr uint32_t kSpanRowsShort = 7;       // rows whose table fits its first 32 bytes
 constexpr uint32_t kSpanRowsOverflow = 0xffffu;
 constexpr float kSpanQ = 9.01f;
 constexpr float kSpanPad = 0.015625f;

@@ -174,7 +174,8 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
 
 // Tiles the ellipse reaches (0: the Gaussian is culled), and the packed row table the
 // duplicate kernel reads (16 words): word 0 = first row | rows << 16; words 1..15 = first
-// column | (tiles in the earlier rows) << 16 per row.  More than kSpanRows rows or more
+// column | (tiles in the earlier rows) << 16 per row; words past the last row are unused
+// (the second 32-byte half is stored only for tables of more than kSpanRowsShort rows).  More than kSpanRows rows or more
 // than 65535 tiles mark a table the kernel recomputes instead.  The table is written to
 // table[k * stride] (a thread's column of a shared-memory array).  Done for the 32 records
 // of a warp at once (warp-collective; lanes whose record is not visible pass
@@ -372,8 +373,10 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         rect[r] = make_uint2((uint32_t)P.x0 | ((uint32_t)P.y0 << 16),
                              (uint32_t)P.x1 | ((uint32_t)P.y1 << 16));
         tiles[r] = hits;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
+        // words 0-7 (one 32-byte sector) hold the tables of up to 7 rows; the second sector
+        // is written only for longer ones, and the duplicate reads it only then
+        const int chunks = (table[0] >> 16) > kSpanRowsShort ? 4 : 2;
+        for (int k = 0; k < chunks; ++k)
             spans[4 * r + k] = make_uint4(table[(4 * k) * kPreThreads], table[(4 * k + 1) * kPreThreads],
                                           table[(4 * k + 2) * kPreThreads], table[(4 * k + 3) * kPreThreads]);
     }
