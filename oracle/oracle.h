@@ -4,7 +4,9 @@
  * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg
  * may load this library.  It shares no code, header or constant table with the CUDA
  * path under paper_2501_00342_b300/; both sides are written separately from the
- * paper (Eq. 2-9) and from the rasterizer conventions listed in the design doc.
+ * paper (Eq. 2-9) and from the 3D Gaussian splatting rasterizer conventions it builds
+ * on (3-sigma support, alpha clamp 0.99, alpha cutoff 1/255, early stop below
+ * transmittance 1e-4, EWA dilation 0.3 px).
  *
  * Three parts:
  *   mirror32.cpp   FP32 "binning mirror": the integer decisions of the method taken in
