@@ -153,6 +153,8 @@ __device__ __forceinline__ SupportTerms support_terms(float qa, float qb, float 
 // preprocess and the keys in duplicate agree exactly.
 constexpr int kSpanRows = 15;                // rows kept in a record's packed table
 constexpr uint32_t kSpanRowsShort = 7;       // rows whose table fits its first 32 bytes
+static_assert(1 + kSpanRows == 16, "a row table is a header word and kSpanRows rows in 64 bytes");
+static_assert(1 + kSpanRowsShort == 8, "a short table is a header word and its rows in 32 bytes");
 constexpr uint32_t kSpanRowsOverflow = 0xffffu;
 constexpr float kSpanQ = 9.01f;
 constexpr float kSpanPad = 0.015625f;
