@@ -38,26 +38,24 @@ WORKLOAD = ("3M clustered Gaussians, SH-1 + 4 SG lobes (free axes), 16 orbit vie
             "{640x360,1280x720,1600x900,1920x1080}, L1 vs U(0,1) targets, forward + backward")
 
 
-# DRAM bytes per unit of the profiled kernels (profiles/dram_traffic.md), valid while the
-# kernel's source file keeps the hash recorded there
+# DRAM bytes per unit of work of the profiled kernels (profiles/dram_traffic.json), valid
+# while the kernel's source file keeps the hash recorded there
 def _traffic_rates():
     import hashlib
-    import re
     rates = {}
     try:
-        text = open(os.path.join(ROOT, "profiles", "dram_traffic.md")).read()
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            table = json.load(f)["kernels"]
+    except (OSError, ValueError, KeyError):
         return rates
-    for m in re.finditer(r"^\| (\w+)(?: \([^)]*\))? \| (\w+\.cu) \| ([0-9a-f]{12}) \| [^|]+ \| (\w+) \| ([0-9.]+) \|",
-                         text, re.M):
-        kernel, src, sha, unit, rate = m.groups()
-        path = os.path.join(ROOT, "paper_2501_00342_b300", "csrc", src)
+    for kernel, e in table.items():
+        path = os.path.join(ROOT, "paper_2501_00342_b300", "csrc", e["source"])
         try:
             now = hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
         except OSError:
             continue
-        if now == sha:
-            rates[kernel] = (unit, float(rate))
+        if now == e["sha1"]:
+            rates[kernel] = (e["unit"], float(e["bytes_per_unit"]))
     return rates
 
 
@@ -116,6 +114,32 @@ class ClockSampler:
                           if len(r) > 3 + k and r[3 + k].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(self.rows), "reasons": reasons}
+
+
+def measure_alu_peak(index: int, reps: int = 10, iters: int = 1 << 19):
+    """FP32 throughput of this GPU, measured: the library's probe kernel (8 independent
+    multiply-add chains per thread over a multiple of the SM count) timed with CUDA events,
+    as scalar fma.rn.f32 and as packed fma.rn.f32x2, with the SM clock sampled meanwhile.
+    Returns Tops/s (a multiply-add counted as one operation, like the kernels' counts)."""
+    import torch
+    from paper_2501_00342_b300 import binding as B
+    stream = torch.cuda.current_stream()
+    out = torch.empty(B.alu_probe_size(), dtype=torch.float32, device="cuda")
+    res = {}
+    for label, packed in (("ffma", False), ("ffma2", True)):
+        B.alu_probe(packed, 1024, out.data_ptr(), stream.cuda_stream)  # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(index) as clk:
+            a.record(stream)
+            ops = 0.0
+            for _ in range(reps):
+                ops += B.alu_probe(packed, iters, out.data_ptr(), stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res[label] = {"tops": round(ops / (ms / 1e3) / 1e12, 3), "ms": round(ms, 2), "clocks": clk.summary()}
+    return res
 
 
 # ------------------------------------------------------------------------------ GPU arm
@@ -278,7 +302,18 @@ def run_gpu(args):
     e_eval, e_contrib = int(counts[:, 0].sum().item()), int(counts[:, 1].sum().item())
     p_bytes = 4 * scene.floats_per_gaussian()
     hbm, sm_max, peak_kind = _peaks()
-    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12  # Tops/s: one FP32 op per lane per clock
+    # FP32 peak measured on this GPU (scalar and packed multiply-adds); when the probe ran at
+    # a lower SM clock than the timed step, it is scaled up to the step's clock, so that the
+    # blend kernels' fractions are not inflated by a slower probe
+    alu = measure_alu_peak(local)
+    step_mhz = clk.summary().get("sm_mhz") or sm_max
+    best = max(("ffma", "ffma2"), key=lambda k: alu[k]["tops"])
+    probe_mhz = alu[best]["clocks"].get("sm_mhz") or step_mhz
+    alu_peak = alu[best]["tops"] * max(1.0, step_mhz / probe_mhz)
+    alu["peak_tops"] = round(alu_peak, 3)
+    alu["peak_from"] = f"{best} at {probe_mhz:.0f} MHz, scaled to the timed step's {step_mhz:.0f} MHz" \
+        if step_mhz > probe_mhz else f"{best} at {probe_mhz:.0f} MHz"
+    alu["sm_count"] = torch.cuda.get_device_properties(local).multi_processor_count
     fwd_name = "blend_pair_kernel" if settings.fwd_pixels in (0, 2) else "blend_kernel"
     bwd_name = "blend_pair_backward_kernel" if settings.bwd_pixels in (0, 2) else "blend_backward_kernel"
     kernels = {
@@ -317,9 +352,10 @@ def run_gpu(args):
                            "algorithmic_ops_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
     dominant = dict(roofs.get(dom_name, {}))
     dominant["kernel"] = dom_name
-    dominant["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs; alu = 148 SMs x 128 lanes x sm_max_mhz)"
+    dominant["peak_source"] = (f"hbm: {peak_kind} (MEASURED_PEAKS.json hbm_gbs); alu: measured FP32 multiply-add "
+                               f"throughput of this GPU ({alu['peak_from']})")
     dominant["traffic_source"] = ("ncu DRAM bytes per unit on a smaller case, scaled by this workload's units "
-                                  "(profiles/dram_traffic.md)")
+                                  "(profiles/dram_traffic.json)")
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -348,6 +384,7 @@ def run_gpu(args):
                      "trials": [dict({k: v for k, v in t["settings"].items() if k != "bg"}, ms=round(t["ms"], 3))
                                 for t in tune_log]},
         "clocks": clk.summary(),
+        "alu_peak": alu,
     }
 
     # ---- the same views as 16 plain launches (one view each)
@@ -512,36 +549,45 @@ def run_gpu(args):
         del r4, m4, i4, t4, g4, sc4
         torch.cuda.empty_cache()
 
-    # ---- end to end: host (pinned) parameters and targets in, loss out, every step.  The
-    # inputs are double-buffered: while step k runs on the compute stream, the copies of
-    # step k + 1's inputs run on a copy stream into the other buffer.  Each buffer's step is
-    # captured as two graphs, the forward and then the loss with the backward, so that a
-    # step's forward waits only for its parameters and its targets arrive during the
-    # forward.  Every step's copies are in the timed region; the first step's parameters
-    # are not overlapped.
+    # ---- end to end: host (pinned) parameters and targets in, loss and every parameter
+    # gradient plane out, every step.  The inputs are double-buffered: while step k runs on
+    # the compute stream, the copies of step k + 1's inputs run on a copy stream into the
+    # other buffer.  Each buffer's step is captured as two graphs, the forward and then the
+    # loss with the backward, so that a step's forward waits only for its parameters and its
+    # targets arrive during the forward.  Each buffer has its own gradient planes, read back
+    # into pinned host memory on a second copy stream (the other direction of the link)
+    # while the next step runs; a buffer's planes are rewritten only after that read-back.
+    # Every step's copies are in the timed region, and the timed region ends after the last
+    # step's gradients have reached the host.
     host_planes = {p: (None if t is None else t.cpu().pin_memory()) for p, t in model.planes.items()}
     host_target = target.cpu().pin_memory()
     h2d = sum(t.numel() * 4 for t in host_planes.values() if t is not None) + host_target.numel() * 4
-    loss_host = torch.empty(1).pin_memory()
+    loss_host = [torch.empty(1).pin_memory(), torch.empty(1).pin_memory()]
     model_b = model.with_planes(**{p: t.clone() for p, t in model.planes.items() if t is not None})
     target_b = target.clone()
+    grad_sets = [grads, model.empty_grads()]
+    host_grads = [{p: (None if t is None else torch.empty(t.shape, dtype=t.dtype).pin_memory())
+                   for p, t in g.items()} for g in grad_sets]
+    d2h = sum(t.numel() * 4 for t in grads.values() if t is not None) + 4
 
-    def capture_split(m, t):
+    def capture_split(m, t, g):
         torch.cuda.synchronize()
         gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
         with torch.cuda.graph(gf):
             rast.forward(m, out_rgb=img, sync=False)
         with torch.cuda.graph(gb):
             loss, dimg = l1_loss(img, t)
-            rast.backward(m, dimg, grads=grads)
+            rast.backward(m, dimg, grads=g)
         return gf, gb, loss
 
     bufs = [(model, target), (model_b, target_b)]
-    splits = [capture_split(m, t) for m, t in bufs]
-    copy_stream = torch.cuda.Stream()
+    splits = [capture_split(m, t, g) for (m, t), g in zip(bufs, grad_sets)]
+    copy_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
     params_in = [torch.cuda.Event(), torch.cuda.Event()]
     target_in = [torch.cuda.Event(), torch.cuda.Event()]
     consumed = [torch.cuda.Event(), torch.cuda.Event()]
+    grads_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    grads_read = [torch.cuda.Event(), torch.cuda.Event()]
 
     def upload(k):  # inputs of step k into buffer k % 2, on the copy stream
         m, t = bufs[k % 2]
@@ -555,18 +601,33 @@ def run_gpu(args):
             t.copy_(host_target, non_blocking=True)
             target_in[k % 2].record(copy_stream)
 
+    def download(k):  # gradients and loss of step k to the host, on the second copy stream
+        b = k % 2
+        with torch.cuda.stream(d2h_stream):
+            d2h_stream.wait_event(grads_ready[b])
+            for p, t in grad_sets[b].items():
+                if t is not None:
+                    host_grads[b][p].copy_(t, non_blocking=True)
+            loss_host[b].copy_(splits[b][2], non_blocking=True)
+            grads_read[b].record(d2h_stream)
+
     def e2e_run(steps):
         upload(0)
         for k in range(steps):
-            gf, gb, gl = splits[k % 2]
-            stream.wait_event(params_in[k % 2])
+            b = k % 2
+            gf, gb, _ = splits[b]
+            stream.wait_event(params_in[b])
             gf.replay()
-            stream.wait_event(target_in[k % 2])
+            stream.wait_event(target_in[b])
+            if k >= 2:
+                stream.wait_event(grads_read[b])  # step k - 2's gradients have left this buffer
             gb.replay()
-            consumed[k % 2].record(stream)
-            loss_host.copy_(gl, non_blocking=True)
+            consumed[b].record(stream)
+            grads_ready[b].record(stream)
+            download(k)
             if k + 1 < steps:
                 upload(k + 1)
+        stream.wait_stream(d2h_stream)
 
     e2e_run(2)
     torch.cuda.synchronize()
@@ -579,10 +640,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ems = max_over_ranks(a.elapsed_time(b2) / args.steps)
     out["e2e"] = {"value": round(job_rate(world, nv, ems), 3), "unit": UNIT, "ms_per_step": round(ems, 4),
-                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4,
-                  "overlap": "step k+1's uploads on a copy stream during step k (double-buffered inputs); "
-                             "a step's targets arrive during its forward"}
-    del splits, bufs, model_b, target_b
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                  "overlap": "step k+1's uploads (parameters, targets) on one copy stream and step k's "
+                             "read-back (all gradient planes, loss) on another during the compute; "
+                             "double-buffered inputs and gradients"}
+    del splits, bufs, model_b, target_b, grad_sets, host_grads
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only); same sample checks parity
     if rank == 0 and world == 1 and args.cpu_baseline:

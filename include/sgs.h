@@ -275,6 +275,13 @@ sgs_status sgs_sort_pairs32(uint32_t* keys, uint32_t* vals, int64_t m, int32_t k
  * process exits.
  *  - m must not exceed SGS_SORT_NOALLOC_MAX_PAIRS; a larger m (or other bad argument)
  *    returns SGS_ERR_INVALID and enqueues nothing.
+ *  - digit_bits must be 4..8 (sgs_sort_pairs takes up to 10): the histogram, offset and
+ *    look-back tables of the fixed array are sized for digits of at most 8 bits (radix
+ *    256, up to 16 passes); 9 or 10 returns SGS_ERR_INVALID.
+ *  - A bounded look-back wait that ran out (SGS_ERR_TIMEOUT in sgs_sort_pairs's status
+ *    word) is not reported by this entry point: the status word lives in the fixed array,
+ *    which no entry point reads back.  Such a wait only runs out after about a second of
+ *    polling an unpublished slot, which a healthy GPU does not do.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call before any
  *    stream capture on the device.  A failed lookup returns SGS_ERR_CUDA.
@@ -336,6 +343,17 @@ sgs_status sgs_adam_step(const sgs_gaussians* layout, const sgs_grads* raw, cons
  * host (SGS_ERR_INVALID for num_slots < 0 or a null pointer); asynchronous on `stream`. */
 sgs_status sgs_selftest_lookback(const uint64_t* slots, int64_t num_slots, uint64_t* sum,
                                  int32_t* status, cudaStream_t stream);
+
+/* Measurement helper (the paper has no counterpart): the device's FP32 arithmetic
+ * throughput, the peak against which the blend kernels (bound by the FP32 pipes and issue
+ * slots) are reported.  One launch of sgs_alu_probe_size() threads (a multiple of the
+ * multiprocessor count), each running 8 independent chains of `iters` multiply-adds,
+ * scalar fma.rn.f32 (packed = 0) or packed fma.rn.f32x2 (packed = 1, two FP32 operations
+ * per instruction).  out: device float[threads] (written, prevents dead-code removal);
+ * *fp32_ops: the FP32 operations enqueued (a multiply-add counted as one), for the caller
+ * to divide by the launch time it measures with CUDA events.  Asynchronous on `stream`. */
+sgs_status sgs_alu_probe_size(int64_t* threads);
+sgs_status sgs_alu_probe(int32_t packed, int32_t iters, float* out, double* fp32_ops, cudaStream_t stream);
 
 const char* sgs_status_string(sgs_status s);
 

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsgs.so")
-SOURCES = ["api.cu", "preprocess.cu", "binning.cu", "sort.cu", "blend.cu", "sort_noalloc.cu", "optim.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "binning.cu", "sort.cu", "blend.cu", "sort_noalloc.cu", "optim.cu", "probe.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("common.cuh", "colour.cuh", "kernels.h")] + \
           [os.path.join(INCLUDE, "sgs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -464,7 +464,7 @@ cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t count, cudaStrea
     if (count == 0) return cudaSuccess;
     const int threads = 256;
     const size_t want = (count + threads - 1) / threads;
-    const int blocks = (int)(want < 148 * 32 ? want : 148 * 32);
+    const int blocks = (int)stride_grid((int64_t)want, 32);
     fill_u32_kernel<<<blocks, threads, 0, s>>>(p, value, count);
     return cudaGetLastError();
 }
@@ -496,7 +496,7 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
     if (passes > (32 + digit_bits - 1) / digit_bits) return cudaErrorInvalidValue;
     const int threads = 256;
     const int64_t want = (R + threads - 1) / threads;
-    const unsigned blocks = (unsigned)(want < 148 * 8 ? want : 148 * 8);
+    const unsigned blocks = (unsigned)stride_grid(want, 8);
     switch (digit_bits) {
 #define SGS_DUP(RB) case RB: duplicate_kernel<RB><<<blocks, threads, 0, s>>>(vt, p.spans, record_value(R), p.rec0, \
         p.rec1, perm, offsets, n, R, st, capacity, keys, vals, passes, hist); break;
@@ -519,7 +519,7 @@ cudaError_t launch_ranges(const uint32_t* keys, const DeviceStatus* st, int64_t 
     if (capacity == 0) return cudaSuccess;
     const int threads = 256;
     const int64_t want = (capacity / 4 + threads) / threads;
-    const int blocks = (int)(want < 148 * 32 ? want : 148 * 32);
+    const int blocks = (int)stride_grid(want, 32);
     ranges_kernel<<<blocks, threads, 0, s>>>(keys, st, (uint32_t)num_tiles, ranges);
     return cudaGetLastError();
 }
@@ -536,7 +536,7 @@ cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int64_t want = (R + threads - 1) / threads;
-    const unsigned blocks = (unsigned)(want < 1 ? 1 : (want < 148 * 8 ? want : 148 * 8));
+    const unsigned blocks = (unsigned)stride_grid(want, 8);
     const size_t smem = (size_t)8 * passes * ((size_t)1 << rb) * sizeof(uint32_t);
     switch (rb) {
 #define SGS_RH(RB)                                                                                              \

@@ -925,7 +925,7 @@ cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count,
     l1_zero_kernel<<<1, 1, 0, s>>>(loss);
     if (count > 0) {
         const int64_t want = (count + 255) / 256;
-        l1_kernel<<<(int)(want < 148 * 8 ? want : 148 * 8), 256, 0, s>>>(img, target, count, loss, dL_dimg);
+        l1_kernel<<<(int)stride_grid(want, 8), 256, 0, s>>>(img, target, count, loss, dL_dimg);
     }
     return cudaGetLastError();
 }

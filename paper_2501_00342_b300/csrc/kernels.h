@@ -2,9 +2,30 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace sgs {
+
+// Streaming multiprocessors of the current device, read from the device once per device.
+// The grid-stride kernels size their grids as a multiple of it.
+inline int sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    cached[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
+// Grid of a grid-stride loop: enough CTAs for `want`, at most per_sm per multiprocessor.
+inline int64_t stride_grid(int64_t want, int per_sm) {
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    return want < 1 ? 1 : (want < cap ? want : cap);
+}
 
 // Records a timing probe on s.  While s is being captured into a CUDA graph the record
 // becomes an event-record node of the graph (a plain record would only mark a fork point).

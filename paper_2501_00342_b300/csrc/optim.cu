@@ -141,7 +141,7 @@ cudaError_t launch_adam(const sgs_gaussians& layout, const sgs_grads& raw, const
     if (layout.n == 0 || t.rows == 0) return cudaSuccess;
     const int64_t work = (layout.n + 3) / 4 * t.rows;
     const int64_t want = (work + 255) / 256;
-    adam_kernel<<<(unsigned)(want < 148 * 16 ? want : 148 * 16), 256, 0, s>>>(t);
+    adam_kernel<<<(unsigned)stride_grid(want, 16), 256, 0, s>>>(t);
     return cudaGetLastError();
 }
 

@@ -346,7 +346,7 @@ cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
     }
     if (!histogram_ready) {
         const int64_t want = (capacity + 255) / 256;
-        const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
+        const int blocks = (int)stride_grid(want, 8);
         const size_t hs = (size_t)passes * RADIX * sizeof(uint32_t);
         if ((e = cudaFuncSetAttribute(histogram_kernel<KeyT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)hs)) != cudaSuccess)
@@ -427,7 +427,7 @@ template <typename KeyT>
 cudaError_t copy_pairs_t(const KeyT* ks, const uint32_t* vs, KeyT* kd, uint32_t* vd, int64_t m, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     const int64_t want = (m + 255) / 256;
-    copy_pairs_kernel<KeyT><<<(int)(want < 148 * 16 ? want : 148 * 16), 256, 0, s>>>(ks, vs, kd, vd, m);
+    copy_pairs_kernel<KeyT><<<(int)stride_grid(want, 16), 256, 0, s>>>(ks, vs, kd, vd, m);
     return cudaGetLastError();
 }
 }  // namespace

@@ -15,6 +15,9 @@ sizes, so the checks are sampled:
 * gradients: dL/dpixel non-zero on the sampled patches only; every parameter plane against
   the FP64 adjoint of those pixels, |g - g*| <= 1e-3 max(|g*|, 1e-3 max|g*|) per element
   (cancelling entries: see tests.helpers.check_gradients).
+
+Workloads 3 and 4 run twice: with the default settings (16x16 tiles, 256 Gaussians per
+batch) and with the settings the benchmark times (TUNED below).
 """
 import numpy as np
 import pytest
@@ -33,17 +36,28 @@ AMBIGUOUS = 1e-5
 SUBSET = 20_000
 
 
-@pytest.fixture(scope="module", params=[1, 2, 3, 4, "2-adaptive"])
+# The launch settings of the benchmark's timed step: 32x32 tiles (CTAs of 512 threads, a
+# 15-bit tile sort in 2 passes), 1024 Gaussians per shared-memory batch, 9-bit digits, the
+# two-pixel forward and backward kernels.
+TUNED = RenderSettings(tile_w=32, tile_h=32, batch_depth=1024, digit_bits=9, fwd_pixels=2, bwd_pixels=2)
+
+
+@pytest.fixture(scope="module", params=[1, 2, 3, 4, "2-adaptive", "3-tuned", "4-tuned"])
 def full(request):
     config = request.param
+    settings = RenderSettings()
     if config == "2-adaptive":  # degree-2 storage, bands 0 / 0-1 / 0-2 below 4 / 16 pixels
         config = 2
         sc, cams = I.workload(2, sh_degree=2)
         sc.sh_adaptive, sc.sh_radius = 1, (4.0, 16.0)
+    elif isinstance(config, str) and config.endswith("-tuned"):
+        config = int(config[0])
+        settings = TUNED
+        sc, cams = I.workload(config)
     else:
         sc, cams = I.workload(config)
     model = GaussianModel.from_scene(sc)
-    rast = Rasterizer(model, cams, RenderSettings())
+    rast = Rasterizer(model, cams, settings)
     img = rast.forward(model, sync=True)
     torch.cuda.synchronize()
     assert rast.device_status() == 0
@@ -117,8 +131,9 @@ def test_instance_invariants(full):
     # the record sort's values carry a record's tile count in the 32 - ceil(log2 R) bits
     # above its id; larger counts saturate and are read back from TILES.  The 8M x 8-view
     # 4K workload (R = 6.4e7, 6 count bits) has records past the saturation, so the sorted
-    # instances checked here cover that path.
-    if config == 4:
+    # instances checked here cover that path (with 16x16 tiles; 32x32 tiles cut the counts
+    # by about 4x).
+    if config == 4 and rast.settings.tile_w == 16:
         id_bits = max(1, int(R - 1).bit_length())
         assert int(tiles.max().item()) >= (1 << (32 - id_bits)) - 1
     keys = rast.region("KEYS", torch.int32)[:M]  # tile ids < 2^31: signed order is the order
