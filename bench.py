@@ -10,8 +10,9 @@ times from CUDA events inside the timed region, the roofline of the dominant ker
 end-to-end number through host buffers, and the CPU oracle timed on a bounded sample.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-Under torchrun each rank renders its own batch (weak scaling, no collective on the data
-path); times are the max over ranks.
+Under torchrun each rank renders its own batch against a replica of the Gaussians (weak
+scaling) and every step ends with one all-reduce of the gradient planes (view-sharded
+training's exchange); times are the max over ranks.
 """
 from __future__ import annotations
 
@@ -172,6 +173,7 @@ def run_gpu(args):
 
     from paper_2501_00342_b300 import binding as B
     from paper_2501_00342_b300.render import GaussianModel, Rasterizer, RenderSettings, l1_loss
+    from paper_2501_00342_b300.train import GradientBucket
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -209,11 +211,28 @@ def run_gpu(args):
     rast.forward(model, out_rgb=img, sync=True)  # sizes the instance capacity
     M = rast.num_instances
     rast = Rasterizer(model, cams, settings, capacity=int(M * 1.02) + 4096)
-    grads = model.empty_grads()
+    # Under torchrun every rank renders its own batch of views against a replica of the
+    # Gaussians (the same 16 cameras on every rank in this synthetic workload) and the step
+    # ends with the one exchange of view-sharded training: an all-reduce (sum) of all the
+    # gradient planes, held in one flat buffer.  The L1 of each rank is normalised by the
+    # pixel values of all ranks, so the summed gradient is that of the job's mean L1.
+    norm = world * img.numel() if world > 1 else None
+
+    def make_grads():
+        if world == 1:
+            return model.empty_grads(), None
+        bucket = GradientBucket(model)
+        return bucket.planes, bucket
+
+    grads, bucket = make_grads()
+
+    def exchange(bk):
+        if bk is not None:
+            bk.allreduce()
 
     def step(sync=False):
         rast.forward(model, out_rgb=img, sync=sync)
-        loss, dimg = l1_loss(img, target)
+        loss, dimg = l1_loss(img, target, norm=norm)
         rast.backward(model, dimg, grads=grads)
         return loss
 
@@ -232,11 +251,13 @@ def run_gpu(args):
     B.set_events(rast.plan, handles)
     for _ in range(args.warmup):
         step()
+        exchange(bucket)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
         step()
+        exchange(bucket)
     t1.record(stream)
     torch.cuda.synchronize()
     eager_ms = t0.elapsed_time(t1) / args.steps
@@ -254,12 +275,14 @@ def run_gpu(args):
     graph.instantiate()
     for _ in range(args.warmup):
         graph.replay()
+        exchange(bucket)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t0.record(stream)
         for _ in range(args.steps):
             graph.replay()
+            exchange(bucket)
         t1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -373,7 +396,9 @@ def run_gpu(args):
                    "bwd_pixels": settings.bwd_pixels,
                    "l2": f"inputs larger than L2: {n * p_bytes / 1e6:.0f} MB parameters, "
                          f"{rast.nbytes / 1e9:.2f} GB workspace",
-                   "parallelism": f"view batches per rank x{world}"},
+                   "parallelism": (f"view-sharded x{world}: each rank renders its own 16-view batch, one "
+                                   f"all-reduce of the gradient planes per step") if world > 1
+                                  else "one GPU, one 16-view batch per step"},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "blend_evaluations": e_eval, "blend_contributions": e_contrib, "visible_records": visible,
         "roofline": dominant, "roofline_all": roofs,
@@ -565,7 +590,8 @@ def run_gpu(args):
     loss_host = [torch.empty(1).pin_memory(), torch.empty(1).pin_memory()]
     model_b = model.with_planes(**{p: t.clone() for p, t in model.planes.items() if t is not None})
     target_b = target.clone()
-    grad_sets = [grads, model.empty_grads()]
+    second = make_grads()
+    grad_sets, buckets = [grads, second[0]], [bucket, second[1]]
     host_grads = [{p: (None if t is None else torch.empty(t.shape, dtype=t.dtype).pin_memory())
                    for p, t in g.items()} for g in grad_sets]
     d2h = sum(t.numel() * 4 for t in grads.values() if t is not None) + 4
@@ -576,7 +602,7 @@ def run_gpu(args):
         with torch.cuda.graph(gf):
             rast.forward(m, out_rgb=img, sync=False)
         with torch.cuda.graph(gb):
-            loss, dimg = l1_loss(img, t)
+            loss, dimg = l1_loss(img, t, norm=norm)
             rast.backward(m, dimg, grads=g)
         return gf, gb, loss
 
@@ -622,6 +648,7 @@ def run_gpu(args):
             if k >= 2:
                 stream.wait_event(grads_read[b])  # step k - 2's gradients have left this buffer
             gb.replay()
+            exchange(buckets[b])
             consumed[b].record(stream)
             grads_ready[b].record(stream)
             download(k)

@@ -300,6 +300,14 @@ sgs_status sgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t m, int
 sgs_status sgs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
                        float* dL_dimg, cudaStream_t stream);
 
+/* sgs_l1_loss with the normaliser given: loss[0] = scale * sum |img - target|, dL_dimg =
+ * scale * sign(img - target), scale >= 0 (else SGS_ERR_INVALID).  In view-sharded
+ * training each rank renders its own views and passes scale = 1 / (the pixel values of
+ * all ranks' views), so that the sum over ranks of the losses and of the parameter
+ * gradients is the mean absolute error over every view and its gradient. */
+sgs_status sgs_l1_loss_scaled(const float* img, const float* target, int64_t count, float scale, float* loss,
+                              float* dL_dimg, cudaStream_t stream);
+
 /* ---- Training: fused Adam step over the parameter planes ----
  * The optimiser works on raw planes (same layouts as sgs_gaussians): scale holds log s and
  * opacity holds logit o (the 3D-GS activations), every other plane is the parameter

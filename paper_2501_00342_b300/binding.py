@@ -28,7 +28,7 @@ EXPORTS = ("sgs_workspace_size", "sgs_preprocess", "sgs_bin_sort", "sgs_render",
            "sgs_render_backward", "sgs_read_device_status", "sgs_region_info",
            "sgs_sort_temp_bytes", "sgs_sort_pairs", "sgs_l1_loss", "sgs_status_string",
            "sgs_abi_sizes", "sgs_set_events", "sgs_sort_pairs_noalloc", "sgs_selftest_lookback",
-           "sgs_sort_pairs32", "sgs_adam_step", "sgs_alu_probe_size", "sgs_alu_probe")
+           "sgs_sort_pairs32", "sgs_adam_step", "sgs_alu_probe_size", "sgs_alu_probe", "sgs_l1_loss_scaled")
 
 SORT_NOALLOC_MAX_PAIRS = 1 << 18
 
@@ -125,6 +125,8 @@ def lib():
         L.sgs_adam_step.restype = st
         L.sgs_selftest_lookback.argtypes = [vp, i64, vp, vp, vp]
         L.sgs_selftest_lookback.restype = st
+        L.sgs_l1_loss_scaled.argtypes = [vp, vp, i64, C.c_float, vp, vp, vp]
+        L.sgs_l1_loss_scaled.restype = st
         L.sgs_alu_probe_size.argtypes = [P(C.c_int64)]
         L.sgs_alu_probe_size.restype = st
         L.sgs_alu_probe.argtypes = [i32, i32, vp, P(C.c_double), vp]
@@ -270,6 +272,11 @@ def selftest_lookback(slots_ptr, num_slots, sum_ptr, status_ptr, stream):
 
 def l1_loss(img_ptr, target_ptr, count, loss_ptr, grad_ptr, stream):
     check("sgs_l1_loss", lib().sgs_l1_loss(img_ptr, target_ptr, int(count), loss_ptr, grad_ptr, stream))
+
+
+def l1_loss_scaled(img_ptr, target_ptr, count, scale, loss_ptr, grad_ptr, stream):
+    check("sgs_l1_loss_scaled",
+          lib().sgs_l1_loss_scaled(img_ptr, target_ptr, int(count), float(scale), loss_ptr, grad_ptr, stream))
 
 
 def alu_probe_size() -> int:

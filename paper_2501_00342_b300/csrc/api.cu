@@ -558,7 +558,14 @@ sgs_status sgs_adam_step(const sgs_gaussians* layout, const sgs_grads* raw, cons
 sgs_status sgs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
                        float* dL_dimg, cudaStream_t stream) {
     if (count < 0 || !loss || (count > 0 && (!img || !target || !dL_dimg))) return SGS_ERR_INVALID;
-    SGS_TRY(launch_l1_loss(img, target, count, loss, dL_dimg, stream));
+    SGS_TRY(launch_l1_loss(img, target, count, count > 0 ? 1.0f / (float)count : 0.0f, loss, dL_dimg, stream));
+    return SGS_OK;
+}
+
+sgs_status sgs_l1_loss_scaled(const float* img, const float* target, int64_t count, float scale, float* loss,
+                              float* dL_dimg, cudaStream_t stream) {
+    if (count < 0 || !loss || (count > 0 && (!img || !target || !dL_dimg)) || !(scale >= 0.0f)) return SGS_ERR_INVALID;
+    SGS_TRY(launch_l1_loss(img, target, count, scale, loss, dL_dimg, stream));
     return SGS_OK;
 }
 

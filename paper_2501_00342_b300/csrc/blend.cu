@@ -793,8 +793,7 @@ __global__ void __launch_bounds__(512) blend_pair_backward_kernel(
 __global__ void l1_zero_kernel(float* loss) { *loss = 0.0f; }
 
 __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                  int64_t count, float* loss, float* __restrict__ grad) {
-    const float inv = 1.0f / (float)count;
+                                                  int64_t count, float inv, float* loss, float* __restrict__ grad) {
     float acc = 0.0f;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -920,12 +919,12 @@ cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R,
     return cudaMemsetAsync(grad2d, 0, (size_t)R * (2 * sizeof(float4) + sizeof(float)), s);
 }
 
-cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float* loss,
+cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float scale, float* loss,
                            float* dL_dimg, cudaStream_t s) {
     l1_zero_kernel<<<1, 1, 0, s>>>(loss);
     if (count > 0) {
         const int64_t want = (count + 255) / 256;
-        l1_kernel<<<(int)stride_grid(want, 8), 256, 0, s>>>(img, target, count, loss, dL_dimg);
+        l1_kernel<<<(int)stride_grid(want, 8), 256, 0, s>>>(img, target, count, scale, loss, dL_dimg);
     }
     return cudaGetLastError();
 }

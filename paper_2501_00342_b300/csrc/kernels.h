@@ -164,7 +164,8 @@ cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R,
 cudaError_t launch_adam(const sgs_gaussians& layout, const sgs_grads& raw, const sgs_grads& act,
                         const sgs_grads& grad, const sgs_grads& m, const sgs_grads& v, const sgs_adam_config& cfg,
                         cudaStream_t s);
-cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float* loss,
+// loss[0] = scale * sum |img - target|, dL_dimg = scale * sign(img - target)
+cudaError_t launch_l1_loss(const float* img, const float* target, int64_t count, float scale, float* loss,
                            float* dL_dimg, cudaStream_t s);
 cudaError_t launch_copy_pairs(const unsigned long long* ks, const uint32_t* vs, unsigned long long* kd,
                               uint32_t* vd, int64_t m, cudaStream_t s);

@@ -182,9 +182,15 @@ def render(rast: Rasterizer, model: GaussianModel) -> torch.Tensor:
     return _RenderFunction.apply(rast, model, *[model.planes[p] for p in PLANES])
 
 
-def l1_loss(img: torch.Tensor, target: torch.Tensor):
-    """Mean absolute error and its gradient, computed by the library's kernel."""
+def l1_loss(img: torch.Tensor, target: torch.Tensor, norm: Optional[int] = None):
+    """Mean absolute error and its gradient, computed by the library's kernel.  With
+    ``norm`` the sum is divided by ``norm`` instead of the element count (view-sharded
+    training: the element count of every rank's views)."""
     loss = torch.empty(1, dtype=torch.float32, device=img.device)
     grad = torch.empty_like(img)
-    B.l1_loss(img.data_ptr(), target.data_ptr(), img.numel(), loss.data_ptr(), grad.data_ptr(), _stream())
+    if norm is None:
+        B.l1_loss(img.data_ptr(), target.data_ptr(), img.numel(), loss.data_ptr(), grad.data_ptr(), _stream())
+    else:
+        B.l1_loss_scaled(img.data_ptr(), target.data_ptr(), img.numel(), 1.0 / norm, loss.data_ptr(),
+                         grad.data_ptr(), _stream())
     return loss, grad

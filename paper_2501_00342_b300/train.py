@@ -1,5 +1,6 @@
 """Training loop of the rasterizer: render -> L1 loss -> backward -> fused Adam step, all in
-the library's kernels (four calls per step after the forward's three).
+the library's kernels (four calls per step after the forward's three), on one GPU or
+view-sharded over several (ShardedTrainer: one all-reduce of the gradients per step).
 
 The optimiser owns raw planes (log-scale, logit-opacity, the rest as is) and the activated
 planes the renderer reads; identity planes are shared.  Learning rates follow the 3D-GS
@@ -95,3 +96,75 @@ class Trainer:
 
 def numpy_planes(model: GaussianModel) -> Dict[str, Optional[np.ndarray]]:
     return {p: (None if t is None else t.detach().cpu().numpy().astype(np.float64)) for p, t in model.planes.items()}
+
+
+# ------------------------------------------------------------------ view-sharded training
+def shard_views(num_views: int, world: int, rank: int) -> range:
+    """The views of rank ``rank`` when ``num_views`` views are split over ``world`` ranks:
+    a contiguous block, the first ``num_views % world`` ranks one view more."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError(f"rank {rank} of {world}")
+    base, extra = divmod(num_views, world)
+    start = rank * base + min(rank, extra)
+    return range(start, start + base + (1 if rank < extra else 0))
+
+
+class GradientBucket:
+    """Every gradient plane of a model as a view into one flat buffer, so that the
+    exchange of a view-sharded step is a single all-reduce.  ``planes`` has the layout of
+    ``GaussianModel.empty_grads`` (padding entries zero)."""
+
+    def __init__(self, model: GaussianModel, dtype=torch.float32, device=None):
+        device = device if device is not None else model.planes["mean"].device
+        shapes = {p: (None if t is None else tuple(t.shape)) for p, t in model.planes.items()}
+        total = sum(int(np.prod(sh)) for sh in shapes.values() if sh is not None)
+        # planes start on 16-byte boundaries: every plane's length is a multiple of the
+        # stride, itself a multiple of 4 floats
+        self.flat = torch.zeros(total, dtype=dtype, device=device)
+        self.planes: Dict[str, Optional[torch.Tensor]] = {}
+        off = 0
+        for p in PLANES:
+            sh = shapes[p]
+            if sh is None:
+                self.planes[p] = None
+                continue
+            k = int(np.prod(sh))
+            self.planes[p] = self.flat[off:off + k].view(sh)
+            off += k
+
+    def allreduce(self, group=None) -> None:
+        """Sums the buffer over the ranks of ``group`` in place (every rank gets the sum)."""
+        import torch.distributed as dist
+        dist.all_reduce(self.flat, op=dist.ReduceOp.SUM, group=group)
+
+
+class ShardedTrainer(Trainer):
+    """Data-parallel training over views: each rank renders only its own cameras (its
+    shard of the batch) against a full replica of the Gaussians, the loss of every rank is
+    normalised by the pixel values of all ranks' views, the gradient planes (one flat
+    bucket) are summed over the ranks by one all-reduce, and every rank then runs the same
+    Adam step on its replica -- so the replicas stay identical and the step equals one-GPU
+    training on all the views at once (up to the order of the float additions).  The paper
+    trains on one GPU (Sec. "Experiment Settings"); this is the split its per-view
+    independence allows.  ``cams``/``targets`` are this rank's shard; ``total_values`` the
+    3 x pixels of every rank's views together."""
+
+    def __init__(self, model: GaussianModel, cams: Sequence, targets: torch.Tensor, total_values: int,
+                 settings: RenderSettings = RenderSettings(), config: TrainConfig = TrainConfig(), group=None):
+        super().__init__(model, cams, targets, settings, config)
+        self.group, self.total_values = group, int(total_values)
+        self.bucket = GradientBucket(model)
+        self.grads = self.bucket.planes
+        self._structs = [_grads_struct(d) for d in (self.raw, self.act, self.grads, self.m, self.v)]
+
+    def step(self, sync: bool = False) -> torch.Tensor:
+        """One iteration; returns this rank's share of the loss (the all-reduced sum of the
+        shares is the mean absolute error over every view)."""
+        stream = torch.cuda.current_stream().cuda_stream
+        self.rast.forward(self.model, out_rgb=self.img, sync=sync)
+        loss, dimg = l1_loss(self.img, self.target, norm=self.total_values)
+        self.rast.backward(self.model, dimg, grads=self.grads)
+        self.bucket.allreduce(self.group)
+        B.adam_step(self.model.struct(), *self._structs, self.adam_config(self.iteration), stream)
+        self.iteration += 1
+        return loss

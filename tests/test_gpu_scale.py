@@ -70,7 +70,8 @@ def test_records_of_sampled_gaussians(full):
     config, sc, cams, model, rast, _ = full
     idx = np.sort(np.random.default_rng(config).choice(sc.n, min(SUBSET, sc.n), replace=False))
     sub = sc.subset(idx)
-    m = O.mirror_preprocess(sub, cams)
+    st = rast.settings
+    m = O.mirror_preprocess(sub, cams, st.tile_w, st.tile_h)
     R = sc.n * len(cams)
     rows = torch.from_numpy((np.arange(len(cams))[:, None] * sc.n + idx[None, :]).ravel()).cuda()
     rec0 = rast.region("REC0", torch.float32)[:4 * R].view(R, 4)[rows].cpu().numpy()
@@ -114,7 +115,7 @@ def test_sorted_instances_of_sampled_gaussians(full):
         got_d.append(depth[v[keep]].cpu().numpy().view(np.uint32))
     sub_vals = np.concatenate(got_v).astype(np.uint32)
     keys = (np.concatenate(got_t).astype(np.uint64) << np.uint64(32)) | np.concatenate(got_d).astype(np.uint64)
-    b = O.mirror_bin(sc.subset(idx), cams)
+    b = O.mirror_bin(sc.subset(idx), cams, rast.settings.tile_w, rast.settings.tile_h)
     assert len(b["keys"]) > 1000
     assert len(keys) == len(b["keys"])
     assert (keys == b["keys"]).all()

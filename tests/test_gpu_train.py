@@ -7,7 +7,7 @@ import torch
 from oracle import adam as A
 from paper_2501_00342_b300 import binding as B
 from paper_2501_00342_b300 import inputs as I
-from paper_2501_00342_b300.render import PLANES, GaussianModel, Rasterizer, RenderSettings
+from paper_2501_00342_b300.render import PLANES, GaussianModel, Rasterizer, RenderSettings, l1_loss
 from paper_2501_00342_b300.train import TrainConfig, Trainer
 from tests.helpers import axis_camera, random_small_scene
 
@@ -88,3 +88,80 @@ def test_training_fits_and_introduces_lobes_late():
     assert not torch.equal(model.planes["sg_amp"], sg0["sg_amp"])  # and trained after
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
     assert tr.rast.device_status() == 0
+
+
+def _views_problem():
+    sc = random_small_scene(400, seed=80, sh_degree=1, K=4, axis_mode=I.AXIS_FREE)
+    cams = I.orbit_cameras(4, [64, 48, 80, 32], [48, 64, 40, 32], fov_x_deg=55.0, radius=3.2)
+    targets = [torch.from_numpy(t.reshape(-1)).cuda() for t in I.target_images(cams, config=2, stream=13)]
+    return sc, cams, targets
+
+
+def test_view_shards_sum_to_the_batched_gradient():
+    """The kernels' side of view-sharded training: two shards of the views, each with its L1
+    normalised by the pixel values of all views, give gradients whose sum is the gradient of
+    the mean L1 over every view rendered in one batched launch."""
+    sc, cams, targets = _views_problem()
+    model = GaussianModel.from_scene(sc)
+    total = sum(3 * c.width * c.height for c in cams)
+    full = Rasterizer(model, cams, RenderSettings())
+    img = full.forward(model)
+    loss_all, d_all = l1_loss(img, torch.cat(targets))
+    g_all = full.backward(model, d_all)
+    summed, loss_sum = None, 0.0
+    for shard in (range(0, 1), range(1, 4)):
+        r = Rasterizer(model, [cams[v] for v in shard], RenderSettings())
+        im = r.forward(model)
+        loss, d = l1_loss(im, torch.cat([targets[v] for v in shard]), norm=total)
+        loss_sum += float(loss.item())
+        g = r.backward(model, d)
+        summed = g if summed is None else {p: (None if t is None else t + g[p]) for p, t in summed.items()}
+    torch.cuda.synchronize()
+    assert abs(loss_sum - float(loss_all.item())) <= 1e-6 * float(loss_all.item())
+    for p in PLANES:
+        if g_all[p] is None:
+            continue
+        scale = float(g_all[p].abs().max())
+        assert scale > 0, p
+        assert float((summed[p] - g_all[p]).abs().max()) <= 1e-5 * scale, p  # float atomics' order
+
+
+def test_sharded_trainer_with_one_rank_equals_trainer():
+    """ShardedTrainer over a one-rank NCCL group (its all-reduce is the identity) computes
+    the gradients and takes the step of the single-GPU Trainer.  Adam's first step moves an
+    entry by lr * sign(gradient), so the parameters are compared where the sign is certain
+    (the float atomics leave the gradients equal up to 1e-5 of their largest entry)."""
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_2501_00342_b300.train import ShardedTrainer
+    sc, cams, targets = _views_problem()
+    target = torch.cat(targets)
+    cfg = TrainConfig(iterations=100, sg_start=0)
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    group_made = not dist.is_initialized()
+    if group_made:
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", 0))
+    try:
+        a, b = GaussianModel.from_scene(sc), GaussianModel.from_scene(sc)
+        ta = Trainer(a, cams, target, RenderSettings(), cfg)
+        tb = ShardedTrainer(b, cams, target, target.numel(), RenderSettings(), cfg)
+        la, lb = ta.step(), tb.step()
+        torch.cuda.synchronize()
+        assert abs(float(la.item()) - float(lb.item())) <= 1e-6 * float(la.item())
+        for p in PLANES:
+            if a.planes[p] is None:
+                continue
+            ga, gb = ta.grads[p][..., :sc.n], tb.grads[p][..., :sc.n]
+            gmax = float(ga.abs().max())
+            assert gmax > 0 and float((ga - gb).abs().max()) <= 1e-5 * gmax, p
+            sure = ga.abs() > 1e-4 * gmax
+            pa, pb = a.planes[p][..., :sc.n], b.planes[p][..., :sc.n]
+            assert bool(sure.any())
+            assert float((pa - pb)[sure].abs().max()) <= 1e-6 * max(1.0, float(pa.abs().max())), p
+    finally:
+        if group_made:
+            dist.destroy_process_group()
