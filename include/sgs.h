@@ -134,6 +134,11 @@ typedef struct {
                                whose support holds it before it finished and the number it
                                blended (region SGS_REGION_PIX_COUNT); 0: not (faster).  May be
                                changed in the plan between calls. */
+    int32_t persistent;     /* 1: the two-pixel blend passes (forward and backward) run as
+                               persistent kernels -- as many CTAs as fit on the device at once,
+                               each claiming the next tile (most expensive first) from a
+                               counter in the workspace until none is left; 0: one CTA per
+                               tile, in the same order.  Results do not depend on it. */
 } sgs_settings;
 
 /* Host-side plan: sizes and workspace offsets.  Filled by sgs_workspace_size(); the

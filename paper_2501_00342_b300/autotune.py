@@ -4,8 +4,8 @@ batch, radix-sort digit width and the blend kernels' pixels per thread.
 The image does not depend on any of them (the support is the 3-sigma ellipse, not the
 tile), so they can be chosen for speed alone.  The tuner times one forward + backward
 step per candidate on the caller's own Gaussians and cameras (coordinate descent: tile
-size first, then batch depth, digit width and pixels per thread) and caches the winner per workload
-signature in a JSON file.
+size first, then batch depth, digit width, pixels per thread and persistent or one-CTA-per-tile
+blend kernels) and caches the winner per workload signature in a JSON file.
 """
 from __future__ import annotations
 
@@ -26,6 +26,7 @@ BATCHES: Tuple[int, ...] = (128, 256, 512, 1024)
 DIGITS: Tuple[int, ...] = (8, 9, 10)
 FWD_PIXELS: Tuple[int, ...] = (1, 2)
 BWD_PIXELS: Tuple[int, ...] = (2, 4)
+PERSISTENT: Tuple[int, ...] = (0, 1)
 
 
 def signature(model: GaussianModel, cams) -> str:
@@ -77,7 +78,8 @@ def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings()
              cache_path: Optional[str] = None, steps: int = 3,
              tiles: Sequence[Tuple[int, int]] = TILES, batches: Sequence[int] = BATCHES,
              digits: Sequence[int] = DIGITS, fwd_pixels: Sequence[int] = FWD_PIXELS,
-             bwd_pixels: Sequence[int] = BWD_PIXELS, log: Optional[List[Dict]] = None) -> RenderSettings:
+             bwd_pixels: Sequence[int] = BWD_PIXELS, persistent: Sequence[int] = PERSISTENT,
+             log: Optional[List[Dict]] = None) -> RenderSettings:
     """Best settings for this workload (from the cache when present)."""
     key = signature(model, cams)
     cache: Dict[str, Dict] = {}
@@ -91,7 +93,7 @@ def autotune(model: GaussianModel, cams, base: RenderSettings = RenderSettings()
     best_ms = _measure(model, cams, best, steps)
     trials = [dict(settings=dataclasses.asdict(best), ms=best_ms)]
     for field, values in (("tile", tiles), ("batch_depth", batches), ("digit_bits", digits),
-                          ("fwd_pixels", fwd_pixels), ("bwd_pixels", bwd_pixels)):
+                          ("fwd_pixels", fwd_pixels), ("bwd_pixels", bwd_pixels), ("persistent", persistent)):
         for v in values:
             if field == "tile":
                 cand = dataclasses.replace(best, tile_w=v[0], tile_h=v[1])

@@ -68,7 +68,8 @@ class AdamConfig(C.Structure):
 class Settings(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch_depth", C.c_int32),
                 ("digit_bits", C.c_int32), ("memory_mode", C.c_int32), ("bg", C.c_float * 3),
-                ("fwd_pixels", C.c_int32), ("bwd_pixels", C.c_int32), ("count_pairs", C.c_int32)]
+                ("fwd_pixels", C.c_int32), ("bwd_pixels", C.c_int32), ("count_pairs", C.c_int32),
+                ("persistent", C.c_int32)]
 
 
 class Plan(C.Structure):

@@ -94,6 +94,8 @@ ViewTable view_table(const sgs_plan* p) {
     vt.order = p->workspace ? region<uint32_t>(p, O_TORDER) : nullptr;
     vt.tile_top = p->workspace ? region<uint32_t>(p, O_TTOP) : nullptr;
     vt.masks = p->workspace ? region<uint16_t>(p, O_MASKS) : nullptr;
+    vt.persistent = p->settings.persistent ? 1 : 0;
+    vt.work = p->workspace ? region<DeviceStatus>(p, O_STATUS)->work : nullptr;
     for (int v = 0; v < p->B; ++v) {
         const sgs_camera& c = p->cams[v];
         View& w = vt.v[v];
@@ -186,6 +188,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     if (settings->count_pairs != 0 && settings->count_pairs != 1) return SGS_ERR_INVALID;
     if (settings->digit_bits < kMinDigitBits || settings->digit_bits > kMaxDigitBits) return SGS_ERR_INVALID;
     if (settings->memory_mode != 0) return SGS_ERR_INVALID;
+    if (settings->persistent != 0 && settings->persistent != 1) return SGS_ERR_INVALID;
     if (instance_capacity < 0 || instance_capacity > 0xffffffffll) return SGS_ERR_INVALID;
     std::memset(plan, 0, sizeof(*plan));
     plan->n = g->n;
@@ -393,6 +396,7 @@ sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const flo
     SGS_TRY(probe(plan, SGS_EV_BWD_ZERO_END, stream));
     ViewTable vtb = vt;
     vtb.order = region<uint32_t>(plan, O_BORDER);
+    vtb.work = region<DeviceStatus>(plan, O_STATUS)->work + 1;
     // the two-pixel kernels of both passes share warp blocks: the backward reads the masks
     // the forward stored
     if (!(vt.fwd_ppt == 2 && vt.bwd_ppt == 2)) vtb.masks = nullptr;

@@ -354,18 +354,19 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
 // each half rounded exactly as the scalar pass rounds it; the decisions and the colour
 // sums stay per pixel.
 template <bool COUNT>
-__global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, const uint2* __restrict__ ranges,
-                                                          const uint32_t* __restrict__ vals, uint32_t R,
-                                                          const float4* __restrict__ rec0,
-                                                          const float4* __restrict__ rec1,
-                                                          const float4* __restrict__ rec2, int batch,
-                                                          float bg0, float bg1, float bg2,
-                                                          float* __restrict__ out_rgb,
-                                                          float* __restrict__ out_T,
-                                                          float* __restrict__ pix_T,
-                                                          uint32_t* __restrict__ pix_last,
-                                                          uint2* __restrict__ pix_count,
-                                                          const DeviceStatus* __restrict__ st) {
+__device__ __forceinline__ void blend_pair_tile(const ViewTable& vt, const uint32_t tile,
+                                                const uint2* __restrict__ ranges,
+                                                const uint32_t* __restrict__ vals, uint32_t R,
+                                                const float4* __restrict__ rec0,
+                                                const float4* __restrict__ rec1,
+                                                const float4* __restrict__ rec2, int batch,
+                                                float bg0, float bg1, float bg2,
+                                                float* __restrict__ out_rgb,
+                                                float* __restrict__ out_T,
+                                                float* __restrict__ pix_T,
+                                                uint32_t* __restrict__ pix_last,
+                                                uint2* __restrict__ pix_count,
+                                                const DeviceStatus* __restrict__ st) {
     extern __shared__ float4 sbuf[];
     const float4* e_q = sbuf;              // (qa qa, qb qb)
     const float4* e_c = sbuf + batch;      // (qc qc, o o)
@@ -374,7 +375,6 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
     const int words = (batch + 31) >> 5;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairs) * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
-    const uint32_t tile = vt.order ? vt.order[blockIdx.x] : blockIdx.x;
     const TileCoord tc = tile_of(vt, tile);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<2>(vt);
@@ -456,6 +456,46 @@ __global__ void __launch_bounds__(512) blend_pair_kernel(const ViewTable vt, con
         if (COUNT) pix_count[cam.pixel_base + pi] = q ? make_uint2(ev1, ct1) : make_uint2(ev0, ct0);
     }
     write_backward_key(vt, tile, max(last0, last1));
+}
+
+// Tiles of a pass: the CTA's own (one CTA per tile, vt.order[blockIdx.x]) or, PERSIST,
+// every tile whose slot in vt.order the CTA claims from *work (one atomic per tile, the
+// slots in increasing order, i.e. the most expensive tiles first), until none is left.
+// The grid of a persistent launch is the number of CTAs resident at once.
+template <bool PERSIST, typename F>
+__device__ __forceinline__ void for_each_tile(const ViewTable& vt, uint32_t* work, F&& body) {
+    if (!PERSIST) {
+        body(vt.order ? vt.order[blockIdx.x] : blockIdx.x);
+        return;
+    }
+    __shared__ uint32_t s_slot;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint32_t slot = s_slot;
+        if ((int64_t)slot >= vt.num_tiles) break;  // uniform over the CTA
+        body(vt.order ? vt.order[slot] : slot);
+        __syncthreads();  // the claim word and the staging buffers are rewritten next
+    }
+}
+
+template <bool COUNT, bool PERSIST>
+__global__ void __launch_bounds__(512, 2) blend_pair_kernel(const ViewTable vt, const uint2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ vals, uint32_t R,
+                                                          const float4* __restrict__ rec0,
+                                                          const float4* __restrict__ rec1,
+                                                          const float4* __restrict__ rec2, int batch,
+                                                          float bg0, float bg1, float bg2,
+                                                          float* __restrict__ out_rgb,
+                                                          float* __restrict__ out_T,
+                                                          float* __restrict__ pix_T,
+                                                          uint32_t* __restrict__ pix_last,
+                                                          uint2* __restrict__ pix_count,
+                                                          const DeviceStatus* __restrict__ st, uint32_t* work) {
+    for_each_tile<PERSIST>(vt, work, [&](uint32_t tile) {
+        blend_pair_tile<COUNT>(vt, tile, ranges, vals, R, rec0, rec1, rec2, batch, bg0, bg1, bg2, out_rgb, out_T,
+                               pix_T, pix_last, pix_count, st);
+    });
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -642,9 +682,9 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
 // as f32x2 instructions, each half rounded exactly as the scalar pass rounds it, so every
 // skip decision matches the forward.  The transmittance and the colour behind are updated
 // per pixel; a pixel that does not blend the Gaussian contributes zero-weighted terms.
-__global__ void __launch_bounds__(512) blend_pair_backward_kernel(
-    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, uint32_t R32,
-    const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
+__device__ __forceinline__ void blend_pair_backward_tile(
+    const ViewTable& vt, const uint32_t tile, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+    uint32_t R32, const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
     int batch, float bg0, float bg1, float bg2, const float* __restrict__ pix_T,
     const uint32_t* __restrict__ pix_last, const float* __restrict__ dL_drgb,
     float4* __restrict__ grad2d, int64_t R, const DeviceStatus* __restrict__ st) {
@@ -659,7 +699,6 @@ __global__ void __launch_bounds__(512) blend_pair_backward_kernel(
     uint32_t* bits = sid + batch;
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
     __shared__ uint32_t s_max_last;
-    const uint32_t tile = vt.order ? vt.order[blockIdx.x] : blockIdx.x;
     const TileCoord tc = tile_of(vt, tile);
     const View& cam = vt.v[tc.v];
     const WarpBlock wb = warp_block<2>(vt);
@@ -790,6 +829,19 @@ __global__ void __launch_bounds__(512) blend_pair_backward_kernel(
     }
 }
 
+template <bool PERSIST>
+__global__ void __launch_bounds__(512, 2) blend_pair_backward_kernel(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, uint32_t R32,
+    const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
+    int batch, float bg0, float bg1, float bg2, const float* __restrict__ pix_T,
+    const uint32_t* __restrict__ pix_last, const float* __restrict__ dL_drgb,
+    float4* __restrict__ grad2d, int64_t R, const DeviceStatus* __restrict__ st, uint32_t* work) {
+    for_each_tile<PERSIST>(vt, work, [&](uint32_t tile) {
+        blend_pair_backward_tile(vt, tile, ranges, vals, R32, rec0, rec1, rec2, batch, bg0, bg1, bg2, pix_T,
+                                 pix_last, dL_drgb, grad2d, R, st);
+    });
+}
+
 __global__ void l1_zero_kernel(float* loss) { *loss = 0.0f; }
 
 __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, const float* __restrict__ tgt,
@@ -814,7 +866,23 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ img, 
 
 }  // namespace
 
-template <bool COUNT>
+// Grid of a pass over the tiles: one CTA per tile, or (persistent) the CTAs that fit on
+// the device at once, with the tile-claim counter cleared on the stream first.
+template <typename K>
+static cudaError_t tile_grid(K kernel, const ViewTable& vt, int threads, size_t smem, bool persistent,
+                             unsigned* grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    *grid = (unsigned)vt.num_tiles;
+    if (!persistent) return cudaSuccess;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
+    const int64_t resident = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+    *grid = (unsigned)(resident < vt.num_tiles ? resident : vt.num_tiles);
+    return cudaMemsetAsync(vt.work, 0, sizeof(uint32_t), s);
+}
+
+template <bool COUNT, bool PERSIST>
 static cudaError_t blend_pair(const ViewTable& vt, const uint2* ranges, const uint32_t* vals, int64_t R,
                               const RecordPtrs& p, int batch, float bg0, float bg1, float bg2, float* out_rgb,
                               float* out_T, float* pix_T, uint32_t* pix_last, uint2* pix_count,
@@ -822,13 +890,12 @@ static cudaError_t blend_pair(const ViewTable& vt, const uint2* ranges, const ui
     const int threads = vt.tile_w * vt.tile_h / 2;
     const size_t smem =
         (size_t)batch * stage_fields(kPairs) * sizeof(float4) + (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
-    cudaError_t e =
-        cudaFuncSetAttribute(blend_pair_kernel<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned grid = 0;
+    cudaError_t e = tile_grid(blend_pair_kernel<COUNT, PERSIST>, vt, threads, smem, PERSIST, &grid, s);
     if (e != cudaSuccess) return e;
-    blend_pair_kernel<COUNT><<<(unsigned)vt.num_tiles, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0,
-                                                                           p.rec1, p.rec2, batch, bg0, bg1, bg2,
-                                                                           out_rgb, out_T, pix_T, pix_last,
-                                                                           pix_count, st);
+    blend_pair_kernel<COUNT, PERSIST><<<grid, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1,
+                                                                  p.rec2, batch, bg0, bg1, bg2, out_rgb, out_T,
+                                                                  pix_T, pix_last, pix_count, st, vt.work);
     return cudaGetLastError();
 }
 
@@ -875,11 +942,16 @@ cudaError_t launch_blend(const ViewTable& vt, const uint2* ranges, const uint32_
     return blend_ppt<PPT, COUNT>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, \
                                  pix_count, st, s)
     if (vt.fwd_ppt == 2) {
-        if (vt.count_pairs)
-            return blend_pair<true>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last,
-                                    pix_count, st, s);
-        return blend_pair<false>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last,
-                                 pix_count, st, s);
+#define SGS_PAIR(COUNT, PERSIST)                                                                                 \
+    return blend_pair<COUNT, PERSIST>(vt, ranges, vals, R, p, batch, bg0, bg1, bg2, out_rgb, out_T, pix_T, pix_last, \
+                                      pix_count, st, s)
+        if (vt.count_pairs) {
+            if (vt.persistent) SGS_PAIR(true, true);
+            SGS_PAIR(true, false);
+        }
+        if (vt.persistent) SGS_PAIR(false, true);
+        SGS_PAIR(false, false);
+#undef SGS_PAIR
     }
     if (vt.count_pairs) SGS_BLEND(1, true);
     SGS_BLEND(1, false);
@@ -899,12 +971,19 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
         const int threads = vt.tile_w * vt.tile_h / 2;
         const size_t smem = (size_t)batch * (stage_fields(kPairsColour) * sizeof(float4) + sizeof(uint32_t)) +
                             (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
-        cudaError_t e = cudaFuncSetAttribute(blend_pair_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        unsigned grid = 0;
+        cudaError_t e = vt.persistent
+                            ? tile_grid(blend_pair_backward_kernel<true>, vt, threads, smem, true, &grid, s)
+                            : tile_grid(blend_pair_backward_kernel<false>, vt, threads, smem, false, &grid, s);
         if (e != cudaSuccess) return e;
-        blend_pair_backward_kernel<<<(unsigned)vt.num_tiles, threads, smem, s>>>(
-            vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1, p.rec2, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb,
-            grad2d, R, st);
+        if (vt.persistent)
+            blend_pair_backward_kernel<true><<<grid, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0, p.rec1,
+                                                                         p.rec2, batch, bg0, bg1, bg2, pix_T, pix_last,
+                                                                         dL_drgb, grad2d, R, st, vt.work);
+        else
+            blend_pair_backward_kernel<false><<<grid, threads, smem, s>>>(vt, ranges, vals, (uint32_t)R, p.rec0,
+                                                                          p.rec1, p.rec2, batch, bg0, bg1, bg2, pix_T,
+                                                                          pix_last, dL_drgb, grad2d, R, st, vt.work);
         return cudaGetLastError();
     }
     return blend_backward_ppt<1>(vt, ranges, vals, p, batch, bg0, bg1, bg2, pix_T, pix_last, dL_drgb, grad2d, R,

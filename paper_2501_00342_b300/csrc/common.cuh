@@ -38,6 +38,8 @@ struct ViewTable {
     uint16_t* masks;               // per instance, the warp blocks its support may reach: the
                                    // two-pixel forward stores them, the two-pixel backward reads
                                    // them (null: computed)
+    int32_t persistent;            // the two-pixel blend passes run as persistent kernels
+    uint32_t* work;                // their tile-claim counter (cleared before each launch)
     View v[SGS_MAX_VIEWS];
 };
 
@@ -49,6 +51,7 @@ struct DeviceStatus {
     uint32_t tile_counter[16];  // dynamic tile ids: [0] scan, [1..] sort passes
     uint32_t num_records;       // R, the length of the record sort
     uint32_t num_visible;       // records with instances: the record sort keeps only these
+    uint32_t work[2];           // tile slots claimed by the persistent forward / backward blend
 };
 
 // Correctly rounded single-precision operations that the compiler may not fuse or

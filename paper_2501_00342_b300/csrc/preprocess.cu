@@ -245,7 +245,6 @@ __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool vi
         hits += w >> 16;
     }
     hits = s_hits[threadIdx.x];
-    for (int k = rows; k < kSpanRows; ++k) table[(1 + k) * stride] = 0xffff0000u;
     const bool fits = rows <= kSpanRows && hits <= 0xffffu;
     table[0] = (uint32_t)rs.ty0 | ((fits ? (uint32_t)rows : kSpanRowsOverflow) << 16);
     return rs.ok ? hits : 0u;

@@ -24,12 +24,14 @@ class RenderSettings:
     bg: tuple = (0.0, 0.0, 0.0)
     fwd_pixels: int = 0  # pixels per thread of the blend kernels (0: the library's choice)
     bwd_pixels: int = 0
+    persistent: int = 0  # 1: persistent two-pixel blend kernels (tiles claimed from a counter)
 
     def struct(self) -> B.Settings:
         s = B.Settings()
         s.tile_w, s.tile_h = self.tile_w, self.tile_h
         s.batch_depth, s.digit_bits, s.memory_mode = self.batch_depth, self.digit_bits, 0
         s.fwd_pixels, s.bwd_pixels = self.fwd_pixels, self.bwd_pixels
+        s.persistent = self.persistent
         for k in range(3):
             s.bg[k] = float(self.bg[k])
         return s

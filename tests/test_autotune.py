@@ -52,15 +52,15 @@ def test_coordinate_descent_keeps_the_fastest(tmp_path, monkeypatch):
         seen.append(st)
         return cost[(st.tile_w, st.tile_h)] + {128: 0.5, 256: 0.0, 512: 0.2, 1024: 0.3}[st.batch_depth] + \
             {8: 0.3, 9: 0.0, 10: 0.1}[st.digit_bits] + {0: 0.05, 1: 0.0, 2: 0.1}[st.fwd_pixels] + \
-            {0: 0.05, 2: 0.0, 4: 0.2}[st.bwd_pixels]
+            {0: 0.05, 2: 0.0, 4: 0.2}[st.bwd_pixels] + {0: 0.02, 1: 0.0}[st.persistent]
 
     monkeypatch.setattr("paper_2501_00342_b300.autotune.time_step", fake_time)
     log = []
     path = tmp_path / "t.json"
     got = autotune(_fake_model(), I.orbit_cameras(1, 64, 64), cache_path=str(path), log=log)
     assert (got.tile_w, got.tile_h, got.batch_depth, got.digit_bits) == (16, 8, 256, 9)
-    assert (got.fwd_pixels, got.bwd_pixels) == (1, 2)
-    assert len(seen) == len(log) == 1 + 8 + 3 + 2 + 2 + 2
+    assert (got.fwd_pixels, got.bwd_pixels, got.persistent) == (1, 2, 1)
+    assert len(seen) == len(log) == 1 + 8 + 3 + 2 + 2 + 2 + 1
     stored = json.loads(path.read_text())
     assert list(stored.values())[0]["settings"] == {k: v for k, v in dataclasses.asdict(got).items() if k != "bg"}
 

@@ -194,3 +194,19 @@ def test_backward_is_repeatable():
         if a[p] is not None:
             scale = np.abs(a[p]).max()
             assert np.abs(a[p] - b[p]).max() <= 1e-5 * scale  # only atomic-order rounding differs
+
+
+def test_persistent_backward_equals_one_cta_per_tile():
+    """The persistent two-pixel backward gives the gradients of one CTA per tile (the same
+    sums, the float atomics adding in another order), on more tiles than resident CTAs."""
+    sc = I.cluster_scene(30000, 1, 4, config=3)
+    cams = I.orbit_cameras(2, 1280, 720, 50.0)
+    rng = np.random.default_rng(3)
+    ws = [rng.normal(size=(3, c.height, c.width)).astype(np.float32) for c in cams]
+    base = RenderSettings(tile_w=16, tile_h=16, fwd_pixels=2, bwd_pixels=2)
+    a = _gpu_grads(sc, cams, ws, base)
+    b = _gpu_grads(sc, cams, ws, RenderSettings(**{**base.__dict__, "persistent": 1}))
+    for p in PLANES:
+        if a[p] is not None:
+            assert np.abs(a[p]).max() > 0, p
+            assert np.abs(a[p] - b[p]).max() <= 1e-5 * np.abs(a[p]).max(), p

@@ -325,3 +325,19 @@ def test_adaptive_sh_degree_records_and_image():
     _check_records(sc, cams, rast)
     for v in range(len(cams)):
         _check_image(sc, cams, img, view=v, rast=rast, out_T=out_T)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32)])
+def test_persistent_blend_equals_one_cta_per_tile(tile):
+    """The persistent two-pixel forward (CTAs claiming tiles from a counter) gives the same
+    image, transmittance and last contributors as one CTA per tile, bit for bit.  Two
+    1280x720 views have more tiles than CTAs fit on the device, so CTAs take several."""
+    sc = I.cluster_scene(30000, 1, 4, config=3)
+    cams = I.orbit_cameras(2, 1280, 720, 50.0)
+    st = RenderSettings(tile_w=tile[0], tile_h=tile[1], fwd_pixels=2, bwd_pixels=2)
+    ra, _, img_a, t_a = _run(sc, cams, st)
+    rb, _, img_b, t_b = _run(sc, cams, RenderSettings(**{**st.__dict__, "persistent": 1}))
+    assert ra.plan.num_tiles > 148 * 2048 // (tile[0] * tile[1] // 2)  # CTAs at full occupancy
+    assert torch.equal(img_a, img_b) and torch.equal(t_a, t_b)
+    assert torch.equal(ra.region("PIX_LAST", torch.int32)[:ra.num_pixels],
+                       rb.region("PIX_LAST", torch.int32)[:rb.num_pixels])

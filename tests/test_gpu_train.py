@@ -149,8 +149,9 @@ def test_sharded_trainer_with_one_rank_equals_trainer():
         a, b = GaussianModel.from_scene(sc), GaussianModel.from_scene(sc)
         ta = Trainer(a, cams, target, RenderSettings(), cfg)
         tb = ShardedTrainer(b, cams, target, target.numel(), RenderSettings(), cfg)
-        la, lb = ta.step(), tb.step()
+        la, lb = ta.step(sync=True), tb.step(sync=True)  # the first step sizes the instance capacity
         torch.cuda.synchronize()
+        assert ta.rast.device_status() == 0 and tb.rast.device_status() == 0
         assert abs(float(la.item()) - float(lb.item())) <= 1e-6 * float(la.item())
         for p in PLANES:
             if a.planes[p] is None:
