@@ -16,7 +16,7 @@ namespace {
 enum Region {
     O_STATUS, O_REC0, O_REC1, O_REC2, O_RECT, O_TILES, O_OFFS, O_K0, O_V0, O_K1, O_V1,
     O_RANGES, O_PIXT, O_PIXLAST, O_GRAD2D, O_PIXCOUNT, O_SPANS, O_SCANLB, O_HIST, O_GOFF, O_SORTLB,
-    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_TORDER, O_TTOP, O_BORDER, O_MASKS, O_END
+    O_COUNTERS, O_RK0, O_RV0, O_RK1, O_RV1, O_RLB, O_TORDER, O_TTOP, O_BORDER, O_MASKS, O_FLAGS, O_END
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -129,6 +129,7 @@ RecordPtrs records(const sgs_plan* p) {
     r.rect = region<uint2>(p, O_RECT);
     r.tiles = region<uint32_t>(p, O_TILES);
     r.spans = region<uint4>(p, O_SPANS);
+    r.flags = region<uint32_t>(p, O_FLAGS);
     r.sort_keys = region<uint32_t>(p, O_RK0);
     r.sort_vals = region<uint32_t>(p, O_RV0);
     r.rv = record_value(p->num_records);
@@ -255,6 +256,7 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
     // the blend's tile orders and the forward's per-tile last contributor
     sz[O_TORDER] = sz[O_TTOP] = sz[O_BORDER] = 4 * (size_t)tiles;
     sz[O_MASKS] = 2 * cap;  // per instance, the warp blocks its support reaches
+    sz[O_FLAGS] = 4 * (size_t)R;  // per record, the decisions the backward reuses
     size_t off = 0;
     for (int k = 0; k < O_END; ++k) {
         plan->offsets[k] = off;

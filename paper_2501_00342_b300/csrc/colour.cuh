@@ -213,18 +213,26 @@ struct ColourParams {
     __device__ __forceinline__ float camp(int k, int c) const { return amp[k][c]; }
     __device__ __forceinline__ float caxis(int k, int c) const { return axis[k][c]; }
     __device__ __forceinline__ float csharp(int k) const { return sharp[k]; }
+    __device__ __forceinline__ float caxis_norm(int k) const { return axis_norm[k]; }
+    __device__ __forceinline__ float cframe_q(int j) const { return fq[j]; }
+    __device__ __forceinline__ float cframe_norm() const { return fnorm; }
 };
 
 // Number of SH coefficients a record sums: (D+1)^2 with D = sh_degree, or with adaptive
 // degrees D = 0 / 1 / 2 as the record's integer pixel radius is below sh_radius[0] /
 // below sh_radius[1] / not (capped at the stored degree L).
 template <int L>
-__device__ __forceinline__ int record_sh_coeffs(const sgs_gaussians& g, float radius) {
+__device__ __forceinline__ int record_sh_degree(const sgs_gaussians& g, float radius) {
     int D = L;
     if (g.sh_adaptive) {
         D = radius < g.sh_radius[0] ? 0 : (radius < g.sh_radius[1] ? 1 : 2);
         D = D < L ? D : L;
     }
+    return D;
+}
+template <int L>
+__device__ __forceinline__ int record_sh_coeffs(const sgs_gaussians& g, float radius) {
+    const int D = record_sh_degree<L>(g, radius);
     return (D + 1) * (D + 1);
 }
 
@@ -295,8 +303,10 @@ struct ColourGrads {
         }
     }
 
-    __device__ __forceinline__ void store(const ColourParams<L, K, AX>& p, const sgs_grads& out, int64_t S,
-                                          int64_t i) const {
+    // P: ColourParams or any layout with the same accessors (csh, camp, caxis, csharp,
+    // caxis_norm, cframe_q, cframe_norm)
+    template <class P>
+    __device__ __forceinline__ void store(const P& p, const sgs_grads& out, int64_t S, int64_t i) const {
 #pragma unroll
         for (int k = 0; k < NSH; ++k)
 #pragma unroll
@@ -308,11 +318,12 @@ struct ColourGrads {
             out.sg_sharp[k * S + i] = sharp[k];
             if constexpr (AX == kAxFree) {
                 // mu = m/|m|:  dL/dm = (g - mu (mu . g)) / |m|
-                const float dot = axis[k][0] * p.axis[k][0] + axis[k][1] * p.axis[k][1] + axis[k][2] * p.axis[k][2];
-                const float inv = 1.0f / p.axis_norm[k];
+                const float dot =
+                    axis[k][0] * p.caxis(k, 0) + axis[k][1] * p.caxis(k, 1) + axis[k][2] * p.caxis(k, 2);
+                const float inv = 1.0f / p.caxis_norm(k);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.axis[k][c] * dot) * inv;
+                    out.sg_axis[(k * 3 + c) * S + i] = (axis[k][c] - p.caxis(k, c) * dot) * inv;
             }
         }
         if constexpr (AX == kAxFrame && K > 0) {
@@ -323,11 +334,12 @@ struct ColourGrads {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) gR[c][k] = k < K ? axis[k < K ? k : 0][c] : 0.0f;
             float gq[4];
-            quat_to_matrix_vjp(p.fq, gR, gq);
-            const float dot = gq[0] * p.fq[0] + gq[1] * p.fq[1] + gq[2] * p.fq[2] + gq[3] * p.fq[3];
-            const float inv = 1.0f / p.fnorm;
+            const float fq[4] = {p.cframe_q(0), p.cframe_q(1), p.cframe_q(2), p.cframe_q(3)};
+            quat_to_matrix_vjp(fq, gR, gq);
+            const float dot = gq[0] * fq[0] + gq[1] * fq[1] + gq[2] * fq[2] + gq[3] * fq[3];
+            const float inv = 1.0f / p.cframe_norm();
 #pragma unroll
-            for (int j = 0; j < 3; ++j) out.sg_axis[j * S + i] = (gq[1 + j] - p.fq[1 + j] * dot) * inv;
+            for (int j = 0; j < 3; ++j) out.sg_axis[j * S + i] = (gq[1 + j] - fq[1 + j] * dot) * inv;
         }
     }
 };

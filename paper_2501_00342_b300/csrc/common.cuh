@@ -240,6 +240,16 @@ __device__ __forceinline__ void async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Per-record flags the preprocess leaves for its backward pass: the record's discrete
+// decisions, so that the backward takes each branch the forward took without recomputing
+// (bit for bit) the values that decided it.  Bits 0-2: colour channel c clamped at 0;
+// bit 3 / 4: x/z / y/z clamped to the frustum limit; bits 5-6: the SH degree D the colour
+// summed; bit 7: the record has instances.  0 for a culled record.
+constexpr uint32_t kFlagClampX = 1u << 3;
+constexpr uint32_t kFlagClampY = 1u << 4;
+constexpr int kFlagShift = 5;
+constexpr uint32_t kFlagVisible = 1u << 7;
+
 constexpr float kSupportPower = -4.5f;     // Mahalanobis distance 3
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;

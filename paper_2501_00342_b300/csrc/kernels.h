@@ -64,6 +64,7 @@ struct RecordPtrs {
     uint2* rect;
     uint32_t* tiles;
     uint4* spans;  // [4][R] packed tile-row table per record (see count_tiles)
+    uint32_t* flags;  // per record: visible, clamp decisions, SH degree (kFlag* bits)
     // the record sort's input, written by the preprocess: keys (view depth bits of a record
     // with instances, 0xffffffff for the others) and values (RecordValue)
     uint32_t* sort_keys;

@@ -87,6 +87,7 @@ struct Projected {
     bool clampx, clampy;
     float J00, J02, J11, J12;
     float T[2][3];
+    float TS[2][3];  // T Sigma (project_fast only)
     float a, b, c;
 };
 
@@ -263,12 +264,15 @@ __device__ __forceinline__ void view_direction(const View& cam, const float X[3]
 constexpr int kPreThreads = 128;
 
 // A Gaussian's colour parameters held in a column of shared memory (stride kPreThreads):
-// the view loop reads them per view instead of keeping ~40 registers live.
+// the view loops of the forward and the backward pass read them per view instead of keeping
+// ~40 registers live.  Layout: sh, amplitudes, unit axes, sharpness, then |mu_k| (free
+// axes) or the frame quaternion and |(1, f)| (frame).
 template <int L, int K, int AX>
 struct ColourShared {
     static constexpr int NSH = (L + 1) * (L + 1);
     static constexpr int NAX = (K > 0 && AX != kAxWorld) ? 3 * K : 0;
-    static constexpr int COUNT = 3 * NSH + 3 * K + NAX + K + NAX / 3;  // sh, amp, unit axes, sharpness, |axis|
+    static constexpr int NEXTRA = (K > 0 && AX == kAxFree) ? K : ((K > 0 && AX == kAxFrame) ? 5 : 0);
+    static constexpr int COUNT = 3 * NSH + 3 * K + NAX + K + NEXTRA;
     float* p;
 
     __device__ __forceinline__ float& at(int j) const { return p[j * kPreThreads]; }
@@ -280,11 +284,14 @@ struct ColourShared {
         if constexpr (AX == kAxFrame && K > 0) {
             const float f[3] = {__ldg(g.sg_axis + i), __ldg(g.sg_axis + S + i), __ldg(g.sg_axis + 2 * S + i)};
             float q[4], R[3][3];
-            frame_axes(f, q, R);
+            const float n = frame_axes(f, q, R);
 #pragma unroll
             for (int k = 0; k < K; ++k)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) at(3 * NSH + 3 * K + 3 * k + c) = R[c][k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) at(3 * NSH + 3 * K + NAX + K + j) = q[j];
+            at(3 * NSH + 3 * K + NAX + K + 4) = n;
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -309,6 +316,8 @@ struct ColourShared {
     __device__ __forceinline__ float caxis(int k, int c) const { return at(3 * NSH + 3 * K + 3 * k + c); }
     __device__ __forceinline__ float csharp(int k) const { return at(3 * NSH + 3 * K + NAX + k); }
     __device__ __forceinline__ float caxis_norm(int k) const { return at(3 * NSH + 3 * K + NAX + K + k); }
+    __device__ __forceinline__ float cframe_q(int j) const { return at(3 * NSH + 3 * K + NAX + K + j); }
+    __device__ __forceinline__ float cframe_norm() const { return at(3 * NSH + 3 * K + NAX + K + 4); }
 };
 
 template <int L, int K, int AX>
@@ -321,6 +330,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
                                                                  uint4* __restrict__ spans,
                                                                  uint32_t* __restrict__ sort_keys,
                                                                  uint32_t* __restrict__ sort_vals,
+                                                                 uint32_t* __restrict__ flags,
                                                                  const RecordValue rv) {
     using CS = ColourShared<L, K, AX>;
     __shared__ float s_colour[CS::COUNT * kPreThreads];
@@ -353,12 +363,14 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         if (hits == 0u) {
             rect[r] = make_uint2(0u, 0u);
             tiles[r] = 0u;
+            flags[r] = 0u;
             continue;
         }
         float d[3], len;
         view_direction(cam, X, d, len);
         float pre[3];
-        colour_eval<L, K, AX>(cp, d, pre, record_sh_coeffs<L>(g, P.radius));
+        const int D = record_sh_degree<L>(g, P.radius);
+        colour_eval<L, K, AX>(cp, d, pre, (D + 1) * (D + 1));
         uint32_t mask = 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -369,6 +381,8 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
         rec0[r] = make_float4(P.px, P.py, -0.5f * P.A, -P.B);
         rec1[r] = make_float4(-0.5f * P.C, opacity, P.t[2], P.radius);
         rec2[r] = make_float4(pre[0], pre[1], pre[2], __uint_as_float(mask));
+        flags[r] = kFlagVisible | mask | (P.clampx ? kFlagClampX : 0u) | (P.clampy ? kFlagClampY : 0u) |
+                   ((uint32_t)D << kFlagShift);
         rect[r] = make_uint2((uint32_t)P.x0 | ((uint32_t)P.y0 << 16),
                              (uint32_t)P.x1 | ((uint32_t)P.y1 << 16));
         tiles[r] = hits;
@@ -382,10 +396,51 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
 }
 
 // ------------------------------------------------------------------------------ backward
+// The intermediates of the projection that the chain rule needs (t, the clamped x/z and
+// y/z, J, T = J W, T Sigma and the conic), recomputed in plain single precision with fused
+// multiply-adds and one reciprocal.  The frustum-clamp decisions are the forward's, read
+// from the record's flags (kFlagClampX/Y), so every branch is the one the forward took; the
+// values differ from the forward's correctly rounded ones by a few units in the last place,
+// far inside the gradients' tolerance.
+__device__ __forceinline__ void project_fast(const View& cam, const float X[3], const Geometry& G, uint32_t f,
+                                             Projected& P) {
+    const float* V = cam.V;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        P.t[r] = fmaf(V[4 * r], X[0], fmaf(V[4 * r + 1], X[1], fmaf(V[4 * r + 2], X[2], V[4 * r + 3])));
+    const float tz = P.t[2], iz = 1.0f / tz;
+    const float u0 = P.t[0] * iz, v0 = P.t[1] * iz;
+    P.clampx = (f & kFlagClampX) != 0u;
+    P.clampy = (f & kFlagClampY) != 0u;
+    P.u = P.clampx ? copysignf(cam.limx, u0) : u0;
+    P.v = P.clampy ? copysignf(cam.limy, v0) : v0;
+    P.J00 = cam.fx * iz;
+    P.J02 = -cam.fx * P.u * iz;
+    P.J11 = cam.fy * iz;
+    P.J12 = -cam.fy * P.v * iz;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        P.T[0][c] = fmaf(P.J00, V[c], P.J02 * V[8 + c]);
+        P.T[1][c] = fmaf(P.J11, V[4 + c], P.J12 * V[8 + c]);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            P.TS[r][c] = fmaf(P.T[r][0], G.Sig[0][c], fmaf(P.T[r][1], G.Sig[1][c], P.T[r][2] * G.Sig[2][c]));
+    P.a = fmaf(P.TS[0][0], P.T[0][0], fmaf(P.TS[0][1], P.T[0][1], fmaf(P.TS[0][2], P.T[0][2], 0.3f)));
+    P.b = fmaf(P.TS[0][0], P.T[1][0], fmaf(P.TS[0][1], P.T[1][1], P.TS[0][2] * P.T[1][2]));
+    P.c = fmaf(P.TS[1][0], P.T[1][0], fmaf(P.TS[1][1], P.T[1][1], fmaf(P.TS[1][2], P.T[1][2], 0.3f)));
+    const float idet = 1.0f / fmaf(P.a, P.c, -P.b * P.b);
+    P.A = P.c * idet;
+    P.B = -P.b * idet;
+    P.C = P.a * idet;
+}
+
 template <int L, int K, int AX>
 __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     const sgs_gaussians g, const ViewTable vt, const float4* __restrict__ rec0,
-    const float4* __restrict__ rec1, const uint32_t* __restrict__ tiles,
+    const float4* __restrict__ rec1, const uint32_t* __restrict__ flags,
     const float4* __restrict__ grad2d, int64_t R, sgs_grads out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
@@ -393,7 +448,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     const float X[3] = {__ldg(g.mean + i), __ldg(g.mean + S + i), __ldg(g.mean + 2 * S + i)};
     Geometry G;
     geometry_exact(g, i, G);
-    ColourParams<L, K, AX> cp;
+    using CS = ColourShared<L, K, AX>;
+    __shared__ float s_colour[CS::COUNT * kPreThreads];
+    const CS cp{s_colour + threadIdx.x};
     cp.load(g, i);
     ColourGrads<L, K, AX> cg;
     cg.zero();
@@ -404,14 +461,14 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
 #pragma unroll
         for (int c = 0; c < 3; ++c) gSig[r][c] = 0.0f;
     float gop = 0.0f;
-    // the next view's tile count and 2D gradients travel to shared memory while this view's
-    // chain rule runs (double-buffered, one slot per thread)
+    // the next view's record flags and 2D gradients travel to shared memory while this
+    // view's chain rule runs (double-buffered, one slot per thread)
     __shared__ __align__(16) float4 s_g[2][3][kPreThreads];
     __shared__ uint32_t s_t[2][kPreThreads];
     const int tx = threadIdx.x;
     auto prefetch = [&](int v, int b) {
         const int64_t r = (int64_t)v * g.n + i;
-        async_copy4(&s_t[b][tx], tiles + r);
+        async_copy4(&s_t[b][tx], flags + r);
 #pragma unroll
         for (int c = 0; c < 2; ++c) async_copy16(&s_g[b][c][tx], grad2d + c * R + r);
         async_copy4(&s_g[b][2][tx].x, reinterpret_cast<const float*>(grad2d + 2 * R) + r);
@@ -426,24 +483,23 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         } else {
             async_wait<0>();
         }
-        if (s_t[b][tx] == 0u) continue;
+        const uint32_t f = s_t[b][tx];
+        if (!(f & kFlagVisible)) continue;
         const float4 g0 = s_g[b][0][tx], g1 = s_g[b][1][tx], g2 = s_g[b][2][tx];
         const View& cam = vt.v[v];
         Projected P;
-        project_exact(cam, X, G, vt.inv_tile_w, vt.inv_tile_h, P);
+        project_fast(cam, X, G, f, P);
         gop += g1.y;
-        // colour
+        // colour: the SH degree and the colour-clamp decisions are the forward's (flags)
         {
             float d[3], len;
             view_direction(cam, X, d, len);
-            // the forward's colour, bit for bit (same arithmetic), for its clamp decisions
-            const int nsh = record_sh_coeffs<L>(g, P.radius);
-            float pre[3];
-            colour_eval<L, K, AX>(cp, d, pre, nsh);
+            const int D = (int)((f >> kFlagShift) & 3u);
+            const int nsh = (D + 1) * (D + 1);
             const float grgb[3] = {g1.z, g1.w, g2.x};
             float gpre[3], gd[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gpre[c] = pre[c] < 0.0f ? 0.0f : grgb[c];
+            for (int c = 0; c < 3; ++c) gpre[c] = (f >> c) & 1u ? 0.0f : grgb[c];
             cg.accumulate(cp, d, gpre, gd, nsh);
             const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
             const float inv = 1.0f / len;
@@ -458,12 +514,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         const float G2[2][2] = {{-(P00 * A + P01 * B), -(P00 * B + P01 * C)},
                                 {-(P00 * B + P01 * C), -(P10 * B + P11 * C)}};
         // Sigma2D = T Sigma T^T:  dSigma += T^T G2 T,  dT = 2 G2 T Sigma
-        float TS[2][3];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                TS[rr][c] = P.T[rr][0] * G.Sig[0][c] + P.T[rr][1] * G.Sig[1][c] + P.T[rr][2] * G.Sig[2][c];
+        const float(&TS)[2][3] = P.TS;
         float gT[2][3];
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr)
@@ -543,7 +594,7 @@ cudaError_t launch_pre(const sgs_gaussians& g, const ViewTable& vt, const Record
     if (blocks > 0)
         preprocess_kernel<L, K, AX><<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.rec2, p.rect,
                                                                  p.tiles, p.spans, p.sort_keys, p.sort_vals,
-                                                                 p.rv);
+                                                                 p.flags, p.rv);
     return cudaGetLastError();
 }
 
@@ -554,7 +605,7 @@ cudaError_t launch_pre_bwd(const sgs_gaussians& g, const ViewTable& vt, const Re
     const int blocks = (int)((g.n + threads - 1) / threads);
     if (blocks > 0)
         preprocess_backward_kernel<L, K, AX>
-            <<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.tiles, grad2d, R, out);
+            <<<blocks, threads, 0, s>>>(g, vt, p.rec0, p.rec1, p.flags, grad2d, R, out);
     return cudaGetLastError();
 }
 
