@@ -308,7 +308,7 @@ def run_gpu(args):
         "ranges": span("SORT_END", "RANGES_END"),
         "blend": span("BLEND_BEGIN", "BLEND_END"),
         "loss": span("BLEND_END", "BWD_BEGIN"),
-        "backward_zero": span("BWD_BEGIN", "BWD_ZERO_END"),
+        "backward_tile_order": span("BWD_BEGIN", "BWD_ZERO_END"),
         "backward_blend": span("BWD_ZERO_END", "BWD_BLEND_END"),
         "backward_preprocess": span("BWD_BLEND_END", "BWD_PRE_END"),
     }

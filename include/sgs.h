@@ -173,7 +173,7 @@ typedef enum {
     SGS_EV_SORT_END = 6,                               /* sort: all onesweep passes */
     SGS_EV_RANGES_END = 7,                             /* clears + tile ranges */
     SGS_EV_BLEND_BEGIN = 8, SGS_EV_BLEND_END = 9,      /* blend kernel */
-    SGS_EV_BWD_BEGIN = 10, SGS_EV_BWD_ZERO_END = 11,   /* clear of the 2D gradients */
+    SGS_EV_BWD_BEGIN = 10, SGS_EV_BWD_ZERO_END = 11,   /* the backward's tile order */
     SGS_EV_BWD_BLEND_END = 12,                         /* reverse blend */
     SGS_EV_BWD_PRE_END = 13,                           /* preprocess backward */
     SGS_EV_COUNT = 14
@@ -195,7 +195,12 @@ sgs_status sgs_workspace_size(const sgs_gaussians* g, const sgs_camera* cams, in
 /* Stage (a): per (view, Gaussian) record -- cull, depth, screen mean, conic, radius,
  * tile rectangle, colour -- for all B views in one launch (parameters are read once).
  * Binds `workspace` (device, >= plan->workspace_bytes, 256-byte aligned) to the plan
- * and clears the device status word.  g must match the sizes the plan was made for. */
+ * and clears the device status word.  g must match the sizes the plan was made for.
+ * The workspace keeps state from one call sequence of the plan to the next: the 2D
+ * gradient accumulators, which every backward leaves zero, and the previous forward's
+ * per-tile costs (a schedule hint).  Both are reset when a workspace is bound whose
+ * address differs from the plan's previous one; a workspace that another plan has used
+ * in between needs a new plan (sgs_workspace_size) before this one uses it again. */
 sgs_status sgs_preprocess(sgs_plan* plan, const sgs_gaussians* g, void* workspace,
                           size_t ws_bytes, cudaStream_t stream);
 
@@ -247,7 +252,8 @@ typedef enum {
     SGS_REGION_PIX_LAST = 13, /* uint32[num_pixels]: 1 + position of the last contributor
                                  in the tile's list (0: none) */
     SGS_REGION_GRAD2D = 14, /* float4[2][R] then float[R]: dL/d(px, py, A, B), (C, opacity, r, g),
-                               then dL/db */
+                               then dL/db; zero outside sgs_render_backward (its last kernel
+                               clears what its reverse blend accumulated) */
     SGS_REGION_PIX_COUNT = 15, /* uint2[num_pixels]: list entries the pixel evaluated, and
                                   how many of them it blended */
     SGS_REGION_COUNT = 16

@@ -281,6 +281,9 @@ sgs_status sgs_preprocess(sgs_plan* plan, const sgs_gaussians* g, void* workspac
     // a newly bound workspace has none
     if (rebind && plan->num_tiles > 0)
         SGS_TRY(cudaMemsetAsync(region<uint32_t>(plan, O_TTOP), 0, 4 * (size_t)plan->num_tiles, stream));
+    // the reverse blend adds into zeroed 2D gradients; after this clear every backward
+    // leaves them zero again (the preprocess backward clears what it reads)
+    if (rebind) SGS_TRY(launch_zero_grad2d(region<float4>(plan, O_GRAD2D), plan->num_records, stream));
     const ViewTable vt = view_table(plan);
     SGS_TRY(probe(plan, SGS_EV_PRE_BEGIN, stream));
     if (plan->n > 0) SGS_TRY(launch_preprocess(*g, vt, records(plan), stream));
@@ -390,7 +393,6 @@ sgs_status sgs_render_backward(sgs_plan* plan, const sgs_gaussians* g, const flo
     const int vreg = (plan->sort_passes & 1) ? O_V1 : O_V0;
     const sgs_settings& s = plan->settings;
     SGS_TRY(probe(plan, SGS_EV_BWD_BEGIN, stream));
-    SGS_TRY(launch_zero_grad2d(grad2d, rp.tiles, R, stream));
     // the backward's tile order: tiles by decreasing position of their last contributor
     // (written by the forward), so the longest reverse walks start first
     SGS_TRY(launch_tile_order(nullptr, region<uint32_t>(plan, O_TTOP), plan->num_tiles,

@@ -990,11 +990,8 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                  st, s);
 }
 
-cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s) {
+cudaError_t launch_zero_grad2d(float4* grad2d, int64_t R, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
-    // one plain clear of the two float4 planes and the float plane streams at full write
-    // bandwidth; skipping the culled records saves little and costs a dependent load each
-    (void)tiles;
     return cudaMemsetAsync(grad2d, 0, (size_t)R * (2 * sizeof(float4) + sizeof(float)), s);
 }
 

@@ -75,8 +75,10 @@ struct RecordPtrs {
 // (a) preprocess and its backward
 cudaError_t launch_preprocess(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
                               cudaStream_t s);
+// Reads the 2D gradients of the visible records and clears them (the region is zero after
+// the call: the next reverse blend adds into zeros).
 cudaError_t launch_preprocess_backward(const sgs_gaussians& g, const ViewTable& vt,
-                                       const RecordPtrs& p, const float4* grad2d, int64_t R,
+                                       const RecordPtrs& p, float4* grad2d, int64_t R,
                                        const sgs_grads& out, cudaStream_t s);
 
 // (b), (d): scan + duplicate, ranges
@@ -158,8 +160,9 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                   const float* dL_drgb, float4* grad2d, int64_t R,
                                   const DeviceStatus* st, cudaStream_t s);
 // grad2d: per record dL/d(px, py, A, B) and dL/d(C, opacity, r, g) as float4[2][R], then
-// dL/db as float[R] (from grad2d + 2 R).
-cudaError_t launch_zero_grad2d(float4* grad2d, const uint32_t* tiles, int64_t R, cudaStream_t s);
+// dL/db as float[R] (from grad2d + 2 R).  Cleared once when a workspace is bound; the
+// preprocess backward clears what the reverse blend wrote.
+cudaError_t launch_zero_grad2d(float4* grad2d, int64_t R, cudaStream_t s);
 
 // training: fused Adam step over all parameter planes
 cudaError_t launch_adam(const sgs_gaussians& layout, const sgs_grads& raw, const sgs_grads& act,

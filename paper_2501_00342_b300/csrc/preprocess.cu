@@ -441,7 +441,7 @@ template <int L, int K, int AX>
 __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
     const sgs_gaussians g, const ViewTable vt, const float4* __restrict__ rec0,
     const float4* __restrict__ rec1, const uint32_t* __restrict__ flags,
-    const float4* __restrict__ grad2d, int64_t R, sgs_grads out) {
+    float4* __restrict__ grad2d, int64_t R, sgs_grads out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int64_t S = g.stride;
@@ -486,6 +486,14 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         const uint32_t f = s_t[b][tx];
         if (!(f & kFlagVisible)) continue;
         const float4 g0 = s_g[b][0][tx], g1 = s_g[b][1][tx], g2 = s_g[b][2][tx];
+        {
+            // the reverse blend adds into the 2D gradients of visible records only: clearing
+            // them here, once read, leaves the whole region zero for the next backward
+            const int64_t r = (int64_t)v * g.n + i;
+            grad2d[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            grad2d[R + r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            reinterpret_cast<float*>(grad2d + 2 * R)[r] = 0.0f;
+        }
         const View& cam = vt.v[v];
         Projected P;
         project_fast(cam, X, G, f, P);
@@ -600,7 +608,7 @@ cudaError_t launch_pre(const sgs_gaussians& g, const ViewTable& vt, const Record
 
 template <int L, int K, int AX>
 cudaError_t launch_pre_bwd(const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
-                           const float4* grad2d, int64_t R, const sgs_grads& out, cudaStream_t s) {
+                           float4* grad2d, int64_t R, const sgs_grads& out, cudaStream_t s) {
     const int threads = 128;
     const int blocks = (int)((g.n + threads - 1) / threads);
     if (blocks > 0)
@@ -611,7 +619,7 @@ cudaError_t launch_pre_bwd(const sgs_gaussians& g, const ViewTable& vt, const Re
 
 template <int L, int K>
 cudaError_t dispatch_axis(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
-                          const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
+                          float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
     if (g.axis_mode == SGS_AXIS_ORTHO_FIXED || g.axis_mode == SGS_AXIS_ORTHO_FRAME) {
         if constexpr (K <= 3) {
             if (g.axis_mode == SGS_AXIS_ORTHO_FIXED)
@@ -628,7 +636,7 @@ cudaError_t dispatch_axis(bool fwd, const sgs_gaussians& g, const ViewTable& vt,
 
 template <int L>
 cudaError_t dispatch_k(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
-                       const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
+                       float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
     switch (g.num_lobes) {
         case 0: return dispatch_axis<L, 0>(fwd, g, vt, p, grad2d, R, out, s);
         case 1: return dispatch_axis<L, 1>(fwd, g, vt, p, grad2d, R, out, s);
@@ -640,7 +648,7 @@ cudaError_t dispatch_k(bool fwd, const sgs_gaussians& g, const ViewTable& vt, co
 }
 
 cudaError_t dispatch(bool fwd, const sgs_gaussians& g, const ViewTable& vt, const RecordPtrs& p,
-                     const float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
+                     float4* grad2d, int64_t R, const sgs_grads* out, cudaStream_t s) {
     switch (g.sh_degree) {
         case 0: return dispatch_k<0>(fwd, g, vt, p, grad2d, R, out, s);
         case 1: return dispatch_k<1>(fwd, g, vt, p, grad2d, R, out, s);
@@ -658,7 +666,7 @@ cudaError_t launch_preprocess(const sgs_gaussians& g, const ViewTable& vt, const
 }
 
 cudaError_t launch_preprocess_backward(const sgs_gaussians& g, const ViewTable& vt,
-                                       const RecordPtrs& p, const float4* grad2d, int64_t R,
+                                       const RecordPtrs& p, float4* grad2d, int64_t R,
                                        const sgs_grads& out, cudaStream_t s) {
     return dispatch(false, g, vt, p, grad2d, R, &out, s);
 }

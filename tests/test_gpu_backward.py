@@ -210,3 +210,30 @@ def test_persistent_backward_equals_one_cta_per_tile():
         if a[p] is not None:
             assert np.abs(a[p]).max() > 0, p
             assert np.abs(a[p] - b[p]).max() <= 1e-5 * np.abs(a[p]).max(), p
+
+
+def test_backwards_on_one_workspace_leave_the_2d_gradients_zero():
+    """The reverse blend adds into per-record 2D gradients that the preprocess backward
+    clears as it reads them: after every backward the region is zero, and backwards in a
+    row (other weights, another forward in between) on one workspace give the gradients of
+    a fresh workspace."""
+    sc, cams = I.workload(0)
+    w1, w2 = _weights(sc, cams, 21), _weights(sc, cams, 22)
+    model = GaussianModel.from_scene(sc)
+    rast = Rasterizer(model, cams, RenderSettings())
+    flat = [torch.from_numpy(np.concatenate([w.reshape(-1) for w in ws])).cuda() for ws in (w1, w2, w1)]
+    got = []
+    for k, dl in enumerate(flat):
+        if k != 1:
+            rast.forward(model)
+        g = rast.backward(model, dl)
+        torch.cuda.synchronize()
+        assert rast.device_status() == 0
+        assert not bool(rast.region("GRAD2D", torch.float32).any().item())
+        got.append({p: (None if t is None else t.cpu().numpy().astype(np.float64)) for p, t in g.items()})
+    for ws, g in ((w1, got[0]), (w2, got[1]), (w1, got[2])):
+        ref = _gpu_grads(sc, cams, ws)
+        for p in PLANES:
+            if ref[p] is not None:
+                assert np.abs(ref[p]).max() > 0, p
+                assert np.abs(g[p] - ref[p]).max() <= 1e-5 * np.abs(ref[p]).max(), p
