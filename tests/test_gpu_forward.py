@@ -341,3 +341,29 @@ def test_persistent_blend_equals_one_cta_per_tile(tile):
     assert torch.equal(img_a, img_b) and torch.equal(t_a, t_b)
     assert torch.equal(ra.region("PIX_LAST", torch.int32)[:ra.num_pixels],
                        rb.region("PIX_LAST", torch.int32)[:rb.num_pixels])
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_gaussians_just_outside_the_grid_keep_exact_records(tile):
+    """The preprocess culls a record early when its screen position lies farther outside the
+    tile grid than a conservative bound of its pixel radius.  Gaussians centred in a band up
+    to 60 pixels outside a 128x96 image, with scales from tiny to large and anisotropic,
+    must still give every record (culled or not) bit for bit as the FP32 mirror does."""
+    rng = np.random.default_rng(31)
+    n = 4000
+    cam = axis_camera(128, 96, 60.0, 4.0)
+    depth = rng.uniform(1.0, 7.0, n)
+    side = rng.integers(0, 4, n)
+    px = np.where(side == 0, rng.uniform(-60, 0, n), np.where(side == 1, rng.uniform(128, 188, n), rng.uniform(-60, 188, n)))
+    py = np.where(side == 2, rng.uniform(-60, 0, n), np.where(side == 3, rng.uniform(96, 156, n), rng.uniform(-60, 156, n)))
+    # pixel (px, py) at depth z: camera on +z at distance 4 looking at the origin (x right, y down)
+    x = (px - cam.cx) * depth / cam.fx
+    y = -(py - cam.cy) * depth / cam.fy
+    means = np.stack([x, y, 4.0 - depth], 1)
+    scales = np.exp(rng.uniform(np.log(0.002), np.log(0.6), (n, 3)))
+    quats = rng.normal(size=(n, 4))
+    sc = make_scene(means, scales, quats, rng.uniform(0.05, 0.95, n), rng.normal(0.5, 0.2, (n, 1, 3)))
+    st = RenderSettings(tile_w=tile, tile_h=tile)
+    rast, _, _, _ = _run(sc, [cam], st)
+    vis = _check_records(sc, [cam], rast, tile, tile)
+    assert 200 < vis < n - 200  # both outcomes are common
