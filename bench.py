@@ -143,6 +143,37 @@ def measure_alu_peak(index: int, reps: int = 10, iters: int = 1 << 19):
     return res
 
 
+def copy_bandwidth(nbytes: int = 1 << 30, reps: int = 5):
+    """Pinned host <-> device copy rates (GB/s): host-to-device alone, device-to-host alone,
+    and both at once on two streams, as the end-to-end leg overlaps them (CUDA events, best
+    of `reps`)."""
+    import torch
+    h_src, h_dst = (torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(2))
+    d_dst, d_src = (torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2))
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    out = {}
+    for name, h2d, d2h in (("h2d", True, False), ("d2h", False, True), ("both", True, True)):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            for st, on, dst, src in ((up, h2d, d_dst, h_src), (down, d2h, h_dst, d_src)):
+                if on:
+                    st.wait_event(a)
+                    with torch.cuda.stream(st):
+                        dst.copy_(src, non_blocking=True)
+                    main.wait_stream(st)
+            b.record(main)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        out[name] = round((int(h2d) + int(d2h)) * nbytes / (best / 1e3) / 1e9, 1)
+    del h_src, h_dst, d_dst, d_src
+    return out
+
+
 # ------------------------------------------------------------------------------ GPU arm
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -339,16 +370,29 @@ def run_gpu(args):
     alu["sm_count"] = torch.cuda.get_device_properties(local).multi_processor_count
     fwd_name = "blend_pair_kernel" if settings.fwd_pixels in (0, 2) else "blend_kernel"
     bwd_name = "blend_pair_backward_kernel" if settings.bwd_pixels in (0, 2) else "blend_backward_kernel"
+    # algorithmic bytes of each HBM-bound kernel: everything this design's kernel must read
+    # and write ("work"), and, where the survey gives a narrower count (parameters plus the
+    # records of its own model), that count too ("survey_work")
+    R = n * nv
     kernels = {
+        # parameters once; per visible record its 48-byte record and the row table's first
+        # 32-byte sector; per record its rectangle, tile count, flags and record-sort pair
         "preprocess_kernel": dict(ms=stages["preprocess"], launches=1, bound="hbm",
-                                  work=n * p_bytes + visible * 48 + n * nv * 12),
+                                  work=n * p_bytes + visible * (48 + 32) + R * (8 + 4 + 4 + 8),
+                                  survey_work=n * p_bytes + R * 44),
+        # the instances written (u32 tile id + u32 record id); per visible record its row
+        # table sector, sorted position and scan offset read
+        "duplicate_kernel": dict(ms=stages["duplicate"], launches=1, bound="hbm", work=8 * M + visible * (32 + 8)),
         "onesweep_kernel": dict(ms=stages["sort_onesweep_all_passes"] / max(P, 1), launches=P, bound="hbm",
                                 work=16 * M),  # u32 tile id + u32 record id, read and written
         # two pixels per thread run the packed-pair kernels
         fwd_name: dict(ms=stages["blend"], launches=1, bound="alu", work=8 * e_eval + 11 * e_contrib),
         bwd_name: dict(ms=stages["backward_blend"], launches=1, bound="alu", work=8 * e_eval + 40 * e_contrib),
+        # parameters read and their gradients written; per record its flags; per visible
+        # record its 36-byte 2D gradient read and cleared
         "preprocess_backward_kernel": dict(ms=stages["backward_preprocess"], launches=1, bound="hbm",
-                                           work=2 * n * p_bytes + visible * 48),
+                                           work=2 * n * p_bytes + R * 4 + visible * 72,
+                                           survey_work=2 * n * p_bytes + visible * 36),
     }
     dom_name = max(kernels, key=lambda k: kernels[k]["ms"] * kernels[k]["launches"])
     units = {"pixel": rast.num_pixels, "instance": M}
@@ -368,6 +412,9 @@ def run_gpu(args):
             roofs[name] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                            "frac": round(achieved / hbm, 4), "traffic": traffic(name),
                            "algorithmic_bytes_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
+            if "survey_work" in k:
+                roofs[name]["survey_bytes_per_launch"] = int(k["survey_work"])
+                roofs[name]["frac_survey_count"] = round(k["survey_work"] / (k["ms"] / 1e3) / 1e9 / hbm, 4)
         else:
             achieved = k["work"] / (k["ms"] / 1e3) / 1e12
             roofs[name] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
@@ -441,10 +488,25 @@ def run_gpu(args):
             plain_step()
         b2.record(stream)
         torch.cuda.synchronize()
+        pms_eager = max_over_ranks(a.elapsed_time(b2) / args.steps)
+        # like for like with the headline: the 16 one-view steps captured as one CUDA graph
+        plain_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(plain_graph):
+            plain_step()
+        for _ in range(max(1, args.warmup)):
+            plain_graph.replay()
+        torch.cuda.synchronize()
+        barrier()
+        a.record(stream)
+        for _ in range(args.steps):
+            plain_graph.replay()
+        b2.record(stream)
+        torch.cuda.synchronize()
         pms = max_over_ranks(a.elapsed_time(b2) / args.steps)
         out["plain"] = {"ms_per_16_views": round(pms, 4), "views_per_s": round(job_rate(world, nv, pms), 3),
-                        "batched_over_plain": round(pms / ms, 4)}
-        del plain
+                        "batched_over_plain": round(pms / ms, 4), "timing": "CUDA graph replays, as the headline",
+                        "eager_ms_per_16_views": round(pms_eager, 4)}
+        del plain, plain_graph
 
         # ---- render FPS, 1 M Gaussians at 1280x720: SG colour vs SH degree 3
         fps = {}
@@ -452,7 +514,6 @@ def run_gpu(args):
                                             ("adaptive_sh012_sg3", 2, 3, (0.5, 0.9), I.AXIS_FREE),
                                             ("dc_sg3_frame", 0, 3, None, I.AXIS_ORTHO_FRAME)):
             sc1, cams1 = I.workload(1, sh_degree=L, num_lobes=K, axis_mode=mode)
-            cams1 = cams1[:8]
             if adaptive:
                 # degree 0 for the smaller half of the records, 1 up to the 90th percentile
                 # of the pixel radius, 2 above (the paper: most Gaussians are small)
@@ -481,9 +542,26 @@ def run_gpu(args):
             b2.record(stream)
             torch.cuda.synchronize()
             fms = max_over_ranks(a.elapsed_time(b2) / (reps * len(rs)))
+            # the same 32 views in one batched forward launch
+            rb_ = Rasterizer(m1, cams1, settings)
+            ob = torch.empty(3 * rb_.num_pixels, device="cuda")
+            rb_.forward(m1, out_rgb=ob, sync=True)
+            rb_ = Rasterizer(m1, cams1, settings, capacity=int(rb_.num_instances * 1.02) + 4096)
+            ob = torch.empty(3 * rb_.num_pixels, device="cuda")
+            for _ in range(2):
+                rb_.forward(m1, out_rgb=ob, sync=False)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(reps):
+                rb_.forward(m1, out_rgb=ob, sync=False)
+            b2.record(stream)
+            torch.cuda.synchronize()
+            bms = max_over_ranks(a.elapsed_time(b2) / reps)
             fps[label] = {"ms_per_frame": round(fms, 4), "fps": round(1e3 / fms, 1),
+                          "batched_32_views_ms": round(bms, 4), "batched_fps": round(len(cams1) * 1e3 / bms, 1),
                           "floats_per_gaussian": sc1.floats_per_gaussian(),
                           "model_mb": round(sc1.n * 4 * sc1.floats_per_gaussian() / 1e6, 1)}
+            del rb_, ob
             if adaptive:  # share of the visible records that summed bands up to 0, 1, 2
                 rad = torch.cat([r1.region("REC1", torch.float32)[:4 * sc1.n].view(-1, 4)[:, 3][
                     r1.region("TILES", torch.int32)[:sc1.n] != 0] for r1, _ in rs])
@@ -494,7 +572,8 @@ def run_gpu(args):
         fps["sg_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["sh1_sg3"]["ms_per_frame"], 4)
         fps["adaptive_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["adaptive_sh012_sg3"]["ms_per_frame"], 4)
         fps["frame_over_sh3_speedup"] = round(fps["sh3"]["ms_per_frame"] / fps["dc_sg3_frame"]["ms_per_frame"], 4)
-        fps["workload"] = "1M clustered Gaussians, 8 orbit views at 1280x720, forward only, one view per launch"
+        fps["workload"] = ("1M clustered Gaussians, 32 orbit views at 1280x720, forward only: one view per launch "
+                           "(fps) and all 32 in one batched launch (batched_fps)")
         out["render_fps"] = fps
 
         # ---- training iterations (render, L1, backward, fused Adam) on 2.5M Gaussians, one
@@ -668,6 +747,7 @@ def run_gpu(args):
     ems = max_over_ranks(a.elapsed_time(b2) / args.steps)
     out["e2e"] = {"value": round(job_rate(world, nv, ems), 3), "unit": UNIT, "ms_per_step": round(ems, 4),
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                  "link_gbps": copy_bandwidth(),
                   "overlap": "step k+1's uploads (parameters, targets) on one copy stream and step k's "
                              "read-back (all gradient planes, loss) on another during the compute; "
                              "double-buffered inputs and gradients"}
