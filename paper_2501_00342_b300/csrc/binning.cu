@@ -249,7 +249,10 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, cons
     const bool overflow = st->m > (unsigned long long)capacity;  // reported by the scan
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const uint32_t n32 = (uint32_t)n;
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < R;
+    // only the first num_visible sorted positions hold records with instances (the record
+    // sort dropped the others); the positions past them have no tiles
+    const int64_t kept = min(R, (int64_t)st->num_visible);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < kept;
          base += warps * 32) {
         const int64_t j = base + lane;
         // the record's count from the scan: the difference of consecutive offsets
