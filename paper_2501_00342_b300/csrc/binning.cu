@@ -51,8 +51,20 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
     uint32_t v[kScanItems];
     if (perm) {  // counts carried by the depth-sorted record values; none past the kept ones
         const int64_t nv = n_valid ? (int64_t)*n_valid : R;
+        if (base + kScanItems <= nv) {  // 16-byte loads: the thread's 16 values are consecutive
+            const uint4* p4 = reinterpret_cast<const uint4*>(perm + base);
 #pragma unroll
-        for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < nv) ? rv.count(perm[base + q], in) : 0u;
+            for (int q = 0; q < kScanItems / 4; ++q) {
+                const uint4 w = __ldg(p4 + q);
+                v[4 * q] = rv.count(w.x, in);
+                v[4 * q + 1] = rv.count(w.y, in);
+                v[4 * q + 2] = rv.count(w.z, in);
+                v[4 * q + 3] = rv.count(w.w, in);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < nv) ? rv.count(perm[base + q], in) : 0u;
+        }
     } else if (base + kScanItems <= R) {
         const uint4* p4 = reinterpret_cast<const uint4*>(in + base);
 #pragma unroll
@@ -125,29 +137,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* __re
 
 // Keys of the record sort: the float bits of the view depth of a record with instances
 // (depth > near > 0, so the bits order like the values), 0xffffffff for the others.
-// The lanes holding the same value d (d < 2^BITS), from one ballot per bit.
-template <int BITS>
-__device__ __forceinline__ uint32_t same_value_lanes(uint32_t d) {
-    uint32_t peers = kFullMask;
-#pragma unroll
-    for (int i = 0; i < BITS; ++i) {
-        const uint32_t bit = (d >> i) & 1u;
-        const uint32_t b = __ballot_sync(kFullMask, bit);
-        peers &= bit ? b : ~b;
-    }
-    return peers;
-}
-
 // Digit histograms of every pass of the record sort over the keys of the records with
 // instances (view depth bits; 0xffffffff marks the others, which the sort drops), per-warp
 // shared copies.  The low digits of depth bits are spread: one shared atomic each; the
-// high ones (exponent and top mantissa bits) repeat within a warp: the warp adds each
-// distinct digit once.  Also stores R in st->num_records and adds the kept records to
-// st->num_visible (cleared before the launch).
+// high ones (exponent and top mantissa bits) repeat within a warp: the warp finds the lanes
+// of each distinct digit with one match-any and adds it once.  Also stores R in
+// st->num_records and adds the kept records to st->num_visible (cleared before the launch).
 template <int RB>
 __global__ void __launch_bounds__(256) record_hist_kernel(const uint32_t* __restrict__ keys, int64_t R,
-                                                          DeviceStatus* st, int passes, uint32_t* __restrict__ hist) {
+                                                          DeviceStatus* st, uint32_t* __restrict__ hist) {
     constexpr int RADIX = 1 << RB;
+    constexpr int passes = (32 + RB - 1) / RB;  // a 32-bit key in digits of RB bits (the last narrower)
     extern __shared__ uint32_t h[];  // [8 warps][passes][RADIX]
     for (int j = threadIdx.x; j < 8 * passes * RADIX; j += blockDim.x) h[j] = 0;
     __syncthreads();
@@ -172,12 +172,13 @@ __global__ void __launch_bounds__(256) record_hist_kernel(const uint32_t* __rest
             const bool kept = key[u] != 0xffffffffu;
             const uint32_t live = __ballot_sync(kFullMask, kept);
             kept_count += __popc(live);
+#pragma unroll
             for (int p = 0; p < passes; ++p) {
                 const uint32_t d = (key[u] >> (p * RB)) & (RADIX - 1);
                 if (2 * p < passes) {
                     if (kept) atomicAdd(&hw[p * RADIX + d], 1u);
                 } else {
-                    const uint32_t peers = same_value_lanes<RB>(d) & live;
+                    const uint32_t peers = __match_any_sync(kFullMask, kept ? d : 0xffffffffu) & live;
                     if (kept && lane == 31 - __clz(peers)) hw[p * RADIX + d] += __popc(peers);
                     __syncwarp();
                 }
@@ -534,6 +535,7 @@ cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st
                                cudaStream_t s) {
     int passes, rb;
     sort_digit_plan(0, 32, digit_bits, &passes, &rb);
+    if (passes != (32 + rb - 1) / rb) return cudaErrorInvalidValue;  // the kernel's pass count
     cudaError_t e = launch_fill_u32(hist, 0u, (size_t)passes << rb, s);
     if (e == cudaSuccess) e = launch_fill_u32(&st->num_visible, 0u, 1, s);
     if (e != cudaSuccess) return e;
@@ -547,7 +549,7 @@ cudaError_t launch_record_hist(const uint32_t* keys, int64_t R, DeviceStatus* st
         if ((e = cudaFuncSetAttribute(record_hist_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem)) != cudaSuccess)                                                \
             return e;                                                                                            \
-        record_hist_kernel<RB><<<blocks, threads, smem, s>>>(keys, R, st, passes, hist);                         \
+        record_hist_kernel<RB><<<blocks, threads, smem, s>>>(keys, R, st, hist);                                 \
         break;
         SGS_RH(4) SGS_RH(5) SGS_RH(6) SGS_RH(7) SGS_RH(8)
 #undef SGS_RH
