@@ -228,7 +228,7 @@ __device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, uint3
 // depth never has to travel with the instances.  The digit histograms of that tile sort are
 // counted here (count_tile_digits).
 template <int RB>
-__global__ void __launch_bounds__(256) duplicate_kernel(const ViewTable vt, const uint4* __restrict__ spans,
+__global__ void __launch_bounds__(256, 5) duplicate_kernel(const ViewTable vt, const uint4* __restrict__ spans,
                                                          const RecordValue rv,
                                                          const float4* __restrict__ rec0,
                                                          const float4* __restrict__ rec1,
@@ -500,7 +500,9 @@ cudaError_t launch_duplicate(const ViewTable& vt, const RecordPtrs& p, const uin
     if (passes > (32 + digit_bits - 1) / digit_bits) return cudaErrorInvalidValue;
     const int threads = 256;
     const int64_t want = (R + threads - 1) / threads;
-    const unsigned blocks = (unsigned)stride_grid(want, 8);
+    // 48 registers: 5 CTAs per SM, two waves of them over the grid-stride loop (the kernel
+    // waits on the depth-ordered gathers of the row tables; more warps keep more in flight)
+    const unsigned blocks = (unsigned)stride_grid(want, 10);
     switch (digit_bits) {
 #define SGS_DUP(RB) case RB: duplicate_kernel<RB><<<blocks, threads, 0, s>>>(vt, p.spans, record_value(R), p.rec0, \
         p.rec1, perm, offsets, n, R, st, capacity, keys, vals, passes, hist); break;
