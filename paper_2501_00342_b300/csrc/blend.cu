@@ -74,7 +74,15 @@ __device__ __forceinline__ WarpBlock warp_block(const ViewTable& vt) {
 // rounding of the bounds (the exponential's and logarithm's errors are below 1e-5 there),
 // which the slack and the pad cover (the chord's own rounding is far below that slack), so
 // a warp without its bit has no pixel that blends the Gaussian.  A degenerate conic or a
-// non-finite centre sets every bit; an opacity at which no alpha reaches 1/255 none.
+// non-finite centre sets every bit; an opacity at which no alpha reaches 1/255 none.  The
+// divisions and square roots are the hardware's approximate ones (relative error a few
+// 1e-7): the test needs no correctly rounded operation, the slack covers them many times.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int PPT>
 __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCoord& tc, float px, float py,
                                                float qa, float qb, float qc, float o) {
@@ -89,10 +97,10 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
     const float Qs = fminf(kSpanQ, (2.0f * __logf(o * 255.0f) + 0.002f) * (kSpanQ / 9.0f));
     if (!(Qs > 0.0f)) return 0u;
     const int nbx = vt.tile_w >> 3, nby = vt.tile_h / BH;
-    const float k = Qs / det;
-    const float ex = sqrtf(k * C), ey = sqrtf(k * A);
-    const float dyr = -B * ex / C;  // row offset of the rightmost point
-    const float iA = 1.0f / A, Ak = A * Qs;
+    const float k = __fdividef(Qs, det);
+    const float ex = sqrt_approx(k * C), ey = sqrt_approx(k * A);
+    const float dyr = __fdividef(-B * ex, C);  // row offset of the rightmost point
+    const float iA = __fdividef(1.0f, A), Ak = A * Qs;
     const float b0 = fmaxf(ceilf((gy - ey - kSpanPad - (float)(BH - 1)) * (1.0f / BH)), 0.0f);
     const float b1 = fminf(floorf((gy + ey + kSpanPad) * (1.0f / BH)), (float)(nby - 1));
     uint32_t mask = 0;
@@ -100,8 +108,8 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
         const float u0 = fmaxf((float)(b * BH) - kSpanPad - gy, -ey);
         const float u1 = fminf((float)(b * BH + BH - 1) + kSpanPad - gy, ey);
         if (!(u0 <= u1)) continue;
-        const float s0 = sqrtf(fmaxf(0.0f, Ak - det * u0 * u0));
-        const float s1 = sqrtf(fmaxf(0.0f, Ak - det * u1 * u1));
+        const float s0 = sqrt_approx(fmaxf(0.0f, Ak - det * u0 * u0));
+        const float s1 = sqrt_approx(fmaxf(0.0f, Ak - det * u1 * u1));
         const float xmax = (u0 <= dyr && dyr <= u1) ? ex : fmaxf(s0 - B * u0, s1 - B * u1) * iA;
         const float xmin = (u0 <= -dyr && -dyr <= u1) ? -ex : fminf(-B * u0 - s0, -B * u1 - s1) * iA;
         // Block column c holds pixel-centre columns [8c, 8c + 7].

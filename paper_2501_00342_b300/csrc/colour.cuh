@@ -136,10 +136,10 @@ __device__ __forceinline__ float frame_axes(const float f[3], float q[4], float 
 
 // Pre-clamp colour at unit direction d from the first nsh SH coefficients and the K lobes
 // (Eq. 4, 5, 7, 9).  P provides csh(k, c), camp(k, c), caxis(k, c) (unit axes) and
-// csharp(k).  Every operation is written out (fmaf, no contraction left to the compiler),
-// so that the forward pass, which reads the parameters from shared memory, and the
-// backward pass, which holds them in registers, compute the same bits and take the same
-// colour-clamp decisions.
+// csharp(k).  The lobe's exponential is the hardware's (__expf, a few 1e-7 relative at
+// the sharpness range's exponents): colour is not a binning decision, and the backward pass
+// takes the forward's colour-clamp decisions from the record's flags, not from its own
+// evaluation.
 template <int L, int K, int AX, class P>
 __device__ __forceinline__ void colour_eval(const P& p, const float* d, float* pre, int nsh) {
     constexpr int NSH = (L + 1) * (L + 1);
@@ -157,7 +157,7 @@ __device__ __forceinline__ void colour_eval(const P& p, const float* d, float* p
     for (int k = 0; k < K; ++k) {
         const float cosv =
             AX == kAxWorld ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
-        const float e = expf(p.csharp(k) * (cosv - 1.0f));
+        const float e = __expf(p.csharp(k) * (cosv - 1.0f));
 #pragma unroll
         for (int c = 0; c < 3; ++c) pre[c] = fmaf(p.camp(k, c), e, pre[c]);
     }
@@ -282,7 +282,7 @@ struct ColourGrads {
         for (int k = 0; k < K; ++k) {
             const float cs =
                 AX == kAxWorld ? d[k] : fmaf(p.caxis(k, 0), d[0], fmaf(p.caxis(k, 1), d[1], p.caxis(k, 2) * d[2]));
-            const float e = expf(p.csharp(k) * (cs - 1.0f));
+            const float e = __expf(p.csharp(k) * (cs - 1.0f));
             float s = 0.0f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {

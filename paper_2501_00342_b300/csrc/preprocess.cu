@@ -251,14 +251,15 @@ __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool vi
     return rs.ok ? hits : 0u;
 }
 
+// The view direction of Eq. 5, d = (X - campos)/|X - campos|, and 1/|X - campos| (one
+// hardware reciprocal square root: the colour is not a binning decision).
 __device__ __forceinline__ void view_direction(const View& cam, const float X[3], float d[3],
-                                               float& len) {
+                                               float& inv_len) {
     const float dx = X[0] - cam.campos[0], dy = X[1] - cam.campos[1], dz = X[2] - cam.campos[2];
-    len = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float inv = 1.0f / len;
-    d[0] = dx * inv;
-    d[1] = dy * inv;
-    d[2] = dz * inv;
+    inv_len = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    d[0] = dx * inv_len;
+    d[1] = dy * inv_len;
+    d[2] = dz * inv_len;
 }
 
 constexpr int kPreThreads = 128;
@@ -366,8 +367,8 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
             flags[r] = 0u;
             continue;
         }
-        float d[3], len;
-        view_direction(cam, X, d, len);
+        float d[3], inv_len;
+        view_direction(cam, X, d, inv_len);
         float pre[3];
         const int D = record_sh_degree<L>(g, P.radius);
         colour_eval<L, K, AX>(cp, d, pre, (D + 1) * (D + 1));
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(kPreThreads, 8) preprocess_kernel(const sgs_ga
 // ------------------------------------------------------------------------------ backward
 // The intermediates of the projection that the chain rule needs (t, the clamped x/z and
 // y/z, J, T = J W, T Sigma and the conic), recomputed in plain single precision with fused
-// multiply-adds and one reciprocal.  The frustum-clamp decisions are the forward's, read
+// multiply-adds and two approximate reciprocals.  The frustum-clamp decisions are the forward's, read
 // from the record's flags (kFlagClampX/Y), so every branch is the one the forward took; the
 // values differ from the forward's correctly rounded ones by a few units in the last place,
 // far inside the gradients' tolerance.
@@ -408,7 +409,7 @@ __device__ __forceinline__ void project_fast(const View& cam, const float X[3], 
 #pragma unroll
     for (int r = 0; r < 3; ++r)
         P.t[r] = fmaf(V[4 * r], X[0], fmaf(V[4 * r + 1], X[1], fmaf(V[4 * r + 2], X[2], V[4 * r + 3])));
-    const float tz = P.t[2], iz = 1.0f / tz;
+    const float tz = P.t[2], iz = __fdividef(1.0f, tz);
     const float u0 = P.t[0] * iz, v0 = P.t[1] * iz;
     P.clampx = (f & kFlagClampX) != 0u;
     P.clampy = (f & kFlagClampY) != 0u;
@@ -431,7 +432,7 @@ __device__ __forceinline__ void project_fast(const View& cam, const float X[3], 
     P.a = fmaf(P.TS[0][0], P.T[0][0], fmaf(P.TS[0][1], P.T[0][1], fmaf(P.TS[0][2], P.T[0][2], 0.3f)));
     P.b = fmaf(P.TS[0][0], P.T[1][0], fmaf(P.TS[0][1], P.T[1][1], P.TS[0][2] * P.T[1][2]));
     P.c = fmaf(P.TS[1][0], P.T[1][0], fmaf(P.TS[1][1], P.T[1][1], fmaf(P.TS[1][2], P.T[1][2], 0.3f)));
-    const float idet = 1.0f / fmaf(P.a, P.c, -P.b * P.b);
+    const float idet = __fdividef(1.0f, fmaf(P.a, P.c, -P.b * P.b));
     P.A = P.c * idet;
     P.B = -P.b * idet;
     P.C = P.a * idet;
@@ -500,8 +501,8 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         gop += g1.y;
         // colour: the SH degree and the colour-clamp decisions are the forward's (flags)
         {
-            float d[3], len;
-            view_direction(cam, X, d, len);
+            float d[3], inv;
+            view_direction(cam, X, d, inv);
             const int D = (int)((f >> kFlagShift) & 3u);
             const int nsh = (D + 1) * (D + 1);
             const float grgb[3] = {g1.z, g1.w, g2.x};
@@ -510,7 +511,6 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
             for (int c = 0; c < 3; ++c) gpre[c] = (f >> c) & 1u ? 0.0f : grgb[c];
             cg.accumulate(cp, d, gpre, gd, nsh);
             const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
-            const float inv = 1.0f / len;
 #pragma unroll
             for (int c = 0; c < 3; ++c) gX[c] += (gd[c] - d[c] * dot) * inv;
         }
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         const float gJ02 = gT[0][0] * V[8] + gT[0][1] * V[9] + gT[0][2] * V[10];
         const float gJ11 = gT[1][0] * V[4] + gT[1][1] * V[5] + gT[1][2] * V[6];
         const float gJ12 = gT[1][0] * V[8] + gT[1][1] * V[9] + gT[1][2] * V[10];
-        const float tz = P.t[2], iz = 1.0f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        const float tz = P.t[2], iz = __fdividef(1.0f, tz), iz2 = iz * iz, iz3 = iz2 * iz;
         const float tx = P.u * tz, ty = P.v * tz;
         float gt[3] = {0.0f, 0.0f, 0.0f};
         gt[2] += -cam.fx * iz2 * gJ00 - cam.fy * iz2 * gJ11 + 2.0f * cam.fx * tx * iz3 * gJ02 +
