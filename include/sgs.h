@@ -251,8 +251,13 @@ typedef enum {
     SGS_REGION_PIX_T = 12,  /* float[num_pixels]: final transmittance */
     SGS_REGION_PIX_LAST = 13, /* uint32[num_pixels]: 1 + position of the last contributor
                                  in the tile's list (0: none) */
-    SGS_REGION_GRAD2D = 14, /* float4[2][R] then float[R]: dL/d(px, py, A, B), (C, opacity, r, g),
-                               then dL/db; zero outside sgs_render_backward (its last kernel
+    SGS_REGION_GRAD2D = 14, /* float4[2][R] then float[R]: the reverse blend's per-record
+                               pixel sums (S_x, S_y, S_xx, S_xy), (S_yy, S_1, dL/dr, dL/dg),
+                               then dL/db, where S_m sums gG m over the pixels blending the
+                               record below the 0.99 alpha clamp, gG = dL/dalpha exp(power),
+                               m in {1, dx, dy, dx^2, dx dy, dy^2}, d = centre - pixel centre
+                               (the preprocess backward turns them into dL/d(centre, conic,
+                               opacity)); zero outside sgs_render_backward (its last kernel
                                clears what its reverse blend accumulated) */
     SGS_REGION_PIX_COUNT = 15, /* uint2[num_pixels]: list entries the pixel evaluated, and
                                   how many of them it blended */

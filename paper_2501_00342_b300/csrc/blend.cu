@@ -17,8 +17,13 @@
 // rebuilding T_k = T_{k+1} / (1 - alpha_k) from the stored final transmittance and
 // carrying the normalised colour behind (acc += alpha (rgb - acc), starting at bg).  It
 // recomputes power and alpha with the same operations as the forward pass, so every skip
-// decision is identical; per Gaussian the warp's 9 gradient terms are summed with shuffles
-// and added with two 16-byte vector atomics and one scalar atomic.
+// decision is identical; per Gaussian the warp's 9 gradient sums are reduced with shuffles
+// and added with two 16-byte vector atomics and one scalar atomic.  The sums are those of
+// gG = dL/dalpha G (where the 0.99 clamp is not active) and its moments gG dx, gG dy,
+// gG dx^2, gG dx dy, gG dy^2 (d = centre - pixel centre), and of alpha T dL/dC per channel:
+// the power is a quadratic form in d, so its derivatives in the centre and the conic are
+// linear in these sums, and the preprocess backward applies the opacity and the conic once
+// per record instead of once per pixel.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -655,16 +660,14 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                     p.acc1 = fmaf(alpha, e1, p.acc1);
                     p.acc2 = fmaf(alpha, e2, p.acc2);
                     if (oG <= kAlphaMax) {
-                        // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2):
-                        // d/d px = u + qa dx, d/d py = qb dx + 2 qc dy, d/d(qa, qb, qc) = (dx^2, dx dy, dy^2)
+                        // wG = dL/dalpha G and its moments (the 2D gradient record's sums)
                         const float gG = dalpha * G;
-                        const float gpow = gG * b.y;
-                        d[0] = fmaf(gpow, fmaf(a.z, dx, st.u), d[0]);
-                        d[1] = fmaf(gpow, fmaf(a.w, dx, st.t + st.t), d[1]);
-                        const float h = -0.5f * gpow;
-                        d[2] = fmaf(h * dx, dx, d[2]);
-                        d[3] = fmaf(-gpow * dx, dy, d[3]);
-                        d[4] = fmaf(h * dy, dy, d[4]);
+                        const float gx = gG * dx, gy = gG * dy;
+                        d[0] += gx;
+                        d[1] += gy;
+                        d[2] = fmaf(gx, dx, d[2]);
+                        d[3] = fmaf(gx, dy, d[3]);
+                        d[4] = fmaf(gy, dy, d[4]);
                         d[5] += gG;
                     }
                 }
@@ -734,8 +737,10 @@ __device__ __forceinline__ void blend_pair_backward_tile(
     }
     const f32x2 pcx = pk((float)x + 0.5f, (float)x + 0.5f), pcy = pk((float)y0 + 0.5f, (float)y1 + 0.5f);
     const f32x2 gr = pk(g[0][0], g[1][0]), gg = pk(g[0][1], g[1][1]), gb = pk(g[0][2], g[1][2]);
-    const f32x2 one = pk(1.0f, 1.0f), neg_half = pk(-0.5f, -0.5f);
-    float acc[2][3] = {{bg0, bg1, bg2}, {bg0, bg1, bg2}};
+    const f32x2 one = pk(1.0f, 1.0f);
+    // the pixel's upstream gradient dotted with the colour behind (acc += alpha (rgb - acc),
+    // from bg): one value per pixel carries what the three channels' accumulators would
+    f32x2 gacc = fma2(gr, pk(bg0, bg0), fma2(gg, pk(bg1, bg1), mul2(gb, pk(bg2, bg2))));
     const uint32_t wmax = __reduce_max_sync(kFullMask, max(last[0], last[1]));
     if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_max_last, wmax);
     __syncthreads();
@@ -779,44 +784,27 @@ __device__ __forceinline__ void blend_pair_backward_tile(
                 const f32x2 alpha = pk(use0 ? a0 : 0.0f, use1 ? a1 : 0.0f);
                 const f32x2 Tp = pk(T[0], T[1]);
                 const f32x2 w = mul2(alpha, Tp);
-                // colour behind minus this Gaussian's colour; acc += alpha (c - acc)
+                // dL/dalpha = T g.(rgb - acc): the gradient's dot with this Gaussian's colour
+                // minus its dot with the colour behind
                 const ulonglong2 rg = pairs(e_rg + j), bb = pairs(e_b + j);
-                const f32x2 er = sub2(rg.x, pk(acc[0][0], acc[1][0]));
-                const f32x2 eg = sub2(rg.y, pk(acc[0][1], acc[1][1]));
-                const f32x2 eb = sub2(bb.x, pk(acc[0][2], acc[1][2]));
-                const f32x2 dalpha = mul2(Tp, fma2(gr, er, fma2(gg, eg, mul2(gb, eb))));
-                {
-                    const float2 r = upk(er), gv = upk(eg), b = upk(eb);
-                    if (use0) {
-                        acc[0][0] = fmaf(a0, r.x, acc[0][0]);
-                        acc[0][1] = fmaf(a0, gv.x, acc[0][1]);
-                        acc[0][2] = fmaf(a0, b.x, acc[0][2]);
-                    }
-                    if (use1) {
-                        acc[1][0] = fmaf(a1, r.y, acc[1][0]);
-                        acc[1][1] = fmaf(a1, gv.y, acc[1][1]);
-                        acc[1][2] = fmaf(a1, b.y, acc[1][2]);
-                    }
-                }
-                // through alpha = o G only where the 0.99 clamp is not active
+                const f32x2 e = sub2(fma2(gr, rg.x, fma2(gg, rg.y, mul2(gb, bb.x))), gacc);
+                const f32x2 dalpha = mul2(Tp, e);
+                gacc = fma2(alpha, e, gacc);  // alpha is 0 for a pixel that does not blend it
+                // through alpha = o G only where the 0.99 clamp is not active: gG = dL/dalpha G
+                // and its moments gG (dx, dy, dx^2, dx dy, dy^2), summed over the pixels; the
+                // preprocess backward applies o and the conic once per record
                 const float2 gGv = upk(mul2(dalpha, G));
                 const f32x2 gG = pk(use0 && oG.x <= kAlphaMax ? gGv.x : 0.0f, use1 && oG.y <= kAlphaMax ? gGv.y : 0.0f);
-                const f32x2 gpow = mul2(gG, c.y);
-                // power = qa dx^2 + qb dx dy + qc dy^2, (qa, qb, qc) = (-A/2, -B, -C/2):
-                // d/d px = u + qa dx, d/d py = qb dx + 2 qc dy, d/d(qa, qb, qc) = (dx^2, dx dy, dy^2)
-                const f32x2 h = mul2(neg_half, gpow);
-                const float2 t0 = upk(mul2(gpow, fma2(q.x, dx, u)));
-                const float2 t1 = upk(mul2(gpow, fma2(q.y, dx, add2(t, t))));
-                const float2 t2 = upk(mul2(mul2(h, dx), dx));
-                const float2 t3 = upk(mul2(mul2(gpow, dx), dy));
-                const float2 t4 = upk(mul2(mul2(h, dy), dy));
+                const f32x2 gx = mul2(gG, dx), gy = mul2(gG, dy);
+                const float2 t0 = upk(gx), t1 = upk(gy);
+                const float2 t2 = upk(mul2(gx, dx)), t3 = upk(mul2(gx, dy)), t4 = upk(mul2(gy, dy));
                 const float2 t5 = upk(gG);
                 const float2 t6 = upk(mul2(gr, w)), t7 = upk(mul2(gg, w)), t8 = upk(mul2(gb, w));
                 float d[9];
                 d[0] = t0.x + t0.y;
                 d[1] = t1.x + t1.y;
                 d[2] = t2.x + t2.y;
-                d[3] = -(t3.x + t3.y);
+                d[3] = t3.x + t3.y;
                 d[4] = t4.x + t4.y;
                 d[5] = t5.x + t5.y;
                 d[6] = t6.x + t6.y;

@@ -159,9 +159,12 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                   const float* pix_T, const uint32_t* pix_last,
                                   const float* dL_drgb, float4* grad2d, int64_t R,
                                   const DeviceStatus* st, cudaStream_t s);
-// grad2d: per record dL/d(px, py, A, B) and dL/d(C, opacity, r, g) as float4[2][R], then
-// dL/db as float[R] (from grad2d + 2 R).  Cleared once when a workspace is bound; the
-// preprocess backward clears what the reverse blend wrote.
+// grad2d: per record the reverse blend's pixel sums (S_x, S_y, S_xx, S_xy) and
+// (S_yy, S_1, dL/dr, dL/dg) as float4[2][R], then dL/db as float[R] (from grad2d + 2 R);
+// S_m sums gG m, gG = dL/dalpha exp(power), m the moments 1, dx, dy, dx^2, dx dy, dy^2 of
+// d = centre - pixel centre, and the preprocess backward turns them into the centre,
+// conic and opacity gradients.  Cleared once when a workspace is bound; the preprocess
+// backward clears what the reverse blend wrote.
 cudaError_t launch_zero_grad2d(float4* grad2d, int64_t R, cudaStream_t s);
 
 // training: fused Adam step over all parameter planes

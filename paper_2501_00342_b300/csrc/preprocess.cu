@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
 #pragma unroll
         for (int c = 0; c < 3; ++c) gSig[r][c] = 0.0f;
     float gop = 0.0f;
+    const float opacity = __ldg(g.opacity + i);
     // the next view's record flags and 2D gradients travel to shared memory while this
     // view's chain rule runs (double-buffered, one slot per thread)
     __shared__ __align__(16) float4 s_g[2][3][kPreThreads];
@@ -514,9 +515,15 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
 #pragma unroll
             for (int c = 0; c < 3; ++c) gX[c] += (gd[c] - d[c] * dot) * inv;
         }
-        // conic -> Sigma2D:  dS = -Con G Con,  G = [[gA, gB/2], [gB/2, gC]]
+        // The reverse blend's sums over the pixels that blend the record below the alpha
+        // clamp: S = gG (dx, dy, dx^2, dx dy, dy^2) with gG = dL/dalpha G, d = centre - pixel
+        // centre.  power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 and alpha = o G give
+        // dL/d centre = -o (A S_x + B S_y, B S_x + C S_y), dL/d(A, B, C) = -o (S_xx / 2,
+        // S_xy, S_yy / 2).
         const float A = P.A, B = P.B, C = P.C;
-        const float gA = g0.z, gB = g0.w, gC = g1.x;
+        const float gpx = -opacity * fmaf(A, g0.x, B * g0.y), gpy = -opacity * fmaf(B, g0.x, C * g0.y);
+        const float gA = -0.5f * opacity * g0.z, gB = -opacity * g0.w, gC = -0.5f * opacity * g1.x;
+        // conic -> Sigma2D:  dS = -Con G Con,  G = [[gA, gB/2], [gB/2, gC]]
         const float P00 = A * gA + 0.5f * B * gB, P01 = 0.5f * A * gB + B * gC;
         const float P10 = B * gA + 0.5f * C * gB, P11 = 0.5f * B * gB + C * gC;
         const float G2[2][2] = {{-(P00 * A + P01 * B), -(P00 * B + P01 * C)},
@@ -552,10 +559,10 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
         if (P.clampx) gt[2] += gtx * P.u; else gt[0] += gtx;
         if (P.clampy) gt[2] += gty * P.v; else gt[1] += gty;
         // screen mean
-        gt[0] += cam.fx * iz * g0.x;
-        gt[2] += -cam.fx * P.t[0] * iz2 * g0.x;
-        gt[1] += cam.fy * iz * g0.y;
-        gt[2] += -cam.fy * P.t[1] * iz2 * g0.y;
+        gt[0] += cam.fx * iz * gpx;
+        gt[2] += -cam.fx * P.t[0] * iz2 * gpx;
+        gt[1] += cam.fy * iz * gpy;
+        gt[2] += -cam.fy * P.t[1] * iz2 * gpy;
         // t = W X + t_v
 #pragma unroll
         for (int c = 0; c < 3; ++c) gX[c] += V[c] * gt[0] + V[4 + c] * gt[1] + V[8 + c] * gt[2];
