@@ -134,7 +134,8 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
 // kPairs: each scalar the two-pixel kernels combine with a pair of pixels duplicated into
 //         a packed pair, (qa qa, qb qb), (qc qc, o o), (px px, py py), then the colour
 //         record as read;
-// kPairsColour: as kPairs, with the colour as pairs too: (r r, g g), (b b, 0 0).
+// kPairsColour: as kPairs, with the colour as pairs too and the record id beside blue:
+//         (r r, g g), (b b, id 0) (id as the bits of a float).
 enum StageLayout { kPlain = 0, kPairs = 1, kPairsColour = 2 };
 constexpr int stage_fields(int layout) { return layout == kPlain ? 3 : layout == kPairs ? 4 : 5; }
 
@@ -172,7 +173,7 @@ __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileC
                 sb[3 * batch + j] = r2;
             } else {
                 sb[3 * batch + j] = make_float4(r2.x, r2.x, r2.y, r2.y);
-                sb[4 * batch + j] = make_float4(r2.z, r2.z, 0.0f, 0.0f);
+                sb[4 * batch + j] = make_float4(r2.z, r2.z, __uint_as_float(id), 0.0f);
             }
         }
         if (!mask_in) mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x, alpha_bound ? r1.y : 1.0f);
@@ -541,6 +542,40 @@ __device__ __forceinline__ float warp_sum8(const float v[8], int lane) {
     return x;
 }
 
+// Sums 9 values over the warp with 13 shuffles: the first 8 by the reduce-scatter of
+// warp_sum8 and value 8 by butterflies over lane offsets 16, 8, 4; the two steps over
+// offsets 2 and 1 carry both (the lanes with bit 1 clear value ((lane >> 2) & 7), the
+// others value 8).  Returns in lanes with (lane & 3) == 0 the total of value
+// ((lane >> 2) & 7), in lanes with (lane & 3) == 2 the total of value 8.
+__device__ __forceinline__ float warp_sum9(const float v[9], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = b4 ? v[4 + i] : v[i], send = b4 ? v[i] : v[4 + i];
+        w[i] = keep + __shfl_xor_sync(kFullMask, send, 16);
+    }
+    float u[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = b3 ? w[2 + i] : w[i], send = b3 ? w[i] : w[2 + i];
+        u[i] = keep + __shfl_xor_sync(kFullMask, send, 8);
+    }
+    const float x = (b2 ? u[1] : u[0]) + __shfl_xor_sync(kFullMask, b2 ? u[0] : u[1], 4);
+    float e = v[8];
+    e += __shfl_xor_sync(kFullMask, e, 16);
+    e += __shfl_xor_sync(kFullMask, e, 8);
+    e += __shfl_xor_sync(kFullMask, e, 4);
+    float y = (b1 ? e : x) + __shfl_xor_sync(kFullMask, b1 ? x : e, 2);
+    y += __shfl_xor_sync(kFullMask, y, 1);
+    return y;
+}
+
+// *p += v in L2 (no return value).
+__device__ __forceinline__ void red_add1(float* p, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
 // grad += (a, b, c, d) as one 16-byte vector reduction in L2 (no return value).
 __device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -706,8 +741,7 @@ __device__ __forceinline__ void blend_pair_backward_tile(
     const float4* e_rg = sbuf + 3 * batch;  // (r r, g g)
     const float4* e_b = sbuf + 4 * batch;   // (b b, 0 0)
     const int words = (batch + 31) >> 5;
-    uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairsColour) * batch);
-    uint32_t* bits = sid + batch;
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairsColour) * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
     __shared__ uint32_t s_max_last;
     const TileCoord tc = tile_of(vt, tile);
@@ -746,16 +780,20 @@ __device__ __forceinline__ void blend_pair_backward_tile(
     __syncthreads();
     const int top = (int)s_max_last;
     const int lane = threadIdx.x & 31;
+    // where this lane's total of warp_sum9 goes: value i < 8 (lane 4 i) to float 4 id + i of
+    // the first 2D-gradient array (i < 4) or of the second, value 8 (lane 2) to the third
+    const bool red_lane = (lane & 3) == 0 || lane == 2;
+    float* const red_base = reinterpret_cast<float*>(grad2d) +
+                            (lane == 2 ? 8 * R : (int64_t)((lane >> 4) & 1) * 4 * R + ((lane >> 2) & 3));
+    const int red_step = lane == 2 ? 1 : 4;
     const int warp_last = (int)wmax;  // no pixel of this warp blends an entry at or past it
     for (int hi = top; hi > 0; hi -= batch) {
         const int lo = max(0, hi - batch);
         __syncthreads();
         const int cnt = hi - lo, groups = (cnt + 31) >> 5;
         for (int gr_ = (int)(threadIdx.x >> 5); gr_ < groups; gr_ += (int)(blockDim.x >> 5)) {
-            const uint32_t id = stage_group<2, kPairsColour>(vt, tc, gr_, cnt, vals + range.x + lo, R32, rec0, rec1,
-                                                             rec2, sbuf, batch, bits, words, nullptr,
-                vt.masks ? vt.masks + range.x + lo : nullptr);
-            if (gr_ * 32 + lane < cnt) sid[gr_ * 32 + lane] = id;
+            stage_group<2, kPairsColour>(vt, tc, gr_, cnt, vals + range.x + lo, R32, rec0, rec1, rec2, sbuf, batch,
+                                         bits, words, nullptr, vt.masks ? vt.masks + range.x + lo : nullptr);
         }
         __syncthreads();
         // this warp's entries below its last contributor, back to front
@@ -810,16 +848,9 @@ __device__ __forceinline__ void blend_pair_backward_tile(
                 d[6] = t6.x + t6.y;
                 d[7] = t7.x + t7.y;
                 d[8] = t8.x + t8.y;
-                // lanes 0, 4, ..., 28 hold the sums of values 0..7; lanes 0 and 16 gather
-                // values 0-3 and 4-7 and add them with one 16-byte vector reduction each
-                const float s8 = warp_sum8(d, lane);
-                const float s9 = warp_sum(d[8]);
-                const float u1 = __shfl_down_sync(kFullMask, s8, 4);
-                const float u2 = __shfl_down_sync(kFullMask, s8, 8);
-                const float u3 = __shfl_down_sync(kFullMask, s8, 12);
-                const uint32_t id = sid[j];
-                if ((lane & 15) == 0) red_add4(grad2d + (lane >> 4) * R + id, s8, u1, u2, u3);
-                if (lane == 0) atomicAdd(reinterpret_cast<float*>(grad2d + 2 * R) + id, s9);
+                // one reduction instruction: lanes 0, 4, ..., 28 add values 0..7, lane 2 value 8
+                const float s = warp_sum9(d, lane);
+                if (red_lane) red_add1(red_base + (size_t)(uint32_t)bb.y * red_step, s);
             }
         }
     }
@@ -965,7 +996,7 @@ cudaError_t launch_blend_backward(const ViewTable& vt, const uint2* ranges, cons
                                      R, st, s);
     if (vt.bwd_ppt == 2) {
         const int threads = vt.tile_w * vt.tile_h / 2;
-        const size_t smem = (size_t)batch * (stage_fields(kPairsColour) * sizeof(float4) + sizeof(uint32_t)) +
+        const size_t smem = (size_t)batch * stage_fields(kPairsColour) * sizeof(float4) +
                             (size_t)(threads / 32) * ((batch + 31) / 32) * 4;
         unsigned grid = 0;
         cudaError_t e = vt.persistent
