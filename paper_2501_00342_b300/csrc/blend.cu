@@ -128,7 +128,8 @@ __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCo
     return mask;
 }
 
-// Staged layouts of a batch entry in shared memory (field f of entry j at sb[f * batch + j]):
+// Staged layouts of a batch entry in shared memory (field f of entry j at sb[j * fields + f],
+// so that a visit finds all fields of its entry at one address plus constant offsets):
 // kPlain: the three records as read, (px, py, qa, qb), (qc, o, depth, radius),
 //         (r, g, b, clamp mask);
 // kPairs: each scalar the two-pixel kernels combine with a pair of pixels duplicated into
@@ -152,7 +153,7 @@ template <int PPT, int LAYOUT>
 __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileCoord& tc, int g, int cnt,
                                                 const uint32_t* __restrict__ first, uint32_t R,
                                                 const float4* __restrict__ rec0, const float4* __restrict__ rec1,
-                                                const float4* __restrict__ rec2, float4* sb, int batch,
+                                                const float4* __restrict__ rec2, float4* sb,
                                                 uint32_t* bits, int words, uint16_t* __restrict__ mask_out,
                                                 const uint16_t* __restrict__ mask_in, bool alpha_bound = true) {
     const int lane = threadIdx.x & 31, j = g * 32 + lane;
@@ -161,19 +162,20 @@ __device__ __forceinline__ uint32_t stage_group(const ViewTable& vt, const TileC
         if (mask_in) mask = mask_in[j];
         id = min(first[j], R - 1);  // ids are < R by construction
         const float4 r0 = rec0[id], r1 = rec1[id], r2 = rec2[id];
+        float4* e = sb + j * stage_fields(LAYOUT);
         if (LAYOUT == kPlain) {
-            sb[j] = r0;
-            sb[batch + j] = r1;
-            sb[2 * batch + j] = r2;
+            e[0] = r0;
+            e[1] = r1;
+            e[2] = r2;
         } else {
-            sb[j] = make_float4(r0.z, r0.z, r0.w, r0.w);
-            sb[batch + j] = make_float4(r1.x, r1.x, r1.y, r1.y);
-            sb[2 * batch + j] = make_float4(r0.x, r0.x, r0.y, r0.y);
+            e[0] = make_float4(r0.z, r0.z, r0.w, r0.w);
+            e[1] = make_float4(r1.x, r1.x, r1.y, r1.y);
+            e[2] = make_float4(r0.x, r0.x, r0.y, r0.y);
             if (LAYOUT == kPairs) {
-                sb[3 * batch + j] = r2;
+                e[3] = r2;
             } else {
-                sb[3 * batch + j] = make_float4(r2.x, r2.x, r2.y, r2.y);
-                sb[4 * batch + j] = make_float4(r2.z, r2.z, __uint_as_float(id), 0.0f);
+                e[3] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                e[4] = make_float4(r2.z, r2.z, __uint_as_float(id), 0.0f);
             }
         }
         if (!mask_in) mask = block_mask<PPT>(vt, tc, r0.x, r0.y, r0.z, r0.w, r1.x, alpha_bound ? r1.y : 1.0f);
@@ -270,9 +272,6 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
                                                      uint2* __restrict__ pix_count,
                                                      const DeviceStatus* __restrict__ st) {
     extern __shared__ float4 sbuf[];
-    float4* s0 = sbuf;
-    float4* s1 = sbuf + batch;
-    float4* s2 = sbuf + 2 * batch;
     const int words = (batch + 31) >> 5;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
@@ -301,15 +300,15 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
         if (__syncthreads_count(!all_done) == 0) break;
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
-            stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
+            stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, bits,
                                      words, nullptr, nullptr, !COUNT);
         __syncthreads();
         // this warp's entries in increasing order: the set bits of its words
         for (int g = 0; g < groups && !all_done; ++g) {
             for (uint32_t word = my_bits[g]; word != 0 && !all_done; word &= word - 1) {
                 const int k = g * 32 + __ffs(word) - 1;
-                const float4 a = s0[k];
-                const float4 b = s1[k];
+                const float4 a = sbuf[3 * k];
+                const float4 b = sbuf[3 * k + 1];
                 all_done = true;
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
@@ -324,7 +323,7 @@ __global__ void __launch_bounds__(512) blend_kernel(const ViewTable vt, const ui
                                 if (Tn < kTransmittanceMin) {
                                     p.done = true;
                                 } else {
-                                    const float4 c = s2[k];
+                                    const float4 c = sbuf[3 * k + 2];
                                     const float w = alpha * p.T;
                                     p.C0 += c.x * w;
                                     p.C1 += c.y * w;
@@ -381,11 +380,7 @@ __device__ __forceinline__ void blend_pair_tile(const ViewTable& vt, const uint3
                                                 uint32_t* __restrict__ pix_last,
                                                 uint2* __restrict__ pix_count,
                                                 const DeviceStatus* __restrict__ st) {
-    extern __shared__ float4 sbuf[];
-    const float4* e_q = sbuf;              // (qa qa, qb qb)
-    const float4* e_c = sbuf + batch;      // (qc qc, o o)
-    const float4* e_p = sbuf + 2 * batch;  // (px px, py py)
-    const float4* e_rgb = sbuf + 3 * batch;
+    extern __shared__ float4 sbuf[];  // entries (qa qa, qb qb), (qc qc, o o), (px px, py py), rgb
     const int words = (batch + 31) >> 5;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairs) * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
@@ -408,13 +403,14 @@ __device__ __forceinline__ void blend_pair_tile(const ViewTable& vt, const uint3
         if (__syncthreads_count(!all_done) == 0) break;
         const int cnt = min(batch, n - base), groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5))
-            stage_group<2, kPairs>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, batch, bits,
+            stage_group<2, kPairs>(vt, tc, g, cnt, vals + range.x + base, R, rec0, rec1, rec2, sbuf, bits,
                                    words, vt.masks ? vt.masks + range.x + base : nullptr, nullptr, !COUNT);
         __syncthreads();
         for (int g = 0; g < groups && !all_done; ++g) {
             for (uint32_t word = my_bits[g]; word != 0 && !all_done; word &= word - 1) {
                 const int k = g * 32 + __ffs(word) - 1;
-                const ulonglong2 q = pairs(e_q + k), c = pairs(e_c + k), pp = pairs(e_p + k);
+                const float4* e = sbuf + 4 * k;
+                const ulonglong2 q = pairs(e), c = pairs(e + 1), pp = pairs(e + 2);
                 // the exponent of support_power for both pixels
                 const f32x2 dx = sub2(pp.x, pcx), dy = sub2(pp.y, pcy);
                 const float2 pw = upk(fma2(dx, fma2(q.x, dx, mul2(q.y, dy)), mul2(mul2(c.x, dy), dy)));
@@ -435,7 +431,7 @@ __device__ __forceinline__ void blend_pair_tile(const ViewTable& vt, const uint3
                 }
                 done0 |= end0;
                 done1 |= end1;
-                const float4 rgb = e_rgb[k];
+                const float4 rgb = e[3];
                 if (add0) {
                     c00 = fmaf(rgb.x, w.x, c00);
                     c01 = fmaf(rgb.y, w.x, c01);
@@ -597,9 +593,6 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
     const uint32_t* __restrict__ pix_last, const float* __restrict__ dL_drgb,
     float4* __restrict__ grad2d, int64_t R, const DeviceStatus* __restrict__ st) {
     extern __shared__ float4 sbuf[];
-    float4* s0 = sbuf;
-    float4* s1 = sbuf + batch;
-    float4* s2 = sbuf + 2 * batch;
     const int words = (batch + 31) >> 5;
     uint32_t* sid = reinterpret_cast<uint32_t*>(sbuf + 3 * batch);
     uint32_t* bits = sid + batch;
@@ -651,7 +644,7 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
         const int cnt = hi - lo, groups = (cnt + 31) >> 5;
         for (int g = (int)(threadIdx.x >> 5); g < groups; g += (int)(blockDim.x >> 5)) {
             const uint32_t id = stage_group<PPT, kPlain>(vt, tc, g, cnt, vals + range.x + lo, R32, rec0, rec1, rec2,
-                                                         sbuf, batch, bits, words, nullptr, nullptr);
+                                                         sbuf, bits, words, nullptr, nullptr);
             if (g * 32 + lane < cnt) sid[g * 32 + lane] = id;
         }
         __syncthreads();
@@ -664,9 +657,9 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
                 word ^= 1u << bit;
                 const int j = g * 32 + bit;
                 const int k = lo + j;
-                const float4 a = s0[j];
-                const float4 b = s1[j];
-                const float4 c = s2[j];
+                const float4 a = sbuf[3 * j];
+                const float4 b = sbuf[3 * j + 1];
+                const float4 c = sbuf[3 * j + 2];
                 float d[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) d[i] = 0.0f;
@@ -734,12 +727,8 @@ __device__ __forceinline__ void blend_pair_backward_tile(
     int batch, float bg0, float bg1, float bg2, const float* __restrict__ pix_T,
     const uint32_t* __restrict__ pix_last, const float* __restrict__ dL_drgb,
     float4* __restrict__ grad2d, int64_t R, const DeviceStatus* __restrict__ st) {
+    // entries (qa qa, qb qb), (qc qc, o o), (px px, py py), (r r, g g), (b b, id 0)
     extern __shared__ float4 sbuf[];
-    const float4* e_q = sbuf;               // (qa qa, qb qb)
-    const float4* e_c = sbuf + batch;       // (qc qc, o o)
-    const float4* e_p = sbuf + 2 * batch;   // (px px, py py)
-    const float4* e_rg = sbuf + 3 * batch;  // (r r, g g)
-    const float4* e_b = sbuf + 4 * batch;   // (b b, 0 0)
     const int words = (batch + 31) >> 5;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sbuf + stage_fields(kPairsColour) * batch);
     const uint32_t* my_bits = bits + (threadIdx.x >> 5) * words;
@@ -792,7 +781,7 @@ __device__ __forceinline__ void blend_pair_backward_tile(
         __syncthreads();
         const int cnt = hi - lo, groups = (cnt + 31) >> 5;
         for (int gr_ = (int)(threadIdx.x >> 5); gr_ < groups; gr_ += (int)(blockDim.x >> 5)) {
-            stage_group<2, kPairsColour>(vt, tc, gr_, cnt, vals + range.x + lo, R32, rec0, rec1, rec2, sbuf, batch,
+            stage_group<2, kPairsColour>(vt, tc, gr_, cnt, vals + range.x + lo, R32, rec0, rec1, rec2, sbuf,
                                          bits, words, nullptr, vt.masks ? vt.masks + range.x + lo : nullptr);
         }
         __syncthreads();
@@ -805,7 +794,8 @@ __device__ __forceinline__ void blend_pair_backward_tile(
                 word ^= 1u << bit;
                 const int j = grp * 32 + bit;
                 const uint32_t k = (uint32_t)(lo + j);
-                const ulonglong2 q = pairs(e_q + j), c = pairs(e_c + j), pp = pairs(e_p + j);
+                const float4* e = sbuf + 5 * j;
+                const ulonglong2 q = pairs(e), c = pairs(e + 1), pp = pairs(e + 2);
                 // support_terms for both pixels
                 const f32x2 dx = sub2(pp.x, pcx), dy = sub2(pp.y, pcy);
                 const f32x2 u = fma2(q.x, dx, mul2(q.y, dy)), t = mul2(c.x, dy);
@@ -824,10 +814,10 @@ __device__ __forceinline__ void blend_pair_backward_tile(
                 const f32x2 w = mul2(alpha, Tp);
                 // dL/dalpha = T g.(rgb - acc): the gradient's dot with this Gaussian's colour
                 // minus its dot with the colour behind
-                const ulonglong2 rg = pairs(e_rg + j), bb = pairs(e_b + j);
-                const f32x2 e = sub2(fma2(gr, rg.x, fma2(gg, rg.y, mul2(gb, bb.x))), gacc);
-                const f32x2 dalpha = mul2(Tp, e);
-                gacc = fma2(alpha, e, gacc);  // alpha is 0 for a pixel that does not blend it
+                const ulonglong2 rg = pairs(e + 3), bb = pairs(e + 4);
+                const f32x2 ge = sub2(fma2(gr, rg.x, fma2(gg, rg.y, mul2(gb, bb.x))), gacc);
+                const f32x2 dalpha = mul2(Tp, ge);
+                gacc = fma2(alpha, ge, gacc);  // alpha is 0 for a pixel that does not blend it
                 // through alpha = o G only where the 0.99 clamp is not active: gG = dL/dalpha G
                 // and its moments gG (dx, dy, dx^2, dx dy, dy^2), summed over the pixels; the
                 // preprocess backward applies o and the conic once per record
