@@ -395,7 +395,7 @@ def run_gpu(args):
                                            survey_work=2 * n * p_bytes + visible * 36),
     }
     dom_name = max(kernels, key=lambda k: kernels[k]["ms"] * kernels[k]["launches"])
-    units = {"pixel": rast.num_pixels, "instance": M}
+    units = {"pixel": rast.num_pixels, "instance": M, "record": R}
     rates = _traffic_rates()
 
     def traffic(name):
