@@ -87,6 +87,11 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 template <int PPT>
 __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCoord& tc, float px, float py,
@@ -744,7 +749,7 @@ __device__ __forceinline__ void blend_pair_backward_tile(
     const int64_t hw = (int64_t)cam.W * cam.H;
     const float* gi = dL_drgb + 3 * cam.pixel_base;
     float g[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-    float T[2] = {1.0f, 1.0f};
+    float T[2] = {1.0f, 1.0f};  // the pixels' final transmittance, then packed into Tp
     uint32_t last[2] = {0u, 0u};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -761,6 +766,7 @@ __device__ __forceinline__ void blend_pair_backward_tile(
     const f32x2 pcx = pk((float)x + 0.5f, (float)x + 0.5f), pcy = pk((float)y0 + 0.5f, (float)y1 + 0.5f);
     const f32x2 gr = pk(g[0][0], g[1][0]), gg = pk(g[0][1], g[1][1]), gb = pk(g[0][2], g[1][2]);
     const f32x2 one = pk(1.0f, 1.0f);
+    f32x2 Tp = pk(T[0], T[1]);
     // the pixel's upstream gradient dotted with the colour behind (acc += alpha (rgb - acc),
     // from bg): one value per pixel carries what the three channels' accumulators would
     f32x2 gacc = fma2(gr, pk(bg0, bg0), fma2(gg, pk(bg1, bg1), mul2(gb, pk(bg2, bg2))));
@@ -806,11 +812,12 @@ __device__ __forceinline__ void blend_pair_backward_tile(
                 const bool use0 = k < last[0] && pw.x >= kSupportPower && a0 >= kAlphaMin;
                 const bool use1 = k < last[1] && pw.y >= kSupportPower && a1 >= kAlphaMin;
                 if (!__any_sync(kFullMask, use0 || use1)) continue;
-                const float2 om = upk(sub2(one, pk(a0, a1)));
-                if (use0) T[0] = __fdividef(T[0], om.x);
-                if (use1) T[1] = __fdividef(T[1], om.y);
                 const f32x2 alpha = pk(use0 ? a0 : 0.0f, use1 ? a1 : 0.0f);
-                const f32x2 Tp = pk(T[0], T[1]);
+                // T before this Gaussian, T / (1 - alpha) as T times the hardware reciprocal
+                // (the approximate division's own form); a pixel that does not blend it has
+                // alpha 0, whose reciprocal of exactly 1 is exactly 1: its T stays as it is
+                const float2 om = upk(sub2(one, alpha));
+                Tp = mul2(Tp, pk(rcp_approx(om.x), rcp_approx(om.y)));
                 const f32x2 w = mul2(alpha, Tp);
                 // dL/dalpha = T g.(rgb - acc): the gradient's dot with this Gaussian's colour
                 // minus its dot with the colour behind
