@@ -287,16 +287,18 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(const ViewTable vt, c
         const uint32_t obase = __shfl_sync(kFullMask, o, 0);
         const uint32_t incl = overflow ? 0u : o_next - obase;  // inclusive warp scan of the counts
         const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+        // Every kept record has at least one instance, so the records' first slots are
+        // distinct and increasing: slot e belongs to record (records starting at or before
+        // e) - 1.  A record without instances (past the kept ones) starts nowhere.
+        const uint32_t start = cnt ? incl - cnt : 0xffffffffu;
+        const uint32_t le_mask = lane == 31 ? kFullMask : (2u << lane) - 1u;
         for (uint32_t e0 = 0; e0 < total; e0 += 32) {
             const uint32_t e = e0 + lane;
-            int q = 0;  // records whose range ends at or before slot e
-#pragma unroll
-            for (int bstep = 16; bstep > 0; bstep >>= 1) {
-                const uint32_t v = __shfl_sync(kFullMask, incl, q + bstep - 1);
-                if (v <= e) q += bstep;
-            }
-            q = min(q, 31);
-            const uint32_t first = __shfl_sync(kFullMask, incl - cnt, q);
+            const uint32_t rel = start - e0;  // wraps past 32 for records starting before e0
+            const uint32_t starts = __reduce_or_sync(kFullMask, cnt && rel < 32u ? 1u << rel : 0u);
+            const int earlier = __popc(__ballot_sync(kFullMask, cnt && start < e0));
+            const int q = min(max(earlier + __popc(starts & le_mask) - 1, 0), 31);
+            const uint32_t first = __shfl_sync(kFullMask, start, q);
             const uint32_t cq = __shfl_sync(kFullMask, cnt, q);
             const uint32_t tb = __shfl_sync(kFullMask, tbase, q);
             const uint32_t rq = __shfl_sync(kFullMask, r, q);
