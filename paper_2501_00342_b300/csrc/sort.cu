@@ -114,6 +114,12 @@ struct SortShape {
 static_assert(SortShape<uint32_t>::TILE >= kSortTile && SortShape<unsigned long long>::TILE >= kSortTile,
               "a sort tile is smaller than the tile the look-back tables are sized for");
 
+// Asks L2 to fetch [p, p + bytes) from DRAM (a hint: nothing waits for it).  p and bytes
+// must be multiples of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -147,7 +153,8 @@ template <typename KeyT, int RB, bool DROP>
 __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesweep_kernel(
     const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* m_ptr, const uint32_t* __restrict__ goff,
-    unsigned long long* lookback, uint32_t* counter, int shift, int width, int pass, DeviceStatus* st) {
+    unsigned long long* lookback, uint32_t* counter, int shift, int width, int pass, DeviceStatus* st,
+    uint32_t ahead) {
     constexpr int RADIX = 1 << RB;
     constexpr int WARPS = kSortThreads / 32;
     constexpr int DPT = (RADIX + kSortThreads - 1) / kSortThreads;  // digits per thread
@@ -164,6 +171,19 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4) onesw
     const uint32_t tile = sm.tile;
     const uint64_t tile_start = (uint64_t)tile * kSortTile;
     if (tile_start >= m) return;  // whole CTA: nothing in this tile
+    if (threadIdx.x == 0) {
+        // the keys and values of the tile a CTA will claim about one CTA lifetime from now
+        // (`ahead` = the CTAs resident at once) travel to L2 while this tile is sorted; the
+        // ranges start 16-byte aligned (tile starts) and are cut down to 16-byte multiples,
+        // so they end inside the m items
+        const uint64_t ps = ((uint64_t)tile + ahead) * kSortTile;
+        if (ps < m) {
+            const uint32_t n = (uint32_t)(m - ps < (uint64_t)kSortTile ? m - ps : kSortTile);
+            const uint32_t kb = (uint32_t)(n * sizeof(KeyT)) & ~15u, vb = (n * 4u) & ~15u;
+            if (kb) prefetch_l2(kin + ps, kb);
+            if (vb) prefetch_l2(vin + ps, vb);
+        }
+    }
     const uint32_t count = (uint32_t)(m - tile_start < (uint64_t)kSortTile ? m - tile_start : kSortTile);
 
     // load keys warp-striped: item k of lane l of warp w is element w*32*ITEMS + k*32 + l
@@ -362,6 +382,11 @@ cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
     if (drop_first && (e = cudaFuncSetAttribute(onesweep_kernel<KeyT, RB, true>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<KeyT, RB, false>, kSortThreads,
+                                                           smem)) != cudaSuccess)
+        return e;
+    const uint32_t ahead = (uint32_t)(sm_count() * (per_sm > 0 ? per_sm : 1));
     for (int p = 0; p < passes; ++p) {
         const KeyT* kin = (p & 1) ? k1 : k0;
         const uint32_t* vin = (p & 1) ? v1 : v0;
@@ -371,10 +396,12 @@ cudaError_t sort_impl(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1,
         const uint32_t width = pass_width(p, RB, first_bit, key_bits);
         if (p == 0 && drop_first)
             onesweep_kernel<KeyT, RB, true><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-                kin, vin, kout, vout, mp, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, width, p, st);
+                kin, vin, kout, vout, mp, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, width, p, st,
+                ahead);
         else
             onesweep_kernel<KeyT, RB, false><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-                kin, vin, kout, vout, mp, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, width, p, st);
+                kin, vin, kout, vout, mp, goff + p * RADIX, lookback, counters + p, first_bit + p * RB, width, p, st,
+                ahead);
     }
     return cudaGetLastError();
 }
