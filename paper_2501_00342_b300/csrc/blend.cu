@@ -93,6 +93,21 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Asks L2 for the records of the batch entries [first, first + cnt) (ids clamped like the
+// staging's), one thread per entry: while the backward walks one staged batch, the gathers
+// of the next one travel from DRAM (a hint; nothing waits for it).  The forward does not
+// use it: it may stop a tile before its next batch, and the instructions cost more in its
+// issue-bound loop than the latency they hide (measured 3.32 -> 3.50 ms).
+__device__ __forceinline__ void prefetch_batch(const uint32_t* __restrict__ first, int cnt, uint32_t R,
+                                               const float4* rec0, const float4* rec1, const float4* rec2) {
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const uint32_t id = min(first[j], R - 1);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(rec0 + id));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(rec1 + id));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(rec2 + id));
+    }
+}
+
 template <int PPT>
 __device__ __forceinline__ uint32_t block_mask(const ViewTable& vt, const TileCoord& tc, float px, float py,
                                                float qa, float qb, float qc, float o) {
@@ -791,6 +806,7 @@ __device__ __forceinline__ void blend_pair_backward_tile(
                                          bits, words, nullptr, vt.masks ? vt.masks + range.x + lo : nullptr);
         }
         __syncthreads();
+        if (lo > 0) prefetch_batch(vals + range.x + max(0, lo - batch), lo - max(0, lo - batch), R32, rec0, rec1, rec2);
         // this warp's entries below its last contributor, back to front
         const int lim = min(cnt, warp_last - lo);
         for (int grp = ((lim + 31) >> 5) - 1; grp >= 0; --grp) {
