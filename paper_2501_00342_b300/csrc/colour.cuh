@@ -163,61 +163,6 @@ __device__ __forceinline__ void colour_eval(const P& p, const float* d, float* p
     }
 }
 
-// Colour parameters of one Gaussian held in registers.
-template <int L, int K, int AX>
-struct ColourParams {
-    static constexpr int NSH = (L + 1) * (L + 1);
-    static constexpr bool AXES = K > 0 && AX != kAxWorld;  // unit axes held
-    float sh[NSH][3];
-    float amp[K > 0 ? K : 1][3];
-    float axis[AXES ? K : 1][3];                      // unit lobe axes
-    float axis_norm[(K > 0 && AX == kAxFree) ? K : 1];  // |mu_k| (free axes)
-    float fq[AX == kAxFrame ? 4 : 1];                 // frame quaternion and |(1, f)|
-    float fnorm;
-    float sharp[K > 0 ? K : 1];
-
-    __device__ __forceinline__ void load(const sgs_gaussians& g, int64_t i) {
-        const int64_t S = g.stride;
-#pragma unroll
-        for (int k = 0; k < NSH; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sh[k][c] = __ldg(g.sh + (k * 3 + c) * S + i);
-        if constexpr (AX == kAxFrame && K > 0) {
-            const float f[3] = {__ldg(g.sg_axis + i), __ldg(g.sg_axis + S + i), __ldg(g.sg_axis + 2 * S + i)};
-            float R[3][3];
-            fnorm = frame_axes(f, fq, R);
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) axis[k][c] = R[c][k];
-        }
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) amp[k][c] = __ldg(g.sg_amp + (k * 3 + c) * S + i);
-            sharp[k] = __ldg(g.sg_sharp + k * S + i);
-            if constexpr (AX == kAxFree) {
-                float m[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) m[c] = __ldg(g.sg_axis + (k * 3 + c) * S + i);
-                const float n = axis_length(m);
-                axis_norm[k] = n;
-                const float inv = 1.0f / n;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) axis[k][c] = m[c] * inv;
-            }
-        }
-    }
-
-    __device__ __forceinline__ float csh(int k, int c) const { return sh[k][c]; }
-    __device__ __forceinline__ float camp(int k, int c) const { return amp[k][c]; }
-    __device__ __forceinline__ float caxis(int k, int c) const { return axis[k][c]; }
-    __device__ __forceinline__ float csharp(int k) const { return sharp[k]; }
-    __device__ __forceinline__ float caxis_norm(int k) const { return axis_norm[k]; }
-    __device__ __forceinline__ float cframe_q(int j) const { return fq[j]; }
-    __device__ __forceinline__ float cframe_norm() const { return fnorm; }
-};
-
 // Number of SH coefficients a record sums: (D+1)^2 with D = sh_degree, or with adaptive
 // degrees D = 0 / 1 / 2 as the record's integer pixel radius is below sh_radius[0] /
 // below sh_radius[1] / not (capped at the stored degree L).
@@ -303,8 +248,8 @@ struct ColourGrads {
         }
     }
 
-    // P: ColourParams or any layout with the same accessors (csh, camp, caxis, csharp,
-    // caxis_norm, cframe_q, cframe_norm)
+    // P: the colour parameters' accessors (csh, camp, caxis, csharp, caxis_norm, cframe_q,
+    // cframe_norm; ColourShared of the preprocess)
     template <class P>
     __device__ __forceinline__ void store(const P& p, const sgs_grads& out, int64_t S, int64_t i) const {
 #pragma unroll
