@@ -67,6 +67,12 @@ __device__ __forceinline__ void set_status(DeviceStatus* st, int32_t bits) {
 }
 
 // ---- decoupled look-back slots: 64-bit words, a tag in the high bits and a count below ----
+// Asks L2 to fetch [p, p + bytes) from DRAM (a hint: nothing waits for it).  p and bytes
+// must be multiples of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void slot_store(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }

@@ -114,12 +114,6 @@ struct SortShape {
 static_assert(SortShape<uint32_t>::TILE >= kSortTile && SortShape<unsigned long long>::TILE >= kSortTile,
               "a sort tile is smaller than the tile the look-back tables are sized for");
 
-// Asks L2 to fetch [p, p + bytes) from DRAM (a hint: nothing waits for it).  p and bytes
-// must be multiples of 16.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
