@@ -218,9 +218,10 @@ __device__ __forceinline__ void count_tile_digits(uint32_t* h, int passes, uint3
 // (perm, RecordValue ids): sorted position j emits its record's offsets[j + 1] - offsets[j]
 // tiles at offsets[j] (the scan taken in that order), tiles row-major.  One warp per 32
 // consecutive sorted positions, whose instances fill one contiguous output range 32 slots
-// at a time: for slot e a 5-step shuffle search finds the record (the offsets relative to
-// the warp's first are the inclusive scan of the counts), its packed row table (written by
-// preprocess, staged in shared memory) gives the row, and consecutive lanes write
+// at a time: slot e belongs to the record whose first slot is the last at or before e
+// (the offsets relative to the warp's first are the inclusive scan of the counts; the
+// records' first slots are found from one OR-reduction and one ballot), its packed row
+// table (written by preprocess, staged in shared memory) gives the row, and consecutive lanes write
 // consecutive slots.  A record whose table overflowed is filled afterwards by the whole
 // warp, recomputing its rows with row_span.  Since every instance of a record has the same
 // depth, this order is (depth bits, record) -- what the depth half of a stable LSD radix

@@ -15,10 +15,12 @@
 //
 // The backward pass walks each tile's list from the last contributor to the front,
 // rebuilding T_k = T_{k+1} / (1 - alpha_k) from the stored final transmittance and
-// carrying the normalised colour behind (acc += alpha (rgb - acc), starting at bg).  It
+// carrying the normalised colour behind (acc += alpha (rgb - acc), starting at bg; the
+// two-pixel kernel carries its dot product with the pixel's upstream gradient).  It
 // recomputes power and alpha with the same operations as the forward pass, so every skip
 // decision is identical; per Gaussian the warp's 9 gradient sums are reduced with shuffles
-// and added with two 16-byte vector atomics and one scalar atomic.  The sums are those of
+// and added by one scalar reduction instruction from nine lanes (the two-pixel kernel) or
+// two 16-byte vector reductions and a scalar one (the others).  The sums are those of
 // gG = dL/dalpha G (where the 0.99 clamp is not active) and its moments gG dx, gG dy,
 // gG dx^2, gG dx dy, gG dy^2 (d = centre - pixel centre), and of alpha T dL/dC per channel:
 // the power is a quadratic form in d, so its derivatives in the centre and the conic are
@@ -739,8 +741,10 @@ __global__ void __launch_bounds__(512) blend_backward_kernel(
 // The reverse walk with two pixels per thread in packed pairs (the pixel map of
 // blend_pair_kernel).  The exponent, opacity product and gradient terms of both pixels run
 // as f32x2 instructions, each half rounded exactly as the scalar pass rounds it, so every
-// skip decision matches the forward.  The transmittance and the colour behind are updated
-// per pixel; a pixel that does not blend the Gaussian contributes zero-weighted terms.
+// skip decision matches the forward.  The two pixels' transmittance and the dot products
+// of their upstream gradients with the colour behind stay packed; a pixel that does not
+// blend the Gaussian takes alpha 0, which leaves both unchanged and weights its terms
+// zero.
 __device__ __forceinline__ void blend_pair_backward_tile(
     const ViewTable& vt, const uint32_t tile, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
     uint32_t R32, const float4* __restrict__ rec0, const float4* __restrict__ rec1, const float4* __restrict__ rec2,
