@@ -176,15 +176,16 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
 // Tiles the ellipse reaches (0: the Gaussian is culled), and the packed row table the
 // duplicate kernel reads (16 words): word 0 = first row | rows << 16; words 1..15 = first
 // column | (tiles in the earlier rows) << 16 per row; words past the last row are unused
-// (the second 32-byte half is stored only for tables of more than kSpanRowsShort rows).  More than kSpanRows rows or more
-// than 65535 tiles mark a table the kernel recomputes instead.  The table is written to
-// table[k * stride] (a thread's column of a shared-memory array).  Done for the 32 records
-// of a warp at once (warp-collective; lanes whose record is not visible pass
-// visible = false and get 0).  The (record, row) pairs of the warp are dealt out 32 at a
-// time, so a lane with many rows does not hold up the warp: each pair's lane finds its
-// record by a 5-step search of the inclusive scan of the row counts, takes the record's
-// ellipse from that lane by shuffles and runs row_span on it (the same bits as the
-// record's own lane would get).  Rows are written into the owner's table as first column |
+// (the second 32-byte half is stored only for tables of more than kSpanRowsShort rows).
+// More than kSpanRows rows or more than 65535 tiles mark a table the kernel recomputes
+// instead.  The table is written to table[k * stride] (a thread's column of a shared-memory
+// array).  Done for the 32 records of a warp at once (warp-collective; lanes whose record
+// is not visible pass visible = false and get 0).  Each lane computes its own record's
+// first row; the later (record, row) pairs of the warp are dealt out 32 at a time, so a
+// lane with many rows does not hold up the warp: each pair's lane finds its record by a
+// 5-step search of the inclusive scan of the later-row counts, takes the record's ellipse
+// from that lane by shuffles and runs row_span on it (the same bits as the record's own
+// lane would get).  Rows are written into the owner's table as first column |
 // tiles in the row << 16 and turned into first column | tiles in the earlier rows << 16
 // by the owner afterwards.  s_hits: one counter per thread of the block (shared memory).
 __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool visible, const View& cam,
@@ -198,7 +199,17 @@ __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool vi
     if (visible) rs = row_setup(P.px, P.py, P.A, P.B, P.C, vt.inv_tile_h, cam.tiles_y);
     const int rows = rs.ok ? rs.ty1 - rs.ty0 + 1 : 0;
     s_hits[threadIdx.x] = 0u;
-    int incl = rows;  // inclusive scan of the rows over the warp
+    // each record's first row by its own lane (no shuffles)
+    uint32_t hits_first = 0;
+    if (rows > 0) {
+        int a0 = 0, a1 = -1;
+        row_span(rs, P.px, P.py, P.B, rs.ty0, vt.inv_tile_w, vt.tile_h, cam.tiles_x, a0, a1);
+        hits_first = a1 >= a0 ? (uint32_t)(a1 - a0 + 1) : 0u;
+        table[stride] = (uint32_t)(hits_first ? a0 : 0) | (hits_first << 16);
+    }
+    // the later rows, dealt out across the warp
+    const int rest = rows > 1 ? rows - 1 : 0;
+    int incl = rest;  // inclusive scan of the later rows over the warp
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kFullMask, incl, o);
@@ -208,14 +219,14 @@ __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool vi
     __syncwarp();
     for (int e0 = 0; e0 < total; e0 += 32) {
         const int e = e0 + lane;
-        int q = 0;  // records whose rows end at or before pair e
+        int q = 0;  // records whose later rows end at or before pair e
 #pragma unroll
         for (int b = 16; b > 0; b >>= 1) {
             const int v = __shfl_sync(kFullMask, incl, q + b - 1);
             if (v <= e) q += b;
         }
         q = min(q, 31);
-        const int first = __shfl_sync(kFullMask, incl - rows, q);
+        const int first = __shfl_sync(kFullMask, incl - rest, q);
         RowSpans rq;
         rq.ok = true;
         rq.ty0 = __shfl_sync(kFullMask, rs.ty0, q);
@@ -229,7 +240,7 @@ __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool vi
         const float px = __shfl_sync(kFullMask, P.px, q), py = __shfl_sync(kFullMask, P.py, q);
         const float B = __shfl_sync(kFullMask, P.B, q);
         if (e < total) {
-            const int k = e - first;
+            const int k = e - first + 1;  // row index within the record (row 0 is its own lane's)
             int a0 = 0, a1 = -1;
             row_span(rq, px, py, B, rq.ty0 + k, vt.inv_tile_w, vt.tile_h, cam.tiles_x, a0, a1);
             const uint32_t len = a1 >= a0 ? (uint32_t)(a1 - a0 + 1) : 0u;
@@ -245,7 +256,7 @@ __device__ __forceinline__ uint32_t count_tiles_warp(const Projected& P, bool vi
         table[(1 + k) * stride] = (w & 0xffffu) | (min(hits, 0xffffu) << 16);
         hits += w >> 16;
     }
-    hits = s_hits[threadIdx.x];
+    hits = s_hits[threadIdx.x] + hits_first;
     const bool fits = rows <= kSpanRows && hits <= 0xffffu;
     table[0] = (uint32_t)rs.ty0 | ((fits ? (uint32_t)rows : kSpanRowsOverflow) << 16);
     return rs.ok ? hits : 0u;
