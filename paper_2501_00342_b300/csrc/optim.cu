@@ -52,16 +52,16 @@ __device__ __forceinline__ float act_slope(float a, int kind) {
     return 1.0f;
 }
 
+// Grid: blockIdx.y is the row (a block's row constants are uniform), blockIdx.x and the
+// threads stride over the row's quads of four entries.
 __global__ void __launch_bounds__(256) adam_kernel(const RowTable t) {
     const int64_t quads = (t.n + 3) / 4;
-    const int64_t total = quads * t.rows;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(j / quads);
-        const int64_t i0 = (j - (int64_t)r * quads) * 4;
-        const Row& w = t.row[r];
-        const float lr = t.lr[w.group];
-        if (lr == 0.0f) continue;  // frozen group: nothing changes
-        const float c1 = t.c1[w.group], c2 = t.c2[w.group];
+    const Row& w = t.row[blockIdx.y];
+    const float lr = t.lr[w.group];
+    if (lr == 0.0f) return;  // frozen group: nothing changes
+    const float c1 = t.c1[w.group], c2 = t.c2[w.group];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = q * 4;
         // the stride is a multiple of 4: entries i0..i0+3 are inside the padded row
         float4 x = *reinterpret_cast<const float4*>(w.raw + i0);
         const float4 g4 = *reinterpret_cast<const float4*>(w.grad + i0);
@@ -139,9 +139,12 @@ cudaError_t launch_adam(const sgs_gaussians& layout, const sgs_grads& raw, const
             add(raw.sg_axis, act.sg_axis, grad.sg_axis, m.sg_axis, v.sg_axis, axis_rows, SGS_GROUP_SG, kIdentity);
     }
     if (layout.n == 0 || t.rows == 0) return cudaSuccess;
-    const int64_t work = (layout.n + 3) / 4 * t.rows;
-    const int64_t want = (work + 255) / 256;
-    adam_kernel<<<(unsigned)stride_grid(want, 16), 256, 0, s>>>(t);
+    // about 16 CTAs of 256 threads per SM over all rows together
+    const int64_t quads = (layout.n + 3) / 4;
+    const int64_t per_row = (quads + 255) / 256;
+    const int64_t cap = (16 * (int64_t)sm_count() + t.rows - 1) / t.rows;
+    const dim3 grid((unsigned)(per_row < cap ? per_row : (cap > 0 ? cap : 1)), (unsigned)t.rows);
+    adam_kernel<<<grid, 256, 0, s>>>(t);
     return cudaGetLastError();
 }
 
