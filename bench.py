@@ -371,15 +371,16 @@ def run_gpu(args):
     fwd_name = "blend_pair_kernel" if settings.fwd_pixels in (0, 2) else "blend_kernel"
     bwd_name = "blend_pair_backward_kernel" if settings.bwd_pixels in (0, 2) else "blend_backward_kernel"
     # algorithmic bytes of each HBM-bound kernel: everything this design's kernel must read
-    # and write ("work"), and, where the survey gives a narrower count (parameters plus the
-    # records of its own model), that count too ("survey_work")
+    # and write ("work"), and, for the preprocess kernels, a narrower count too: the
+    # parameters plus a minimal 44-byte record per (view, Gaussian) and, backward, 36 bytes
+    # of 2D gradients per visible record ("narrow_work")
     R = n * nv
     kernels = {
         # parameters once; per visible record its 48-byte record and the row table's first
         # 32-byte sector; per record its rectangle, tile count, flags and record-sort pair
         "preprocess_kernel": dict(ms=stages["preprocess"], launches=1, bound="hbm",
                                   work=n * p_bytes + visible * (48 + 32) + R * (8 + 4 + 4 + 8),
-                                  survey_work=n * p_bytes + R * 44),
+                                  narrow_work=n * p_bytes + R * 44),
         # the instances written (u32 tile id + u32 record id); per visible record its row
         # table sector, sorted position and scan offset read
         "duplicate_kernel": dict(ms=stages["duplicate"], launches=1, bound="hbm", work=8 * M + visible * (32 + 8)),
@@ -392,7 +393,7 @@ def run_gpu(args):
         # record its 36-byte 2D gradient read and cleared
         "preprocess_backward_kernel": dict(ms=stages["backward_preprocess"], launches=1, bound="hbm",
                                            work=2 * n * p_bytes + R * 4 + visible * 72,
-                                           survey_work=2 * n * p_bytes + visible * 36),
+                                           narrow_work=2 * n * p_bytes + visible * 36),
     }
     dom_name = max(kernels, key=lambda k: kernels[k]["ms"] * kernels[k]["launches"])
     units = {"pixel": rast.num_pixels, "instance": M, "record": R}
@@ -412,9 +413,9 @@ def run_gpu(args):
             roofs[name] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                            "frac": round(achieved / hbm, 4), "traffic": traffic(name),
                            "algorithmic_bytes_per_launch": int(k["work"]), "ms_per_launch": round(k["ms"], 4)}
-            if "survey_work" in k:
-                roofs[name]["survey_bytes_per_launch"] = int(k["survey_work"])
-                roofs[name]["frac_survey_count"] = round(k["survey_work"] / (k["ms"] / 1e3) / 1e9 / hbm, 4)
+            if "narrow_work" in k:
+                roofs[name]["narrow_bytes_per_launch"] = int(k["narrow_work"])
+                roofs[name]["frac_narrow_count"] = round(k["narrow_work"] / (k["ms"] / 1e3) / 1e9 / hbm, 4)
         else:
             achieved = k["work"] / (k["ms"] / 1e3) / 1e12
             roofs[name] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
