@@ -153,8 +153,8 @@ __device__ __forceinline__ void project_exact(const View& cam, const float X[3],
     const float disc = sub_rn(mul_rn(mid, mid), det);
     const float l1 = add_rn(mid, sqrt_rn(fmaxf(0.1f, disc)));
     const float rad = ceilf(mul_rn(3.0f, sqrt_rn(l1)));
-    const float px = add_rn(mul_rn(cam.fx, div_rn(P.t[0], tz)), cam.cx);
-    const float py = add_rn(mul_rn(cam.fy, div_rn(P.t[1], tz)), cam.cy);
+    const float px = add_rn(mul_rn(cam.fx, u0), cam.cx);  // u0, v0: the unclamped x/z, y/z
+    const float py = add_rn(mul_rn(cam.fy, v0), cam.cy);
     if (rad != rad || px != px || py != py) return;
     const float fx0 = floorf(mul_rn(sub_rn(px, rad), inv_tw));  // == division by the tile side
     const float fx1 = floorf(mul_rn(add_rn(px, rad), inv_tw));
