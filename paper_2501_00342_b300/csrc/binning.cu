@@ -285,6 +285,24 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(const ViewTable vt, c
         }
         __syncwarp();
         const bool slow = cnt && (hdr >> 16) == kSpanRowsOverflow;
+        // For a record of at most 32 instances whose rows all have tiles: bit s set where a
+        // row starts (slot s of the record, bit 0 for row 0), so that a slot's row is the
+        // count of row starts at or before it.  0: the slots search the table instead.
+        uint32_t rowmask = 0u;
+        if (cnt && cnt <= 32u && !slow) {
+            const uint32_t* tl = reinterpret_cast<const uint32_t*>(tab[lane]);
+            const int rws = (int)(hdr >> 16);
+            uint32_t mask = 1u, prev = 0u;
+            bool ok = true;
+            for (int rr = 1; rr < rws; ++rr) {
+                const uint32_t b = tl[1 + rr] >> 16;  // tiles before row rr
+                ok &= b != prev;                      // else row rr - 1 is empty
+                prev = b;
+                mask |= b < 32u ? 1u << b : 0u;
+            }
+            ok &= prev < cnt;  // else the last row is empty
+            rowmask = ok ? mask : 0u;
+        }
         const uint32_t obase = __shfl_sync(kFullMask, o, 0);
         const uint32_t incl = overflow ? 0u : o_next - obase;  // inclusive warp scan of the counts
         const uint32_t total = __shfl_sync(kFullMask, incl, 31);
@@ -305,13 +323,18 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(const ViewTable vt, c
             const uint32_t rq = __shfl_sync(kFullMask, r, q);
             const int TWq = __shfl_sync(kFullMask, TW, q);
             const bool slow_q = __shfl_sync(kFullMask, (uint32_t)slow, q) != 0u;
+            const uint32_t rm = __shfl_sync(kFullMask, rowmask, q);
             if (e < total && !slow_q) {
                 const uint32_t* tq = reinterpret_cast<const uint32_t*>(tab[q]);
                 const uint32_t local = e - first;
                 const int rows = (int)(tq[0] >> 16);
                 // the row holding slot `local`: the last row whose tiles-before <= local
                 int k = 0;
-                while (k + 1 < rows && (tq[2 + k] >> 16) <= local) ++k;
+                if (rm) {
+                    k = __popc(rm & (local >= 31u ? kFullMask : (2u << local) - 1u)) - 1;
+                } else {
+                    while (k + 1 < rows && (tq[2 + k] >> 16) <= local) ++k;
+                }
                 const uint32_t rw = tq[1 + k];
                 const uint32_t before = rw >> 16;
                 const uint32_t after = k + 1 < rows ? (tq[2 + k] >> 16) : cq;
