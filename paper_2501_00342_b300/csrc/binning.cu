@@ -244,7 +244,12 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(const ViewTable vt, c
     constexpr int MAXP = (32 + RB - 1) / RB;  // passes of a tile-id sort
     __shared__ uint32_t h[MAXP * RADIX];
     __shared__ uint4 tab_all[8][32][4];  // the row tables of each warp's 32 records
+    // (tile_base, tiles_x) of every view: read per record with a per-lane view index, which
+    // the constant bank would serialise over the views of a warp
+    __shared__ uint2 s_view[SGS_MAX_VIEWS];
     for (int j = threadIdx.x; j < passes * RADIX; j += blockDim.x) h[j] = 0;
+    for (int j = threadIdx.x; j < vt.B; j += blockDim.x)
+        s_view[j] = make_uint2(vt.v[j].tile_base, (uint32_t)vt.v[j].tiles_x);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     uint4 (*tab)[4] = tab_all[threadIdx.x >> 5];
@@ -270,9 +275,9 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(const ViewTable vt, c
         uint32_t tbase = 0, hdr = 0;
         int TW = 0;
         if (cnt) {
-            const int v = (int)(r / n32);
-            tbase = vt.v[v].tile_base;
-            TW = vt.v[v].tiles_x;
+            const uint2 vw = s_view[r / n32];
+            tbase = vw.x;
+            TW = (int)vw.y;
             // the table's first sector; the second only for more than kSpanRowsShort rows
             // (words past a table's last row are never read)
             tab[lane][0] = spans[4 * (size_t)r];
